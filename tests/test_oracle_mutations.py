@@ -1,0 +1,46 @@
+"""Plant plausible mistakes in a copy of the oracle source (CPU only) and
+check that at least one pin in ``oracle_pins`` catches each of them."""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("row residual drops -A x_k", "r[i] = b[i] - z[i] - Ax[i];", "r[i] = b[i] - z[i];"),
+    ("column step sign flipped", "z[i] -= Ax[i];", "z[i] += Ax[i];"),
+    ("no column step (z_k kept)", "z[i] -= Ax[i];", "(void)0;"),
+    ("x update sign flipped", "x[j] += d[j];", "x[j] -= d[j];"),
+    # (lower_bound in place of upper_bound differs only when a target equals a
+    # prefix sum exactly, probability below len * 2^-61 per draw, so it is not
+    # observable and not listed; an off-by-one in the drawn index is.)
+    ("drawn index off by one", "flag[lo] = 1;", "flag[lo > 0 ? lo - 1 : 0] = 1;"),
+    ("Philox key word swapped", "uint64_t y0 = hi1 ^ x1 ^ k0;", "uint64_t y0 = hi1 ^ x1 ^ k1;"),
+    ("weights not squared", "(v[j] * v[j]) / norm2[j]", "fabs(v[j]) / norm2[j]"),
+    ("LSQR steps along v instead of w", "y[j] += (phi / rho) * w[j];",
+     "y[j] += (phi / rho) * v[j];"),
+    ("quantisation scale too coarse", "const int K = 62 - ceil_log2_i64(len);",
+     "const int K = 2 - ceil_log2_i64(len);"),
+    ("transpose product uses row index", "g[ci[e]] += av[e] * z[i];", "g[ci[e]] += av[e] * z[ci[e] % m];"),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, orig, bad):
+    src = oracle.source()
+    assert src.count(orig) >= 1, f"mutation anchor not found: {orig}"
+    lib = oracle.build_variant(src.replace(orig, bad), os.path.join(tmp_path, "mutant.so"))
+    failed = []
+    with oracle.use_library(lib):
+        for pin in P.ALL_PINS:
+            try:
+                pin()
+            except AssertionError:
+                failed.append(pin.__name__)
+            except Exception as exc:  # a crash of the mutant counts as caught
+                failed.append(f"{pin.__name__}:{type(exc).__name__}")
+            if failed:
+                break
+    assert failed, f"no pin caught the planted mistake: {name}"
