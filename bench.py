@@ -1,0 +1,421 @@
+"""Benchmark of the GB300 RGDBEK solver (one JSON line on stdout).
+
+Workload: the sparse inconsistent least-squares system of 200000 x 50000 with
+20 distinct uniformly random columns per row, N(0,1) values, b = A x* + e,
+e ~ N(0, 1e-4) (sigma 1e-2), solved by RGDBEK with eta = 0.1 for rows and
+columns until ||A^T(b - Ax)|| / ||A^T b|| <= 1e-8 (the minimum-norm
+least-squares solution).  A step is one full solve from x_0 = 0; the metric
+is outer iterations per second over the K timed solves, with the matrix and
+b resident in HBM; L2 is flushed (a 256 MiB write) before every timed solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain implementation of the
+paper's Algorithm 1 used by the tests) on the same workload, each step a
+bounded sample of outer iterations.
+Under torchrun (N > 1) every rank solves its own independent system of the
+same shape (seed + rank): no data-path collective, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = dict(name="sparse_ls_200000x50000_k20", m=200000, n=50000, k=20, sigma=1e-2, seed=1,
+                eta=0.1, tol=1e-8, stop_rule="normal_eq", max_iter=100000)
+METRIC = "RGDBEK outer iterations/s (time-to-1e-8 normal-equation residual)"
+UNIT = "iters/s"
+L2_FLUSH_BYTES = 256 << 20
+ORACLE_SAMPLE_ITERS = 20       # cpu_baseline: outer iterations of the oracle
+REF_STEP_ITERS = 4             # --impl reference: outer iterations per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--max-iter", type=int, default=None,
+                    help="cap on outer iterations per solve (profiling runs only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_system(rank: int):
+    w = WORKLOAD
+    return workloads.sparse_ls(w["m"], w["n"], w["k"], sigma=w["sigma"], seed=w["seed"] + rank)
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes of one solve (FP64 values, int32 indices, int64 pointers),
+# from the per-iteration counters the kernel reports.  Compulsory traffic of
+# each phase: matrix arrays streamed once per pass, each vector read or
+# written once per phase that touches it.
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(st, m: int, n: int, nnz: int) -> float:
+    it = st.iters
+    full_passes = it * ((12 * nnz + 16 * m + 64 * n)        # column pass (A^T z, A^T t, x update)
+                        + (12 * nnz + 24 * m + 16 * n))     # residual pass t = b - A x
+    # the last column pass (the converged test) has no residual pass after it
+    full_passes += 12 * nnz + 16 * m + 64 * n
+    selection = it * (23 * n + 23 * m)                      # quantise, marks, compaction
+    extraction = it * (2 * (8 * m + 4 * nnz + 4 * n) + 8 * m     # A_U: count + write over CSR
+                       + 2 * (8 * n + 4 * nnz + 4 * m) + 8 * n)  # A^J: count + write over CSC
+    extraction += 12 * st.sum_nnz_u + 12 * st.sum_nnz_j + 24 * st.sum_nu + 16 * st.sum_nj
+    zstep = it * 56 * m + 12 * st.sum_nnz_u + 8 * st.sum_nu
+    lsqr_u = 24 * st.lsqr_nnz_u + 32 * m * st.inner_u + 90 * st.lsqr_n_u
+    lsqr_j = (12 * st.sum_nnz_j + 16 * n * it + 8 * st.sum_nj        # first v of each row block
+              + 24 * st.lsqr_nnz_j + 80 * n * st.inner_j + 44 * st.lsqr_n_j)
+    return float(full_passes + selection + extraction + zstep + lsqr_u + lsqr_j)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            import tempfile
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        self.out.close()
+        try:
+            os.remove(self.out.name)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        loaded = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_iters_per_s(S, iters: int):
+    import oracle
+    w = WORKLOAD
+    o = oracle.Options(eta_col=w["eta"], eta_row=w["eta"], stop_rule=2, tol=0.0, inner_tol=1e-10,
+                       inner_max=200, max_iter=iters, seed=0)
+    t0 = time.perf_counter()
+    res = oracle.solve(S.A, S.b, o, n=S.n)
+    dt = time.perf_counter() - t0
+    return res.iters, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    S = make_system(0)
+    for _ in range(args.warmup):
+        oracle_iters_per_s(S, 1)
+    times, iters = [], 0
+    for _ in range(args.steps):
+        it, dt = oracle_iters_per_s(S, REF_STEP_ITERS)
+        times.append(dt)
+        iters += it
+    total = sum(times)
+    value = iters / total
+    w = WORKLOAD
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "nnz": S.nnz,
+                   "eta": w["eta"], "tol": w["tol"], "stop_rule": w["stop_rule"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{REF_STEP_ITERS} outer iterations from x_0 = 0 per step "
+                                   "(FP64 C oracle, single thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_rgdbek_build", os.path.join(ROOT, "paper_2509_19267_gb300", "build.py"))
+    bmod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bmod)
+    if rank == 0:
+        bmod.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2509_19267_gb300 as rg
+
+    w = WORKLOAD
+    max_iter = args.max_iter if args.max_iter is not None else w["max_iter"]
+    S = make_system(rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    opts = dict(eta_col=w["eta"], eta_row=w["eta"], stop_rule=rg.STOP_NORMAL)
+    solver = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, **opts)
+    info = solver.info()
+    b = torch.from_numpy(S.b).to(dev)
+    x = torch.empty(S.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_solve(seed):
+        st = rg.rgdbek_solve(solver.handle, b, x, w["tol"], max_iter, seed)
+        return st
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        one_solve(1000 + i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    for i in range(args.steps):
+        flush.fill_(float(i))                     # evict A and the vectors from L2
+        ev[i][0].record(stream)
+        stats.append(one_solve(i))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(bb) for a, bb in ev]
+    total_s = sum(ms) / 1e3
+    iters = sum(s.iters for s in stats)
+    if dist is not None:
+        t = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_max, iters_all = float(tmax[0]), float(t[1])
+    else:
+        total_max, iters_all = total_s, float(iters)
+    value = iters_all / total_max
+
+    # roofline of the dominant kernel (the persistent solve kernel): algorithmic
+    # bytes per launch over its CUDA-event duration
+    peak, peak_kind = measured_peaks()
+    bytes_per = [algorithmic_bytes(s, S.m, S.n, S.nnz) for s in stats]
+    achieved = sum(bytes_per) / total_s / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("kernel_source_hash") == source_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+
+    # standalone SpMV kernels (the a1 / a5 products), L2 flushed before each launch
+    spmv = spmv_rooflines(rg, solver, S, dev, flush, peak)
+
+    # end to end through the public API with host buffers: create from pinned
+    # host CSR (H2D of A and the CSC/norm set-up), solve with host b and x
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(rg, S, opts, w, max_iter, args)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        it_o, dt_o = oracle_iters_per_s(S, ORACLE_SAMPLE_ITERS)
+        cpu = {"value": it_o / dt_o, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {ORACLE_SAMPLE_ITERS} outer iterations from x_0 = 0 of the same "
+                         f"system (FP64 C oracle, single thread, {dt_o:.1f} s)"}
+
+    if rank == 0:
+        st0 = stats[0]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "m": S.m, "n": S.n, "nnz": S.nnz, "eta": w["eta"],
+                       "tol": w["tol"], "stop_rule": w["stop_rule"],
+                       "l2": "flushed before every timed solve (256 MiB write)",
+                       "grid": info.grid, "threads_per_block": info.threads_per_block,
+                       "parallelism": "independent system per GPU" if world > 1 else "1 GPU"},
+            "time_to_tol_s": statistics.median(ms) / 1e3,
+            "iters_per_solve": [s.iters for s in stats],
+            "final_normal_res": st0.normal_res, "final_rel_res": st0.rel_res,
+            "wall_s": wall,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "solve_kernel (persistent, one launch per solve)",
+                         "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": statistics.mean(bytes_per)},
+            "spmv": spmv,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_19267_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def spmv_rooflines(rg, solver, S, dev, flush, peak):
+    import torch
+    xv = torch.randn(S.n, dtype=torch.float64, device=dev)
+    zv = torch.randn(S.m, dtype=torch.float64, device=dev)
+    y = torch.empty(S.m, dtype=torch.float64, device=dev)
+    g = torch.empty(S.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    # algorithmic bytes: matrix (12 B/nnz + pointers) + source vector once + result once
+    cases = {"csr_Ax": (lambda: rg.rgdbek_spmv(solver.handle, xv, y),
+                        12 * S.nnz + 8 * (S.m + 1) + 8 * S.n + 8 * S.m),
+             "csc_ATz": (lambda: rg.rgdbek_spmv_t(solver.handle, zv, g),
+                         12 * S.nnz + 8 * (S.n + 1) + 8 * S.m + 8 * S.n)}
+    for name, (fn, nbytes) in cases.items():
+        for _ in range(3):
+            fn()
+        ts = []
+        for i in range(10):
+            flush.fill_(float(i))
+            a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            bb.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(bb) / 1e3)
+        t = statistics.median(ts)
+        gbs = nbytes / t / 1e9
+        out[name] = {"us": t * 1e6, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / peak}
+    return out
+
+
+def end_to_end(rg, S, opts, w, max_iter, args):
+    import torch
+    rp = torch.from_numpy(S.row_ptr).pin_memory()
+    ci = torch.from_numpy(S.col_idx).pin_memory()
+    av = torch.from_numpy(S.vals).pin_memory()
+    b = torch.from_numpy(S.b).pin_memory()
+    x = torch.empty(S.n, dtype=torch.float64).pin_memory()
+    o = rg.default_options(**opts)
+
+    def step(seed):
+        h = rg._ptr()
+        st = rg._lib.rgdbek_create(rg.ctypes.byref(h), S.m, S.n, S.nnz, rp.data_ptr(),
+                                   ci.data_ptr(), av.data_ptr(), 0, rg.ctypes.byref(o),
+                                   torch.cuda.current_stream().cuda_stream)
+        rg._check(st, "rgdbek_create")
+        res = rg.rgdbek_solve_host(h.value, b, x, w["tol"], max_iter, seed)
+        rg.rgdbek_destroy(h.value)
+        return res
+
+    nsteps = max(1, min(args.steps, 3))
+    step(99)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    for i in range(nsteps):
+        its += step(i).iters
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 8 * (S.m + 1) + 12 * S.nnz + 8 * S.m
+    d2h = 8 * S.n + 256
+    return {"value": its / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": nsteps,
+            "what": "rgdbek_create from pinned host CSR + rgdbek_solve_host + destroy per step"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

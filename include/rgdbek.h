@@ -1,0 +1,211 @@
+/*
+ * rgdbek.h — C ABI of the GB300 (sm_103a) RGDBEK solver library.
+ *
+ * RGDBEK (Randomized Greedy Double Block Extended Kaczmarz, arXiv 2509.19267)
+ * solves A x = b for A in R^{m x n}, consistent or not (Eq. 1), and converges
+ * to the minimum-norm least-squares solution x* = A^+ b (Theorem 2.3).  One
+ * outer iteration (Algorithm 1) is:
+ *   1. column weights eps^z_j = (A_j^T z_k)^2 / ||A_j||^2            (Section 2)
+ *   2. draw ceil(eta_col * n) columns with probability proportional to eps^z;
+ *      the column block U_k is the set of distinct drawn indices
+ *   3. z_{k+1} = z_k - A_U A_U^+ z_k                                  (Eq. 4)
+ *   4. row weights eps^x_i = (b_i - z_{k+1,i} - A^(i) x_k)^2 / ||A^(i)||^2
+ *   5. draw ceil(eta_row * m) rows the same way -> row block J_k
+ *   6. x_{k+1} = x_k + (A^J)^+ (b^J - z_{k+1}^J - A^J x_k)           (Eq. 4)
+ * with x_0 = 0 and z_0 = b.  The block pseudo-inverse products are computed
+ * by LSQR started from zero (Remark 3.1), which gives minimum-norm solutions.
+ *
+ * Every pointer argument marked "device" is CUDA device memory of the
+ * current device; "host" pointers are ordinary CPU memory.  All device work
+ * of a handle runs on the handle's stream (rgdbek_set_stream).  Handles are
+ * not thread-safe: use one handle per stream.  No function throws; every
+ * int-returning function returns a status code below.
+ */
+#ifndef RGDBEK_H
+#define RGDBEK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define RGDBEK_OK 0                 /* converged / done                          */
+#define RGDBEK_NOT_CONVERGED 1      /* iteration cap reached; x holds x_k        */
+#define RGDBEK_ERR_INVALID_ARG (-1) /* bad size, option or null pointer          */
+#define RGDBEK_ERR_NONFINITE (-2)   /* NaN or Inf met in b, A or a weight        */
+#define RGDBEK_ERR_CUDA (-3)        /* a CUDA runtime call failed                */
+#define RGDBEK_ERR_OOM (-4)         /* device allocation failed                  */
+#define RGDBEK_ERR_TIMEOUT (-5)     /* time budget or a device wait limit hit    */
+#define RGDBEK_ERR_BAD_CSR (-6)     /* row pointers, column order or range wrong */
+
+/* ---- selection rules ----------------------------------------------------- */
+#define RGDBEK_SELECT_RANDOM 0 /* Algorithm 1: draws proportional to the weights */
+#define RGDBEK_SELECT_GREEDY 1 /* GDBEK threshold sets {j: eps_j >= eta max eps} */
+
+/* ---- stopping rules (tested on x_k before each iteration) ---------------- */
+#define RGDBEK_STOP_AUTO 0     /* same as RGDBEK_STOP_NORMAL                      */
+#define RGDBEK_STOP_REL_RES 1  /* ||b - A x|| / ||b|| <= tol (consistent systems) */
+#define RGDBEK_STOP_NORMAL 2   /* ||A^T (b - A x)|| / ||A^T b|| <= tol            */
+#define RGDBEK_STOP_RSE 3      /* ||A x - b||^2 / ||b||^2 <= tol (Section 3.1)    */
+
+typedef struct rgdbek_s *rgdbek_t;
+
+typedef struct {
+    double eta_col;        /* column block fraction eta of Algorithm 1, in (0, 1]  */
+    double eta_row;        /* row block fraction, in (0, 1]                         */
+    int selection;         /* RGDBEK_SELECT_*                                       */
+    double inner_tol;      /* LSQR: stop when ||B^T r|| <= tol ||B||_F ||r|| or
+                              ||r|| <= tol ||c||                                    */
+    int inner_max;         /* LSQR step cap per block (>= 1)                        */
+    int stop_rule;         /* RGDBEK_STOP_*                                         */
+    double time_budget_s;  /* wall-clock cap of one solve on the device, 0 = none   */
+    uint64_t system_id;    /* second word of the Philox key                         */
+    int blocks_per_sm;     /* persistent grid: CTAs per SM, 0 = largest that fits   */
+    int threads_per_block; /* 0 = 512; a multiple of 32 in [64, 1024]               */
+} rgdbek_options;
+
+typedef struct {
+    int64_t iters;      /* outer iterations run                                  */
+    int64_t inner_u;    /* LSQR steps summed over the column steps               */
+    int64_t inner_j;    /* LSQR steps summed over the row steps                  */
+    int64_t sum_nu;     /* sum over iterations of |U_k|                          */
+    int64_t sum_nj;     /* sum over iterations of |J_k|                          */
+    int64_t sum_nnz_u;  /* sum of nnz(A_U) over iterations                       */
+    int64_t sum_nnz_j;  /* sum of nnz(A^J) over iterations                       */
+    int64_t lsqr_nnz_u; /* sum over iterations of (LSQR steps) x nnz(A_U)        */
+    int64_t lsqr_nnz_j; /* sum over iterations of (LSQR steps) x nnz(A^J)        */
+    int64_t lsqr_n_u;   /* sum over iterations of (LSQR steps) x |U_k|           */
+    int64_t lsqr_n_j;   /* sum over iterations of (LSQR steps) x |J_k|           */
+    double rel_res;     /* ||b - A x|| / ||b|| of the returned x                 */
+    double normal_res;  /* ||A^T (b - A x)|| / ||A^T b|| of the returned x       */
+    double rse;         /* rel_res^2, the paper's RSE                            */
+    int status;         /* same as the return code of the solve                  */
+} rgdbek_stats;
+
+typedef struct {
+    int64_t m, n, nnz;
+    int grid;              /* CTAs of the persistent solve kernel                */
+    int threads_per_block;
+    int lanes_per_row;     /* lanes that share one CSR row in the A x products   */
+    int lanes_per_col;     /* lanes that share one CSC column in A^T z products  */
+    int num_sms;
+    int64_t device_bytes;  /* device memory held by the handle                   */
+} rgdbek_info_t;
+
+/* Fills *opt with the defaults: eta_col = eta_row = 0.5 (the paper's
+ * sequential experiments, Section 3.1), random selection, inner_tol = 1e-10,
+ * inner_max = 200, stop_rule = AUTO, no time budget, system_id = 0,
+ * automatic launch shape. */
+void rgdbek_default_options(rgdbek_options *opt);
+
+/* Creates a solver for the m x n matrix A given in CSR form (Eq. 1).
+ *   row_ptr  int64[m + 1], row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz
+ *   col_idx  int32[nnz], strictly increasing within each row, in [0, n)
+ *   vals     double[nnz], finite
+ * ptr_is_device: 0 = the three arrays are host memory, 1 = device memory.
+ * The arrays are copied; the caller keeps ownership.  The handle builds and
+ * owns a CSC copy of A (so A^T products need no atomics), the squared row
+ * and column norms, and all workspace.  opt may be NULL (defaults).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Requires m >= 1, n >= 1, nnz >= 0, m and n below 2^31.
+ * Errors: INVALID_ARG, BAD_CSR (the CSR checks above), NONFINITE, OOM, CUDA.
+ * On error *h is set to NULL and nothing is leaked. */
+int rgdbek_create(rgdbek_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, int ptr_is_device,
+                  const rgdbek_options *opt, void *stream);
+
+/* Releases everything the handle owns (after synchronising its stream). */
+void rgdbek_destroy(rgdbek_t h);
+
+/* Replaces the options (validated as in rgdbek_create). */
+int rgdbek_set_options(rgdbek_t h, const rgdbek_options *opt);
+
+/* Sets the stream used by every later call on the handle. */
+int rgdbek_set_stream(rgdbek_t h, void *stream);
+
+/* Launch shape and sizes of the handle. */
+int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info);
+
+/* Algorithm 1 on the device: x_0 = 0, z_0 = b, iterate until the stopping
+ * rule holds for x_k (tested before each iteration, so b = 0 returns at once),
+ * or max_iter iterations ran, or both blocks of an iteration are empty (x can
+ * no longer change; reported as converged).
+ *   b  device double[m]  (read only)
+ *   x  device double[n]  (output; x_k of the last test)
+ *   seed  first word of the Philox key; (seed, system_id, k) fixes every draw
+ *   st  host, may be NULL
+ * The whole solve is one persistent cooperative kernel: no host round trip
+ * per iteration.  The call returns after the kernel has finished (it
+ * synchronises the handle's stream to read the status).
+ * Returns OK, NOT_CONVERGED, NONFINITE (b or a weight not finite), TIMEOUT,
+ * INVALID_ARG, CUDA. */
+int rgdbek_solve(rgdbek_t h, const double *b, double *x, double tol, int64_t max_iter,
+                 uint64_t seed, rgdbek_stats *st);
+
+/* rgdbek_solve with host buffers: copies b (host double[m]) to the device,
+ * solves, and copies x back into host double[n].  Page-locked host memory
+ * gives the fastest copies. */
+int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double tol,
+                      int64_t max_iter, uint64_t seed, rgdbek_stats *st);
+
+/* Solves nsys independent systems, system i on handle hs[i] with device
+ * buffers b[i] and x[i], tolerance tol[i] and system_id i (seed shared).
+ * st: host array of nsys records, may be NULL.  Returns the worst status
+ * (the most negative error, else NOT_CONVERGED if any system hit the cap). */
+int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
+                         const double *tol, int64_t max_iter, uint64_t seed,
+                         rgdbek_stats *st);
+
+/* Records the blocks of each iteration of the next solves into device
+ * buffers: counts int64[count_cap][4] = (|U_k|, |J_k|, LSQR steps of the
+ * column step, of the row step); lists int32[list_cap] = U_0, J_0, U_1, J_1,
+ * ... concatenated.  Recording stops silently when either buffer is full.
+ * Pass NULLs to turn recording off. */
+int rgdbek_set_trace(rgdbek_t h, int64_t *counts, int64_t count_cap, int32_t *lists,
+                     int64_t list_cap);
+
+/* ---- component entry points (each runs the same device code the solve
+ *      kernel uses; for tests and measurement) ------------------------------ */
+
+/* y = A x: x device double[n], y device double[m]  (CSR product). */
+int rgdbek_spmv(rgdbek_t h, const double *x, double *y);
+
+/* g = A^T z: z device double[m], g device double[n]  (CSC product). */
+int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g);
+
+/* Residual weights of Section 2: which = 0 gives eps_j = v_j^2/||A_j||^2
+ * (v device double[n]), which = 1 gives eps_i = v_i^2/||A^(i)||^2 (v device
+ * double[m]); eps is 0 where the norm is 0.  eps: device output of the same
+ * length; eps_max: host, receives the maximum.  NONFINITE if a weight is NaN
+ * or Inf. */
+int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *eps_max);
+
+/* Block selection of Algorithm 1 on given weights eps (device double[len],
+ * nonnegative, finite; len <= max(m, n)): s draws with probability
+ * eps_j / sum eps, Philox key (seed, sysid), counter (k, phase, t/4, 0);
+ * the sorted distinct drawn indices go to idx (device int32[len]) and their
+ * number to *count (host).  All-zero weights give an empty block.  With
+ * selection = GREEDY in the handle's options the block is instead
+ * {j : eps_j >= eta eps_max} with eta = eta_col (phase 0) or eta_row
+ * (phase 1), and s, seed, sysid, k are ignored. */
+int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_t seed,
+                  uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count);
+
+/* Copies the squared row norms (device double[m]) and squared column norms
+ * (device double[n]) computed at creation; either may be NULL. */
+int rgdbek_get_norms(rgdbek_t h, double *row_norms2, double *col_norms2);
+
+/* Copies the handle's CSC form of A: col_ptr device int64[n + 1], row_idx
+ * device int32[nnz] (increasing within each column), vals device double[nnz]. */
+int rgdbek_get_csc(rgdbek_t h, int64_t *col_ptr, int32_t *row_idx, double *vals);
+
+/* Human-readable name of a status code (static storage). */
+const char *rgdbek_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGDBEK_H */

@@ -1,0 +1,313 @@
+"""GB300 (sm_103a) RGDBEK solver: thin Python binding of the C-ABI library.
+
+RGDBEK (arXiv 2509.19267) solves A x = b, consistent or least squares, with
+randomized column and row blocks drawn from residual-derived probabilities
+(Algorithm 1).  All arithmetic runs in the CUDA kernels of ``librgdbek.so``;
+this module only marshals arguments (torch tensors for device memory and
+streams) to the functions declared in ``include/rgdbek.h``, under the same
+names.  There is no CPU fallback: importing fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librgdbek.so")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_INVALID_ARG = -1
+ERR_NONFINITE = -2
+ERR_CUDA = -3
+ERR_OOM = -4
+ERR_TIMEOUT = -5
+ERR_BAD_CSR = -6
+
+SELECT_RANDOM = 0
+SELECT_GREEDY = 1
+STOP_AUTO = 0
+STOP_REL_RES = 1
+STOP_NORMAL = 2
+STOP_RSE = 3
+
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_ptr = ctypes.c_void_p
+
+
+class rgdbek_options(ctypes.Structure):
+    _fields_ = [
+        ("eta_col", _dbl), ("eta_row", _dbl), ("selection", _int), ("inner_tol", _dbl),
+        ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
+        ("blocks_per_sm", _int), ("threads_per_block", _int),
+    ]
+
+
+class rgdbek_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", _i64), ("inner_u", _i64), ("inner_j", _i64), ("sum_nu", _i64), ("sum_nj", _i64),
+        ("sum_nnz_u", _i64), ("sum_nnz_j", _i64), ("lsqr_nnz_u", _i64), ("lsqr_nnz_j", _i64),
+        ("lsqr_n_u", _i64), ("lsqr_n_j", _i64), ("rel_res", _dbl), ("normal_res", _dbl),
+        ("rse", _dbl), ("status", _int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class rgdbek_info_t(ctypes.Structure):
+    _fields_ = [
+        ("m", _i64), ("n", _i64), ("nnz", _i64), ("grid", _int), ("threads_per_block", _int),
+        ("lanes_per_row", _int), ("lanes_per_col", _int), ("num_sms", _int),
+        ("device_bytes", _i64),
+    ]
+
+
+# (name, restype, argtypes) of every function declared in include/rgdbek.h
+SIGNATURES = [
+    ("rgdbek_default_options", None, [ctypes.POINTER(rgdbek_options)]),
+    ("rgdbek_create", _int, [ctypes.POINTER(_ptr), _i64, _i64, _i64, _ptr, _ptr, _ptr, _int,
+                             ctypes.POINTER(rgdbek_options), _ptr]),
+    ("rgdbek_destroy", None, [_ptr]),
+    ("rgdbek_set_options", _int, [_ptr, ctypes.POINTER(rgdbek_options)]),
+    ("rgdbek_set_stream", _int, [_ptr, _ptr]),
+    ("rgdbek_get_info", _int, [_ptr, ctypes.POINTER(rgdbek_info_t)]),
+    ("rgdbek_solve", _int, [_ptr, _ptr, _ptr, _dbl, _i64, _u64, ctypes.POINTER(rgdbek_stats)]),
+    ("rgdbek_solve_host", _int, [_ptr, _ptr, _ptr, _dbl, _i64, _u64,
+                                 ctypes.POINTER(rgdbek_stats)]),
+    ("rgdbek_solve_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
+                                    ctypes.POINTER(rgdbek_stats)]),
+    ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
+    ("rgdbek_spmv", _int, [_ptr, _ptr, _ptr]),
+    ("rgdbek_spmv_t", _int, [_ptr, _ptr, _ptr]),
+    ("rgdbek_weights", _int, [_ptr, _int, _ptr, _ptr, ctypes.POINTER(_dbl)]),
+    ("rgdbek_sample", _int, [_ptr, _ptr, _i64, _i64, _u64, _u64, _i64, _int, _ptr,
+                             ctypes.POINTER(_i64)]),
+    ("rgdbek_get_norms", _int, [_ptr, _ptr, _ptr]),
+    ("rgdbek_get_csc", _int, [_ptr, _ptr, _ptr, _ptr]),
+    ("rgdbek_status_string", ctypes.c_char_p, [_int]),
+]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with paper_2509_19267_gb300.build.build() "
+            "(nvcc, sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+class RGDBEKError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def status_string(status: int) -> str:
+    return _lib.rgdbek_status_string(status).decode()
+
+
+def _check(status: int, where: str, allow=(OK,)) -> int:
+    if status not in allow:
+        raise RGDBEKError(status, where)
+    return status
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def default_options(**overrides) -> rgdbek_options:
+    o = rgdbek_options()
+    _lib.rgdbek_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Functions named as in the C ABI
+# ---------------------------------------------------------------------------
+def rgdbek_create(m: int, n: int, row_ptr, col_idx, vals, options: rgdbek_options | None = None,
+                  stream=None) -> int:
+    """Create a handle from CSR arrays: torch CUDA tensors (int64, int32,
+    float64) or host numpy arrays of the same dtypes."""
+    h = _ptr()
+    nnz = int(vals.shape[0]) if hasattr(vals, "shape") else len(vals)
+    is_dev = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
+    if is_dev:
+        ptrs = (_dptr(row_ptr), _dptr(col_idx), _dptr(vals))
+    else:
+        import numpy as np
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        ptrs = (row_ptr.ctypes.data, col_idx.ctypes.data if nnz else None,
+                vals.ctypes.data if nnz else None)
+    st = _lib.rgdbek_create(ctypes.byref(h), m, n, nnz, ptrs[0], ptrs[1], ptrs[2], int(is_dev),
+                            ctypes.byref(options) if options is not None else None,
+                            _stream_ptr(stream))
+    _check(st, "rgdbek_create")
+    return h.value
+
+
+def rgdbek_destroy(h: int) -> None:
+    _lib.rgdbek_destroy(h)
+
+
+def rgdbek_set_options(h: int, options: rgdbek_options) -> None:
+    _check(_lib.rgdbek_set_options(h, ctypes.byref(options)), "rgdbek_set_options")
+
+
+def rgdbek_set_stream(h: int, stream=None) -> None:
+    _check(_lib.rgdbek_set_stream(h, _stream_ptr(stream)), "rgdbek_set_stream")
+
+
+def rgdbek_get_info(h: int) -> rgdbek_info_t:
+    info = rgdbek_info_t()
+    _check(_lib.rgdbek_get_info(h, ctypes.byref(info)), "rgdbek_get_info")
+    return info
+
+
+def rgdbek_solve(h: int, b, x, tol: float, max_iter: int, seed: int = 0,
+                 raise_on_error: bool = True) -> rgdbek_stats:
+    st = rgdbek_stats()
+    status = _lib.rgdbek_solve(h, _dptr(b), _dptr(x), tol, max_iter, seed, ctypes.byref(st))
+    st.status = status
+    if raise_on_error:
+        _check(status, "rgdbek_solve", allow=(OK, NOT_CONVERGED))
+    return st
+
+
+def rgdbek_solve_host(h: int, b, x, tol: float, max_iter: int, seed: int = 0,
+                      raise_on_error: bool = True) -> rgdbek_stats:
+    """b, x: contiguous float64 host buffers (numpy arrays or pinned CPU tensors)."""
+    def hptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    st = rgdbek_stats()
+    status = _lib.rgdbek_solve_host(h, hptr(b), hptr(x), tol, max_iter, seed, ctypes.byref(st))
+    st.status = status
+    if raise_on_error:
+        _check(status, "rgdbek_solve_host", allow=(OK, NOT_CONVERGED))
+    return st
+
+
+def rgdbek_solve_batched(hs, bs, xs, tols, max_iter: int, seed: int = 0):
+    n = len(hs)
+    H = (_ptr * n)(*hs)
+    B = (_ptr * n)(*[_dptr(b) for b in bs])
+    X = (_ptr * n)(*[_dptr(x) for x in xs])
+    T = (_dbl * n)(*tols)
+    S = (rgdbek_stats * n)()
+    status = _lib.rgdbek_solve_batched(n, H, B, X, T, max_iter, seed, S)
+    return status, list(S)
+
+
+def rgdbek_set_trace(h: int, counts=None, lists=None) -> None:
+    """counts: int64 CUDA tensor of shape (cap, 4); lists: int32 CUDA tensor."""
+    if counts is not None and (counts.dim() != 2 or counts.shape[1] != 4):
+        raise ValueError("counts must have shape (cap, 4)")
+    _check(_lib.rgdbek_set_trace(h, _dptr(counts), counts.shape[0] if counts is not None else 0,
+                                 _dptr(lists), lists.shape[0] if lists is not None else 0),
+           "rgdbek_set_trace")
+
+
+def rgdbek_spmv(h: int, x, y) -> None:
+    _check(_lib.rgdbek_spmv(h, _dptr(x), _dptr(y)), "rgdbek_spmv")
+
+
+def rgdbek_spmv_t(h: int, z, g) -> None:
+    _check(_lib.rgdbek_spmv_t(h, _dptr(z), _dptr(g)), "rgdbek_spmv_t")
+
+
+def rgdbek_weights(h: int, which: int, v, eps) -> float:
+    emax = _dbl(0.0)
+    _check(_lib.rgdbek_weights(h, which, _dptr(v), _dptr(eps), ctypes.byref(emax)),
+           "rgdbek_weights")
+    return emax.value
+
+
+def rgdbek_sample(h: int, eps, s: int, seed: int, sysid: int, k: int, phase: int, idx) -> int:
+    cnt = _i64(0)
+    _check(_lib.rgdbek_sample(h, _dptr(eps), eps.shape[0], s, seed, sysid, k, phase, _dptr(idx),
+                              ctypes.byref(cnt)), "rgdbek_sample")
+    return cnt.value
+
+
+def rgdbek_get_norms(h: int, row_norms2=None, col_norms2=None) -> None:
+    _check(_lib.rgdbek_get_norms(h, _dptr(row_norms2), _dptr(col_norms2)), "rgdbek_get_norms")
+
+
+def rgdbek_get_csc(h: int, col_ptr, row_idx, vals) -> None:
+    _check(_lib.rgdbek_get_csc(h, _dptr(col_ptr), _dptr(row_idx), _dptr(vals)), "rgdbek_get_csc")
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper owning a handle
+# ---------------------------------------------------------------------------
+@dataclass
+class SolveResult:
+    x: object
+    stats: rgdbek_stats
+
+
+class Solver:
+    """Owns one handle for an m x n CSR matrix on the current CUDA device."""
+
+    def __init__(self, m: int, n: int, row_ptr, col_idx, vals, stream=None, **options):
+        self.m, self.n = m, n
+        self.options = default_options(**options)
+        self.handle = rgdbek_create(m, n, row_ptr, col_idx, vals, self.options, stream)
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            setattr(self.options, k, v)
+        rgdbek_set_options(self.handle, self.options)
+
+    def info(self) -> rgdbek_info_t:
+        return rgdbek_get_info(self.handle)
+
+    def solve(self, b, tol: float = 1e-8, max_iter: int = 10000, seed: int = 0, x=None,
+              raise_on_error: bool = True) -> SolveResult:
+        import torch
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        st = rgdbek_solve(self.handle, b, x, tol, max_iter, seed, raise_on_error)
+        return SolveResult(x, st)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rgdbek_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,552 @@
+// Host side of the C ABI declared in include/rgdbek.h: handle life cycle,
+// option checks, device memory layout, and the launches of the persistent
+// solve kernel and of the component kernels.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "rgdbek_internal.h"
+
+using namespace rgd;
+
+struct rgdbek_s {
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    rgdbek_options opt{};
+    long long m = 0, n = 0, nnz = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    Ctrl *ctrl_host = nullptr;  // page-locked copy of the control block
+    // A
+    long long *rp = nullptr, *cp = nullptr;
+    int *ci = nullptr, *ri = nullptr;
+    double *av = nullptr, *cv = nullptr, *rn2 = nullptr, *cn2 = nullptr;
+    // work
+    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx;
+    unsigned long long *Q;
+    unsigned char *flag;
+    int *colpos, *rowpos, *ulist, *jlist;
+    long long *srp, *scp;
+    int *sci, *sri;
+    double *sav, *scv;
+    double *pd;
+    long long *pi;
+    Ctrl *ctrl;
+    double *b_stage, *x_stage;
+    // launch shape
+    int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1;
+    // trace
+    long long *tr_counts = nullptr;
+    long long tr_count_cap = 0;
+    int *tr_lists = nullptr;
+    long long tr_list_cap = 0;
+};
+
+namespace {
+
+// Bump allocator over one device allocation; every sub-buffer 256-byte aligned.
+struct Layout {
+    size_t off = 0;
+    char *base = nullptr;
+    template <typename T>
+    T *take(long long count) {
+        const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    }
+};
+
+void carve(rgdbek_s *h, Layout &L) {
+    const long long m = h->m, n = h->n, nnz = h->nnz, mx = m > n ? m : n;
+    h->rp = L.take<long long>(m + 1);
+    h->ci = L.take<int>(nnz);
+    h->av = L.take<double>(nnz);
+    h->cp = L.take<long long>(n + 1);
+    h->ri = L.take<int>(nnz);
+    h->cv = L.take<double>(nnz);
+    h->rn2 = L.take<double>(m);
+    h->cn2 = L.take<double>(n);
+    h->z = L.take<double>(m);
+    h->t = L.take<double>(m);
+    h->r = L.take<double>(m);
+    h->epsr = L.take<double>(m);
+    h->uu = L.take<double>(m);
+    h->g = L.take<double>(n);
+    h->epsc = L.take<double>(n);
+    h->vv = L.take<double>(n);
+    h->ww = L.take<double>(n);
+    h->yy = L.take<double>(n);
+    h->dx = L.take<double>(n);
+    h->Q = L.take<unsigned long long>(mx);
+    h->flag = L.take<unsigned char>(mx);
+    h->colpos = L.take<int>(n);
+    h->rowpos = L.take<int>(mx);
+    h->ulist = L.take<int>(n);
+    h->jlist = L.take<int>(m);
+    h->srp = L.take<long long>(m + 1);
+    h->sci = L.take<int>(nnz);
+    h->sav = L.take<double>(nnz);
+    h->scp = L.take<long long>(n + 1);
+    h->sri = L.take<int>(nnz);
+    h->scv = L.take<double>(nnz);
+    h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
+    h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
+    h->ctrl = L.take<Ctrl>(1);
+    h->b_stage = L.take<double>(m);
+    h->x_stage = L.take<double>(n);
+}
+
+int check_options(const rgdbek_options &o) {
+    if (!(o.eta_col > 0.0 && o.eta_col <= 1.0) || !(o.eta_row > 0.0 && o.eta_row <= 1.0))
+        return RGDBEK_ERR_INVALID_ARG;
+    if (o.selection != RGDBEK_SELECT_RANDOM && o.selection != RGDBEK_SELECT_GREEDY)
+        return RGDBEK_ERR_INVALID_ARG;
+    if (!(o.inner_tol >= 0.0) || o.inner_max < 1) return RGDBEK_ERR_INVALID_ARG;
+    if (o.stop_rule < 0 || o.stop_rule > 3) return RGDBEK_ERR_INVALID_ARG;
+    if (!(o.time_budget_s >= 0.0)) return RGDBEK_ERR_INVALID_ARG;
+    if (o.blocks_per_sm < 0 || o.threads_per_block < 0) return RGDBEK_ERR_INVALID_ARG;
+    if (o.threads_per_block != 0 &&
+        (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
+         o.threads_per_block > kSolveMaxThreads))
+        return RGDBEK_ERR_INVALID_ARG;
+    return RGDBEK_OK;
+}
+
+// launch shape of the persistent kernels for the handle's options
+int configure_launch(rgdbek_s *h) {
+    const int block = h->opt.threads_per_block ? h->opt.threads_per_block : kSolveMaxThreads;
+    int fit = solve_blocks_per_sm(block);
+    int fit_s = sample_blocks_per_sm(block);
+    if (fit < 1 || fit_s < 1) return RGDBEK_ERR_CUDA;
+    int bps = h->opt.blocks_per_sm ? h->opt.blocks_per_sm : fit;
+    if (bps > fit) bps = fit;
+    long long grid = (long long)bps * h->num_sms;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    long long sgrid = (long long)(fit_s < bps ? fit_s : bps) * h->num_sms;
+    if (sgrid > kMaxGrid) sgrid = kMaxGrid;
+    h->block = block;
+    h->grid = (int)grid;
+    h->sample_grid = (int)sgrid;
+    return RGDBEK_OK;
+}
+
+Params make_params(const rgdbek_s *h) {
+    Params P{};
+    P.m = h->m;
+    P.n = h->n;
+    P.nnz = h->nnz;
+    P.rp = h->rp;
+    P.ci = h->ci;
+    P.av = h->av;
+    P.cp = h->cp;
+    P.ri = h->ri;
+    P.cv = h->cv;
+    P.rn2 = h->rn2;
+    P.cn2 = h->cn2;
+    P.z = h->z;
+    P.t = h->t;
+    P.r = h->r;
+    P.g = h->g;
+    P.epsc = h->epsc;
+    P.epsr = h->epsr;
+    P.uu = h->uu;
+    P.vv = h->vv;
+    P.ww = h->ww;
+    P.yy = h->yy;
+    P.dx = h->dx;
+    P.Q = h->Q;
+    P.flag = h->flag;
+    P.colpos = h->colpos;
+    P.rowpos = h->rowpos;
+    P.ulist = h->ulist;
+    P.jlist = h->jlist;
+    P.srp = h->srp;
+    P.sci = h->sci;
+    P.sav = h->sav;
+    P.scp = h->scp;
+    P.sri = h->sri;
+    P.scv = h->scv;
+    P.pd = h->pd;
+    P.pi = h->pi;
+    P.ctrl = h->ctrl;
+    P.tr_counts = h->tr_counts;
+    P.tr_count_cap = h->tr_count_cap;
+    P.tr_lists = h->tr_lists;
+    P.tr_list_cap = h->tr_list_cap;
+    P.eta_col = h->opt.eta_col;
+    P.eta_row = h->opt.eta_row;
+    P.inner_tol = h->opt.inner_tol;
+    P.inner_max = h->opt.inner_max;
+    P.stop_rule = h->opt.stop_rule;
+    P.selection = h->opt.selection;
+    P.sysid = h->opt.system_id;
+    P.time_budget_ns = h->opt.time_budget_s * 1e9;
+    P.tpr = h->tpr;
+    P.tpc = h->tpc;
+    return P;
+}
+
+// ceil(eta * len) draws, at least one (Algorithm 1 selects eta*n columns)
+long long num_draws(double eta, long long len) {
+    if (len <= 0) return 0;
+    double s = std::ceil(eta * (double)len);
+    if (s < 1.0) s = 1.0;
+    return (long long)s;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RGDBEK_OK;
+    if (e == cudaErrorMemoryAllocation) return RGDBEK_ERR_OOM;
+    return RGDBEK_ERR_CUDA;
+}
+
+// Copies the control block back and waits for the stream.
+int read_ctrl(rgdbek_s *h) {
+    cudaError_t e = cudaMemcpyAsync(h->ctrl_host, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+void release(rgdbek_s *h) {
+    if (!h) return;
+    if (h->arena) cudaFree(h->arena);
+    if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rgdbek_default_options(rgdbek_options *opt) {
+    if (!opt) return;
+    opt->eta_col = 0.5;
+    opt->eta_row = 0.5;
+    opt->selection = RGDBEK_SELECT_RANDOM;
+    opt->inner_tol = 1e-10;
+    opt->inner_max = 200;
+    opt->stop_rule = RGDBEK_STOP_AUTO;
+    opt->time_budget_s = 0.0;
+    opt->system_id = 0;
+    opt->blocks_per_sm = 0;
+    opt->threads_per_block = 0;
+}
+
+int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, int ptr_is_device,
+                  const rgdbek_options *opt, void *stream) {
+    if (!out) return RGDBEK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || nnz < 0 || m >= (1ll << 31) || n >= (1ll << 31) || nnz >= (1ll << 50))
+        return RGDBEK_ERR_INVALID_ARG;
+    if (!row_ptr || (nnz > 0 && (!col_idx || !vals))) return RGDBEK_ERR_INVALID_ARG;
+    rgdbek_options o;
+    rgdbek_default_options(&o);
+    if (opt) o = *opt;
+    int st = check_options(o);
+    if (st != RGDBEK_OK) return st;
+
+    rgdbek_s *h = new (std::nothrow) rgdbek_s();
+    if (!h) return RGDBEK_ERR_OOM;
+    h->m = m;
+    h->n = n;
+    h->nnz = nnz;
+    h->opt = o;
+    h->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    int coop = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (e != cudaSuccess || !coop) {
+        release(h);
+        return RGDBEK_ERR_CUDA;
+    }
+    if ((st = configure_launch(h)) != RGDBEK_OK) {
+        release(h);
+        return st;
+    }
+    h->tpr = pick_lanes((double)nnz / (double)m);
+    h->tpc = pick_lanes((double)nnz / (double)n);
+
+    Layout L;
+    carve(h, L);
+    h->arena_bytes = L.off;
+    if ((e = cudaMalloc(&h->arena, h->arena_bytes)) != cudaSuccess ||
+        (e = cudaMallocHost(&h->ctrl_host, sizeof(Ctrl))) != cudaSuccess) {
+        release(h);
+        return cuda_status(e);
+    }
+    L = Layout();
+    L.base = static_cast<char *>(h->arena);
+    carve(h, L);
+
+    // set-up scratch, freed before returning
+    const long long keys = nnz > n ? nnz : n;
+    Layout S;
+    long long *key_a = S.take<long long>(keys);
+    long long *key_b = S.take<long long>(keys);
+    int *row_of = S.take<int>(nnz);
+    long long *cursor = S.take<long long>(n);
+    long long *blk = S.take<long long>(n / 1024 + 2);
+    int *err = S.take<int>(1);
+    (void)key_a; (void)key_b; (void)row_of; (void)cursor; (void)blk; (void)err;
+    void *scratch = nullptr;
+    if ((e = cudaMalloc(&scratch, S.off)) != cudaSuccess) {
+        release(h);
+        return cuda_status(e);
+    }
+    S = Layout();
+    S.base = static_cast<char *>(scratch);
+    key_a = S.take<long long>(keys);
+    key_b = S.take<long long>(keys);
+    row_of = S.take<int>(nnz);
+    cursor = S.take<long long>(n);
+    blk = S.take<long long>(n / 1024 + 2);
+    err = S.take<int>(1);
+
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t s = h->stream;
+    int verdict = RGDBEK_OK;
+    do {
+        if ((e = cudaMemcpyAsync(h->rp, row_ptr, (size_t)(m + 1) * sizeof(long long), kind, s)) !=
+            cudaSuccess)
+            break;
+        if (nnz > 0) {
+            if ((e = cudaMemcpyAsync(h->ci, col_idx, (size_t)nnz * sizeof(int), kind, s)) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaMemcpyAsync(h->av, vals, (size_t)nnz * sizeof(double), kind, s)) !=
+                cudaSuccess)
+                break;
+        }
+        if ((e = validate_csr(m, n, nnz, h->rp, h->ci, h->av, err, &verdict, s)) != cudaSuccess)
+            break;
+        if (verdict != RGDBEK_OK) break;
+        if ((e = build_csc(m, n, nnz, h->rp, h->ci, h->av, h->cp, h->ri, h->cv, key_a, key_b,
+                           row_of, cursor, blk, s)) != cudaSuccess)
+            break;
+        if ((e = line_norms2(m, h->rp, h->av, h->rn2, s)) != cudaSuccess) break;
+        if ((e = line_norms2(n, h->cp, h->cv, h->cn2, s)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);
+    } while (0);
+    cudaFree(scratch);
+    if (e != cudaSuccess) verdict = cuda_status(e);
+    if (verdict != RGDBEK_OK) {
+        release(h);
+        return verdict;
+    }
+    *out = h;
+    return RGDBEK_OK;
+}
+
+void rgdbek_destroy(rgdbek_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+}
+
+int rgdbek_set_options(rgdbek_t h, const rgdbek_options *opt) {
+    if (!h || !opt) return RGDBEK_ERR_INVALID_ARG;
+    const int st = check_options(*opt);
+    if (st != RGDBEK_OK) return st;
+    const rgdbek_options old = h->opt;
+    h->opt = *opt;
+    const int cs = configure_launch(h);
+    if (cs != RGDBEK_OK) {
+        h->opt = old;
+        configure_launch(h);
+    }
+    return cs;
+}
+
+int rgdbek_set_stream(rgdbek_t h, void *stream) {
+    if (!h) return RGDBEK_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)stream;
+    return RGDBEK_OK;
+}
+
+int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
+    if (!h || !info) return RGDBEK_ERR_INVALID_ARG;
+    info->m = h->m;
+    info->n = h->n;
+    info->nnz = h->nnz;
+    info->grid = h->grid;
+    info->threads_per_block = h->block;
+    info->lanes_per_row = h->tpr;
+    info->lanes_per_col = h->tpc;
+    info->num_sms = h->num_sms;
+    info->device_bytes = (int64_t)h->arena_bytes;
+    return RGDBEK_OK;
+}
+
+int rgdbek_set_trace(rgdbek_t h, int64_t *counts, int64_t count_cap, int32_t *lists,
+                     int64_t list_cap) {
+    if (!h || count_cap < 0 || list_cap < 0) return RGDBEK_ERR_INVALID_ARG;
+    h->tr_counts = counts ? (long long *)counts : nullptr;
+    h->tr_count_cap = counts ? count_cap : 0;
+    h->tr_lists = lists;
+    h->tr_list_cap = lists ? list_cap : 0;
+    return RGDBEK_OK;
+}
+
+int rgdbek_solve(rgdbek_t h, const double *b, double *x, double tol, int64_t max_iter,
+                 uint64_t seed, rgdbek_stats *st) {
+    if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return RGDBEK_ERR_INVALID_ARG;
+    Params P = make_params(h);
+    P.b = b;
+    P.x = x;
+    P.tol = tol;
+    P.max_iter = max_iter;
+    P.seed = seed;
+    P.s_col = num_draws(h->opt.eta_col, h->n);
+    P.s_row = num_draws(h->opt.eta_row, h->m);
+    cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
+    if (e == cudaSuccess) e = launch_solve(P, h->grid, h->block, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rs = read_ctrl(h);
+    if (rs != RGDBEK_OK) return rs;
+    const Ctrl &c = *h->ctrl_host;
+    int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
+    if (st) {
+        st->iters = c.iters;
+        st->inner_u = c.inner_u;
+        st->inner_j = c.inner_j;
+        st->sum_nu = c.sum_nu;
+        st->sum_nj = c.sum_nj;
+        st->sum_nnz_u = c.sum_nnzu;
+        st->sum_nnz_j = c.sum_nnzj;
+        st->lsqr_nnz_u = c.lsqr_nnzu;
+        st->lsqr_nnz_j = c.lsqr_nnzj;
+        st->lsqr_n_u = c.lsqr_nu;
+        st->lsqr_n_j = c.lsqr_nj;
+        st->rel_res = c.rel_res;
+        st->normal_res = c.normal_res;
+        st->rse = c.rse;
+        st->status = status;
+    }
+    return status;
+}
+
+int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double tol,
+                      int64_t max_iter, uint64_t seed, rgdbek_stats *st) {
+    if (!h || !b_host || !x_host) return RGDBEK_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(h->b_stage, b_host, (size_t)h->m * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int status = rgdbek_solve(h, h->b_stage, h->x_stage, tol, max_iter, seed, st);
+    if (status < 0 && status != RGDBEK_ERR_NONFINITE && status != RGDBEK_ERR_TIMEOUT) return status;
+    e = cudaMemcpyAsync(x_host, h->x_stage, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? status : cuda_status(e);
+}
+
+int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
+                         const double *tol, int64_t max_iter, uint64_t seed, rgdbek_stats *st) {
+    if (nsys < 0 || (nsys > 0 && (!hs || !b || !x || !tol))) return RGDBEK_ERR_INVALID_ARG;
+    int worst = RGDBEK_OK;
+    for (int i = 0; i < nsys; ++i) {
+        if (!hs[i]) return RGDBEK_ERR_INVALID_ARG;
+        const uint64_t saved = hs[i]->opt.system_id;
+        hs[i]->opt.system_id = (uint64_t)i;
+        const int s = rgdbek_solve(hs[i], b[i], x[i], tol[i], max_iter, seed, st ? st + i : nullptr);
+        hs[i]->opt.system_id = saved;
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        else if (s == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = s;
+    }
+    return worst;
+}
+
+int rgdbek_spmv(rgdbek_t h, const double *x, double *y) {
+    if (!h || !x || !y) return RGDBEK_ERR_INVALID_ARG;
+    return cuda_status(launch_spmv(make_params(h), h->grid, h->block, x, y, h->stream));
+}
+
+int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g) {
+    if (!h || !z || !g) return RGDBEK_ERR_INVALID_ARG;
+    return cuda_status(launch_spmv_t(make_params(h), h->grid, h->block, z, g, h->stream));
+}
+
+int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *eps_max) {
+    if (!h || !v || !eps || !eps_max || (which != 0 && which != 1)) return RGDBEK_ERR_INVALID_ARG;
+    const long long len = which == 0 ? h->n : h->m;
+    cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
+    if (e == cudaSuccess)
+        e = launch_weights(v, which == 0 ? h->cn2 : h->rn2, len, eps, h->ctrl, h->grid, h->block,
+                           h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rs = read_ctrl(h);
+    if (rs != RGDBEK_OK) return rs;
+    *eps_max = h->ctrl_host->emax_out;
+    return h->ctrl_host->bad_out ? RGDBEK_ERR_NONFINITE : RGDBEK_OK;
+}
+
+int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_t seed,
+                  uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count) {
+    const long long mx = h ? (h->m > h->n ? h->m : h->n) : 0;
+    if (!h || !eps || !idx || !count || len < 1 || len > mx || s < 0 || k < 0 ||
+        (phase != 0 && phase != 1))
+        return RGDBEK_ERR_INVALID_ARG;
+    const bool greedy = h->opt.selection == RGDBEK_SELECT_GREEDY;
+    const double eta = phase == 0 ? h->opt.eta_col : h->opt.eta_row;
+    cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
+    if (e == cudaSuccess)
+        e = launch_sample(make_params(h), h->sample_grid, h->block, eps, len, s, seed, sysid,
+                          (unsigned long long)k, (unsigned long long)phase, idx, greedy, eta,
+                          h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rs = read_ctrl(h);
+    if (rs != RGDBEK_OK) return rs;
+    if (h->ctrl_host->status != RGDBEK_OK) return RGDBEK_ERR_TIMEOUT;
+    if (h->ctrl_host->sample_count < 0) return RGDBEK_ERR_NONFINITE;
+    *count = h->ctrl_host->sample_count;
+    return RGDBEK_OK;
+}
+
+int rgdbek_get_norms(rgdbek_t h, double *row_norms2, double *col_norms2) {
+    if (!h) return RGDBEK_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (row_norms2)
+        e = cudaMemcpyAsync(row_norms2, h->rn2, (size_t)h->m * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && col_norms2)
+        e = cudaMemcpyAsync(col_norms2, h->cn2, (size_t)h->n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+int rgdbek_get_csc(rgdbek_t h, int64_t *col_ptr, int32_t *row_idx, double *vals) {
+    if (!h || !col_ptr || (h->nnz > 0 && (!row_idx || !vals))) return RGDBEK_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(col_ptr, h->cp, (size_t)(h->n + 1) * sizeof(long long),
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->nnz > 0)
+        e = cudaMemcpyAsync(row_idx, h->ri, (size_t)h->nnz * sizeof(int), cudaMemcpyDeviceToDevice,
+                            h->stream);
+    if (e == cudaSuccess && h->nnz > 0)
+        e = cudaMemcpyAsync(vals, h->cv, (size_t)h->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+const char *rgdbek_status_string(int status) {
+    switch (status) {
+    case RGDBEK_OK: return "ok";
+    case RGDBEK_NOT_CONVERGED: return "not converged (iteration cap reached)";
+    case RGDBEK_ERR_INVALID_ARG: return "invalid argument";
+    case RGDBEK_ERR_NONFINITE: return "non-finite value in the input or a residual weight";
+    case RGDBEK_ERR_CUDA: return "CUDA runtime error";
+    case RGDBEK_ERR_OOM: return "out of device memory";
+    case RGDBEK_ERR_TIMEOUT: return "time budget or device wait limit exceeded";
+    case RGDBEK_ERR_BAD_CSR: return "malformed CSR matrix";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Internal interface between the host side of the library (rgdbek_api.cu)
+// and the kernel translation units (rgdbek_kernels.cu, rgdbek_setup.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rgdbek_phases.cuh"
+
+namespace rgd {
+
+constexpr int kSolveMaxThreads = 512;   // launch bound of the persistent kernels
+
+// control block to its pre-launch state (status = kStatusRunning)
+cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
+// persistent solve (cooperative launch); returns the launch error
+cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s);
+// standalone sampler on given weights (cooperative launch)
+cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
+                          long long s, unsigned long long seed, unsigned long long sysid,
+                          unsigned long long k, unsigned long long phase, int *idx, bool greedy,
+                          double eta, cudaStream_t st);
+cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, double *y,
+                        cudaStream_t s);
+cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
+                          cudaStream_t s);
+cudaError_t launch_weights(const double *v, const double *norm2, long long len, double *eps,
+                           Ctrl *ctrl, int grid, int block, cudaStream_t s);
+// CTAs of `block` threads of the persistent kernels that fit on one SM
+int solve_blocks_per_sm(int block);
+int sample_blocks_per_sm(int block);
+
+// ---- set-up (rgdbek_setup.cu) ----------------------------------------------
+// Checks the CSR arrays on the device; *err_host receives 0 or a status code.
+cudaError_t validate_csr(long long m, long long n, long long nnz, const long long *rp,
+                         const int *ci, const double *av, int *err_dev, int *err_host,
+                         cudaStream_t s);
+// Builds the CSC form (col_ptr n+1, row_idx, vals; rows ascending within a
+// column) from a valid CSR.  tmp_* are scratch of the stated sizes.
+cudaError_t build_csc(long long m, long long n, long long nnz, const long long *rp, const int *ci,
+                      const double *av, long long *cp, int *ri, double *cv, long long *key_a,
+                      long long *key_b, int *row_of, long long *cursor, long long *blk_sums,
+                      cudaStream_t s);
+// Squared norms of the lines of a compressed matrix (CSR rows or CSC columns).
+cudaError_t line_norms2(long long nlines, const long long *ptr, const double *val, double *out,
+                        cudaStream_t s);
+
+}  // namespace rgd

@@ -1,0 +1,488 @@
+// The persistent RGDBEK solve kernel (one cooperative launch per solve) and
+// the component kernels that reuse its phases.
+//
+// One outer iteration k of Algorithm 1, phase by phase (| = grid barrier):
+//   col:  x_k = x_{k-1} + dx; g = A^T z_k; h = A^T (b - A x_k); eps^z  |
+//         stopping test on x_k (every CTA decides identically)
+//   column block (skipped if eps^z == 0):
+//         quantise eps^z | Philox draws | count marks | compact -> U_k |
+//         count nnz of A_U | extract A_U as CSR, start LSQR (v~ = g_U/||z||) |
+//         LSQR steps on A_U (2 phases each) ...
+//   z:    z_{k+1} = z_k - A_U y; r = (b - A x_k) - z_{k+1}; eps^x             |
+//   row block (skipped if eps^x == 0):
+//         quantise | draws | count | compact -> J_k | count nnz(A^J) |
+//         extract A^J as CSC, u~ = r_J | v~ = (A^J)^T u~ / ||r_J|| |
+//         LSQR steps on A^J; the solution accumulates in dx ...
+//   t:    t_{k+1} = b - A (x_k + dx)                                          |
+// The stopping test of x_{k+1} is taken in the next col phase, which also
+// applies x_{k+1} = x_k + dx, so the returned x is exactly the tested one.
+#include <cmath>
+
+#include "rgdbek_internal.h"
+
+namespace rgd {
+
+struct SolveSmem {
+    BlockScratch bs;
+    long long tab[kMaxGrid];
+};
+
+struct Acc {
+    long long inner_u = 0, inner_j = 0, sum_nu = 0, sum_nj = 0, sum_nnzu = 0, sum_nnzj = 0;
+    long long lsqr_nnzu = 0, lsqr_nnzj = 0, lsqr_nu = 0, lsqr_nj = 0;
+};
+
+__device__ __forceinline__ void finish(const Params &P, int status, long long k, double rel,
+                                       double nrm, const Acc &a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *C = P.ctrl;
+        C->iters = k;
+        C->inner_u = a.inner_u;
+        C->inner_j = a.inner_j;
+        C->sum_nu = a.sum_nu;
+        C->sum_nj = a.sum_nj;
+        C->sum_nnzu = a.sum_nnzu;
+        C->sum_nnzj = a.sum_nnzj;
+        C->lsqr_nnzu = a.lsqr_nnzu;
+        C->lsqr_nnzj = a.lsqr_nnzj;
+        C->lsqr_nu = a.lsqr_nu;
+        C->lsqr_nj = a.lsqr_nj;
+        C->rel_res = rel;
+        C->normal_res = nrm;
+        C->rse = rel * rel;
+        __threadfence();
+        atomicCAS(&C->status, kStatusRunning, status);
+    }
+}
+
+// LSQR on the block given by its row side R (u-space lines) and column side
+// Cs (v-space lines), from y = 0.  c0 = u~_1 (the right-hand side c), beta =
+// ||c||, alpha = ||B^T c|| / beta, with v~_1 already in P.vv.  The solution
+// accumulates into y (zero on entry).  Returns the number of steps, or -1 if
+// a grid barrier was abandoned.
+__device__ __forceinline__ int run_lsqr(const Params &P, const Side &R, const Side &Cs,
+                                        const double *c0, double *y, double alpha, double beta,
+                                        double fro, SolveSmem &S) {
+    const int nct = gridDim.x;
+    double rhobar = alpha, phibar = beta, wcoef = 0.0;
+    const double beta1 = beta;
+    for (int it = 1;; ++it) {
+        lsqr_rows(P, R, Cs.n, it == 1 ? c0 : P.uu, P.uu, P.vv, P.ww, alpha, beta, it == 1, wcoef,
+                  S.bs);
+        if (!grid_barrier(P.ctrl)) return -1;
+        const double bn = sqrt(reduce_partials_sum(P.pd + D_UU * nct, nct, S.bs));
+        const double rho = sqrt(rhobar * rhobar + bn * bn);
+        const double cs = rhobar / rho, sn = bn / rho;
+        const double phi = cs * phibar;
+        phibar = sn * phibar;
+        lsqr_cols(P, Cs, P.uu, P.vv, P.ww, y, alpha, bn, phi / rho, false, S.bs);
+        if (!grid_barrier(P.ctrl)) return -1;
+        const double an = bn > 0.0 ? sqrt(reduce_partials_sum(P.pd + D_VV * nct, nct, S.bs)) : 0.0;
+        const double theta = sn * an;
+        rhobar = -cs * an;
+        wcoef = theta / rho;
+        const double rnorm = phibar;
+        const double arnorm = phibar * an * fabs(cs);
+        alpha = an;
+        beta = bn;
+        if (arnorm <= P.inner_tol * fro * rnorm || rnorm <= P.inner_tol * beta1 || an == 0.0 ||
+            bn == 0.0 || it >= P.inner_max)
+            return it;
+    }
+}
+
+// z_{k+1} = z_k - A_U y (A_U as extracted CSR), r = t_k - z_{k+1},
+// eps^x_i = r_i^2 / ||A^(i)||^2.  Partials: max eps^x, ||z_{k+1}||^2, bad.
+__device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Lsub,
+                                              BlockScratch &bs) {
+    const Grp G(hasU ? Lsub : 1);
+    double emax = 0.0, zz = 0.0;
+    long long bad = 0;
+    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+        const long long i = base + G.sub;
+        double s = 0.0;
+        if (hasU && i < P.m) {
+            const long long e1 = P.srp[i + 1];
+            for (long long e = P.srp[i] + G.sl; e < e1; e += G.L) s = fma(P.sav[e], P.yy[P.sci[e]], s);
+        }
+        s = group_sum(s, G.L);
+        if (i < P.m && G.sl == 0) {
+            const double zi = P.z[i] - s;
+            P.z[i] = zi;
+            const double ri = P.t[i] - zi;
+            P.r[i] = ri;
+            const double c = __ldg(P.rn2 + i);
+            const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(ri, ri), c) : 0.0;
+            P.epsr[i] = e;
+            if (!isfinite(e)) bad = 1;
+            else emax = fmax(emax, e);
+            zz = fma(zi, zi, zz);
+        }
+    }
+    emax = block_max(emax, bs);
+    zz = block_sum(zz, bs);
+    bad = block_sum(bad, bs);
+    if (threadIdx.x == 0) {
+        P.pd[D_EMAX_R * gridDim.x + blockIdx.x] = emax;
+        P.pd[D_ZZ * gridDim.x + blockIdx.x] = zz;
+        P.pi[I_BAD_R * gridDim.x + blockIdx.x] = bad;
+    }
+}
+
+#define RGD_SYNC()                                 \
+    do {                                           \
+        if (!grid_barrier(P.ctrl)) return;         \
+    } while (0)
+
+__global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
+    __shared__ SolveSmem S;
+    BlockScratch &bs = S.bs;
+    const int nct = gridDim.x;
+    const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
+    const unsigned long long t_start = globaltimer_ns();
+
+    // ---- x_0 = 0, z_0 = b, t_0 = b - A x_0 = b, dx = 0
+    {
+        double bb = 0.0;
+        long long bad = 0;
+        for (long long i = gthread(); i < P.m; i += nthreads()) {
+            const double bi = __ldg(P.b + i);
+            P.z[i] = bi;
+            P.t[i] = bi;
+            bb = fma(bi, bi, bb);
+            if (!isfinite(bi)) bad = 1;
+        }
+        for (long long j = gthread(); j < P.n; j += nthreads()) {
+            P.x[j] = 0.0;
+            P.dx[j] = 0.0;
+        }
+        bb = block_sum(bb, bs);
+        bad = block_sum(bad, bs);
+        if (threadIdx.x == 0) {
+            P.pd[D_BB * nct + blockIdx.x] = bb;
+            P.pi[I_BAD_R * nct + blockIdx.x] = bad;
+        }
+    }
+    RGD_SYNC();
+    const double bb = reduce_partials_sum(P.pd + D_BB * nct, nct, bs);
+    const long long badb = reduce_partials_isum(P.pi + I_BAD_R * nct, nct, bs);
+    Acc acc;
+    if (badb != 0 || !isfinite(bb)) {
+        finish(P, RGDBEK_ERR_NONFINITE, 0, NAN, NAN, acc);
+        return;
+    }
+    double tt = bb, zz = bb, atb2 = 0.0;
+    long long tr_off = 0;
+    bool tr_full = P.tr_lists == nullptr;
+
+    for (long long k = 0;; ++k) {
+        // ---- column pass and stopping test on x_k
+        if (blockIdx.x == 0 && threadIdx.x == 0 && P.time_budget_ns > 0.0 &&
+            (double)(globaltimer_ns() - t_start) > P.time_budget_ns)
+            P.ctrl->stop_req = 1;
+        phase_col(P, bs);
+        RGD_SYNC();
+        const double emax_c = reduce_partials_max(P.pd + D_EMAX_C * nct, nct, bs);
+        const double hh = reduce_partials_sum(P.pd + D_HH * nct, nct, bs);
+        const long long badc = reduce_partials_isum(P.pi + I_BAD_C * nct, nct, bs);
+        if (k == 0) atb2 = hh;
+        const double rel = bb > 0.0 ? sqrt(tt / bb) : 0.0;
+        const double nrm = atb2 > 0.0 ? sqrt(hh / atb2) : 0.0;
+        if (badc != 0 || !isfinite(hh) || !isfinite(tt)) {
+            finish(P, RGDBEK_ERR_NONFINITE, k, rel, nrm, acc);
+            return;
+        }
+        if (stop_rule_holds(P.stop_rule, P.tol, rel, nrm)) {
+            finish(P, RGDBEK_OK, k, rel, nrm, acc);
+            return;
+        }
+        if (k >= P.max_iter) {
+            finish(P, RGDBEK_NOT_CONVERGED, k, rel, nrm, acc);
+            return;
+        }
+        if (ld_volatile_i32(&P.ctrl->stop_req)) {
+            finish(P, RGDBEK_ERR_TIMEOUT, k, rel, nrm, acc);
+            return;
+        }
+
+        // ---- column block U_k and z_{k+1} = z_k - A_U A_U^+ z_k
+        long long nU = 0, nnzU = 0;
+        int stepsU = 0, Lsub_u = 1;
+        bool rec_u = !tr_full;
+        if (emax_c > 0.0) {
+            phase_quantize(P, P.epsc, P.n, emax_c, greedy, P.eta_col, bs);
+            RGD_SYNC();
+            if (!greedy) {
+                phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
+                RGD_SYNC();
+            }
+            phase_compact_count(P, P.n, P.cn2, P.g, bs);
+            RGD_SYNC();
+            const double fro2 = reduce_partials_sum(P.pd + D_FRO * nct, nct, bs);
+            const double gu2 = reduce_partials_sum(P.pd + D_EXTRA * nct, nct, bs);
+            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
+            RGD_SYNC();
+            const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
+            phase_extract_count(P, Arows, P.colpos, bs);
+            RGD_SYNC();
+            const double beta1 = sqrt(zz);
+            const double alpha1 = beta1 > 0.0 ? sqrt(gu2) / beta1 : 0.0;
+            rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
+            for (long long p = gthread(); p < nU; p += nthreads()) {
+                const int j = P.ulist[p];
+                P.vv[p] = beta1 > 0.0 ? P.g[j] / beta1 : 0.0;  // v~_1 = A_U^T z_k / beta1
+                P.yy[p] = 0.0;
+                if (rec_u) P.tr_lists[tr_off + p] = j;
+            }
+            nnzU = phase_extract_write(P, Arows, P.colpos, P.srp, P.sci, P.sav, S.tab, bs);
+            RGD_SYNC();
+            Lsub_u = pick_lanes((double)nnzU / (double)P.m);
+            if (beta1 > 0.0 && alpha1 > 0.0) {
+                const Side rows{P.srp, P.sci, P.sav, nullptr, P.m, Lsub_u, false};
+                const Side cols{P.cp, P.ri, P.cv, P.ulist, nU, P.tpc, true};
+                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, alpha1, beta1, sqrt(fro2), S);
+                if (stepsU < 0) return;
+            }
+        }
+
+        // ---- z_{k+1}, row residual r = b - z_{k+1} - A x_k, row weights
+        phase_zupdate(P, nU > 0, Lsub_u, bs);
+        RGD_SYNC();
+        const double emax_r = reduce_partials_max(P.pd + D_EMAX_R * nct, nct, bs);
+        zz = reduce_partials_sum(P.pd + D_ZZ * nct, nct, bs);
+        const long long badr = reduce_partials_isum(P.pi + I_BAD_R * nct, nct, bs);
+        if (badr != 0) {
+            finish(P, RGDBEK_ERR_NONFINITE, k, rel, nrm, acc);
+            return;
+        }
+
+        // ---- row block J_k and dx = (A^J)^+ r_J
+        long long nJ = 0, nnzJ = 0;
+        int stepsJ = 0;
+        bool rec_j = false;
+        if (emax_r > 0.0) {
+            phase_quantize(P, P.epsr, P.m, emax_r, greedy, P.eta_row, bs);
+            RGD_SYNC();
+            if (!greedy) {
+                phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
+                RGD_SYNC();
+            }
+            phase_compact_count(P, P.m, P.rn2, P.r, bs);
+            RGD_SYNC();
+            const double fro2 = reduce_partials_sum(P.pd + D_FRO * nct, nct, bs);
+            const double rj2 = reduce_partials_sum(P.pd + D_EXTRA * nct, nct, bs);
+            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
+            RGD_SYNC();
+            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
+            phase_extract_count(P, Acols, P.rowpos, bs);
+            RGD_SYNC();
+            rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
+            for (long long p = gthread(); p < nJ; p += nthreads()) {
+                const int i = P.jlist[p];
+                P.uu[p] = P.r[i];  // u~_1 = r_J
+                if (rec_j) P.tr_lists[tr_off + nU + p] = i;
+            }
+            nnzJ = phase_extract_write(P, Acols, P.rowpos, P.scp, P.sri, P.scv, S.tab, bs);
+            RGD_SYNC();
+            const double beta1 = sqrt(rj2);
+            if (beta1 > 0.0) {
+                const int Lsub = pick_lanes((double)nnzJ / (double)P.n);
+                const Side cols{P.scp, P.sri, P.scv, nullptr, P.n, Lsub, false};
+                const Side rows{P.rp, P.ci, P.av, P.jlist, nJ, P.tpr, true};
+                lsqr_cols(P, cols, P.uu, P.vv, nullptr, nullptr, 1.0, beta1, 0.0, true, bs);
+                RGD_SYNC();
+                const double alpha1 = sqrt(reduce_partials_sum(P.pd + D_VV * nct, nct, bs));
+                if (alpha1 > 0.0) {
+                    stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, alpha1, beta1, sqrt(fro2), S);
+                    if (stepsJ < 0) return;
+                }
+            }
+        }
+
+        acc.inner_u += stepsU;
+        acc.inner_j += stepsJ;
+        acc.sum_nu += nU;
+        acc.sum_nj += nJ;
+        acc.sum_nnzu += nnzU;
+        acc.sum_nnzj += nnzJ;
+        acc.lsqr_nnzu += (long long)stepsU * nnzU;
+        acc.lsqr_nnzj += (long long)stepsJ * nnzJ;
+        acc.lsqr_nu += (long long)stepsU * nU;
+        acc.lsqr_nj += (long long)stepsJ * nJ;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && P.tr_counts && k < P.tr_count_cap) {
+            P.tr_counts[4 * k + 0] = nU;
+            P.tr_counts[4 * k + 1] = nJ;
+            P.tr_counts[4 * k + 2] = stepsU;
+            P.tr_counts[4 * k + 3] = stepsJ;
+        }
+        if (!tr_full) {
+            const bool ok = rec_u && (nJ == 0 || rec_j) && tr_off + nU + nJ <= P.tr_list_cap;
+            if (ok) tr_off += nU + nJ;
+            else tr_full = true;
+        }
+        if (nU == 0 && nJ == 0) {
+            // both blocks empty: x can no longer change
+            finish(P, RGDBEK_OK, k, rel, nrm, acc);
+            return;
+        }
+
+        // ---- t_{k+1} = b - A x_{k+1}
+        phase_residual(P, bs);
+        RGD_SYNC();
+        tt = reduce_partials_sum(P.pd + D_TT * nct, nct, bs);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Component kernels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSolveMaxThreads) spmv_kernel(const Params P, const double *x,
+                                                                double *y) {
+    rows_matvec(P, x, y);
+}
+__global__ void __launch_bounds__(kSolveMaxThreads) spmv_t_kernel(const Params P, const double *z,
+                                                                  double *g) {
+    cols_matvec(P, z, g);
+}
+
+__global__ void __launch_bounds__(kSolveMaxThreads) weights_kernel(const double *v,
+                                                                   const double *norm2,
+                                                                   long long len, double *eps,
+                                                                   Ctrl *C) {
+    __shared__ BlockScratch bs;
+    double emax = 0.0;
+    long long bad = 0;
+    for (long long j = gthread(); j < len; j += nthreads()) {
+        const double c = norm2[j];
+        const double x = v[j];
+        const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(x, x), c) : 0.0;
+        eps[j] = e;
+        if (!isfinite(e)) bad = 1;
+        else emax = fmax(emax, e);
+    }
+    emax = block_max(emax, bs);
+    bad = block_sum(bad, bs);
+    if (threadIdx.x == 0) {
+        // nonnegative doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long *>(&C->emax_out),
+                  (unsigned long long)__double_as_longlong(emax));
+        if (bad) atomicOr(&C->bad_out, 1);
+    }
+}
+
+__global__ void __launch_bounds__(kSolveMaxThreads, 1)
+    sample_kernel(const Params P, const double *eps, long long len, long long s,
+                  unsigned long long seed, unsigned long long sysid, unsigned long long k,
+                  unsigned long long phase, int *idx, bool greedy, double eta) {
+    __shared__ SolveSmem S;
+    BlockScratch &bs = S.bs;
+    const int nct = gridDim.x;
+    double emax = 0.0;
+    long long bad = 0;
+    for (long long j = gthread(); j < len; j += nthreads()) {
+        const double e = eps[j];
+        if (!isfinite(e) || e < 0.0) bad = 1;
+        else emax = fmax(emax, e);
+    }
+    emax = block_max(emax, bs);
+    bad = block_sum(bad, bs);
+    if (threadIdx.x == 0) {
+        P.pd[D_EMAX_C * nct + blockIdx.x] = emax;
+        P.pi[I_BAD_C * nct + blockIdx.x] = bad;
+    }
+    RGD_SYNC();
+    emax = reduce_partials_max(P.pd + D_EMAX_C * nct, nct, bs);
+    bad = reduce_partials_isum(P.pi + I_BAD_C * nct, nct, bs);
+    long long count = 0;
+    if (bad == 0 && emax > 0.0) {
+        phase_quantize(P, eps, len, emax, greedy, eta, bs);
+        RGD_SYNC();
+        if (!greedy) {
+            phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
+            RGD_SYNC();
+        }
+        phase_compact_count(P, len, eps, eps, bs);
+        RGD_SYNC();
+        count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.ctrl->sample_count = bad ? -1 : count;
+        __threadfence();
+        atomicCAS(&P.ctrl->status, kStatusRunning, RGDBEK_OK);
+    }
+}
+
+#undef RGD_SYNC
+
+__global__ void reset_ctrl_kernel(Ctrl *c) {
+    c->bar_count = 0;
+    c->bar_gen = 0;
+    c->abort = 0;
+    c->status = kStatusRunning;
+    c->stop_req = 0;
+    c->iters = c->inner_u = c->inner_j = 0;
+    c->sum_nu = c->sum_nj = c->sum_nnzu = c->sum_nnzj = 0;
+    c->lsqr_nnzu = c->lsqr_nnzj = c->lsqr_nu = c->lsqr_nj = 0;
+    c->rel_res = c->normal_res = c->rse = 0.0;
+    c->sample_count = 0;
+    c->emax_out = 0.0;
+    c->bad_out = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
+    reset_ctrl_kernel<<<1, 1, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s) {
+    Params p = P;
+    void *args[] = {&p};
+    return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
+                          long long s, unsigned long long seed, unsigned long long sysid,
+                          unsigned long long k, unsigned long long phase, int *idx, bool greedy,
+                          double eta, cudaStream_t st) {
+    Params p = P;
+    void *args[] = {&p, &eps, &len, &s, &seed, &sysid, &k, &phase, &idx, &greedy, &eta};
+    return cudaLaunchCooperativeKernel((const void *)sample_kernel, dim3(grid), dim3(block), args, 0,
+                                       st);
+}
+
+cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, double *y,
+                        cudaStream_t s) {
+    spmv_kernel<<<grid, block, 0, s>>>(P, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
+                          cudaStream_t s) {
+    spmv_t_kernel<<<grid, block, 0, s>>>(P, z, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(const double *v, const double *norm2, long long len, double *eps,
+                           Ctrl *ctrl, int grid, int block, cudaStream_t s) {
+    weights_kernel<<<grid, block, 0, s>>>(v, norm2, len, eps, ctrl);
+    return cudaGetLastError();
+}
+
+int solve_blocks_per_sm(int block) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel, block, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int sample_blocks_per_sm(int block) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel, block, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+}  // namespace rgd

@@ -1,0 +1,555 @@
+// Phases of one RGDBEK outer iteration (Algorithm 1) as device functions.
+//
+// The persistent solve kernel runs them back to back with a grid barrier
+// between phases; the component kernels (spmv, weights, sampler) run the
+// same functions so that the component entry points test the solver's code.
+//
+// Work distribution:
+//  * sparse rows/columns: a group of L lanes (power of two) per row/column,
+//    warp-strided over the grid; the group sums in a fixed xor-tree order.
+//  * scans (quantised weights, compaction, block extraction): the index range
+//    is cut into gridDim.x contiguous chunks, one per CTA, each scanned in
+//    thread order; CTA offsets come from an exclusive prefix of the per-CTA
+//    totals, so every scan is exact (integers) and deterministic.
+//  * reductions: per-CTA partials, then every CTA reduces the partials in
+//    the same order, so all CTAs take identical branch decisions.
+//
+// Buffers that the kernel writes are read with ordinary loads (coherent after
+// the grid barrier); only A, its norms and b, which never change during a
+// solve, go through the read-only path.
+#pragma once
+
+#include "rgdbek_device.cuh"
+
+namespace rgd {
+
+struct Params {
+    long long m, n, nnz;
+    // A in CSR and CSC form, squared row/column norms
+    const long long *__restrict__ rp;
+    const int *__restrict__ ci;
+    const double *__restrict__ av;
+    const long long *__restrict__ cp;
+    const int *__restrict__ ri;
+    const double *__restrict__ cv;
+    const double *__restrict__ rn2;
+    const double *__restrict__ cn2;
+    // right-hand side and solution
+    const double *b;
+    double *x;
+    // work vectors: z (m), t = b - A x (m), r (m), g = A^T z (n), weights,
+    // LSQR vectors u (m), v, w, y (n), the pending x update dx (n)
+    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx;
+    unsigned long long *Q;  // chunk-local inclusive prefix of quantised weights
+    unsigned char *flag;    // drawn / selected marks
+    int *colpos, *rowpos;   // position of a column in U / of a row in J, or -1
+    int *ulist, *jlist;     // U_k and J_k, ascending
+    long long *srp;         // A_U as CSR over all m rows, columns renumbered 0..|U|-1
+    int *sci;
+    double *sav;
+    long long *scp;         // A^J as CSC over all n columns, rows renumbered 0..|J|-1
+    int *sri;
+    double *scv;
+    double *pd;             // double partials [D_NSLOTS][grid]
+    long long *pi;          // int64 partials [I_NSLOTS][grid]
+    Ctrl *ctrl;
+    long long *tr_counts;
+    long long tr_count_cap;
+    int *tr_lists;
+    long long tr_list_cap;
+    // options
+    double tol, inner_tol, eta_col, eta_row;
+    double time_budget_ns;
+    long long max_iter, s_col, s_row;
+    unsigned long long seed, sysid;
+    int inner_max, stop_rule, selection;
+    int tpr, tpc;           // lanes per row of A (CSR) and per column (CSC)
+};
+
+// Lane geometry of a group of L lanes inside a warp.
+struct Grp {
+    int L, sub, sl, rpw, lead;
+    unsigned gmask_shift;
+    __device__ __forceinline__ explicit Grp(int L_) : L(L_) {
+        const int lane = threadIdx.x & 31;
+        const int lg = __ffs(L) - 1;
+        sub = lane >> lg;
+        sl = lane & (L - 1);
+        rpw = 32 >> lg;
+        lead = sub << lg;
+        gmask_shift = (unsigned)lead;
+    }
+    // this group's bits of a warp ballot
+    __device__ __forceinline__ unsigned mine(unsigned bal) const {
+        return L == 32 ? bal : (bal >> gmask_shift) & ((1u << L) - 1u);
+    }
+};
+
+__device__ __forceinline__ long long gwarp() {
+    return (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+}
+__device__ __forceinline__ long long nwarps() {
+    return (long long)gridDim.x * (blockDim.x >> 5);
+}
+__device__ __forceinline__ long long gthread() {
+    return (long long)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ long long nthreads() {
+    return (long long)gridDim.x * blockDim.x;
+}
+
+// ---------------------------------------------------------------------------
+// Full-matrix products
+// ---------------------------------------------------------------------------
+
+// y = A x (rows of the CSR form, L lanes per row).  Component entry point.
+__device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, double *y) {
+    const Grp G(P.tpr);
+    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+        const long long i = base + G.sub;
+        double s = 0.0;
+        if (i < P.m) {
+            const long long e1 = __ldg(P.rp + i + 1);
+            for (long long e = __ldg(P.rp + i) + G.sl; e < e1; e += G.L)
+                s = fma(__ldg(P.av + e), xin[__ldg(P.ci + e)], s);
+        }
+        s = group_sum(s, G.L);
+        if (i < P.m && G.sl == 0) y[i] = s;
+    }
+}
+
+// g = A^T z (columns of the CSC form, L lanes per column).  Component entry point.
+__device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, double *gout) {
+    const Grp G(P.tpc);
+    for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
+        const long long j = base + G.sub;
+        double s = 0.0;
+        if (j < P.n) {
+            const long long e1 = __ldg(P.cp + j + 1);
+            for (long long e = __ldg(P.cp + j) + G.sl; e < e1; e += G.L)
+                s = fma(__ldg(P.cv + e), zin[__ldg(P.ri + e)], s);
+        }
+        s = group_sum(s, G.L);
+        if (j < P.n && G.sl == 0) gout[j] = s;
+    }
+}
+
+// Column pass of iteration k (Algorithm 1, first half; Section 2 weights):
+//   x_k = x_{k-1} + dx (the row update of the previous iteration), dx = 0,
+//   g = A^T z_k, h = A^T t_k with t_k = b - A x_k (for the stopping test),
+//   eps^z_j = g_j^2 / ||A_j||^2.
+// Partials: max eps^z, ||h||^2, non-finite flag.
+__device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
+    const Grp G(P.tpc);
+    double emax = 0.0, hh = 0.0;
+    long long bad = 0;
+    for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
+        const long long j = base + G.sub;
+        double sg = 0.0, sh = 0.0;
+        if (j < P.n) {
+            const long long e1 = __ldg(P.cp + j + 1);
+            for (long long e = __ldg(P.cp + j) + G.sl; e < e1; e += G.L) {
+                const double a = __ldg(P.cv + e);
+                const int i = __ldg(P.ri + e);
+                sg = fma(a, P.z[i], sg);
+                sh = fma(a, P.t[i], sh);
+            }
+        }
+        sg = group_sum(sg, G.L);
+        sh = group_sum(sh, G.L);
+        if (j < P.n && G.sl == 0) {
+            P.x[j] = P.x[j] + P.dx[j];
+            P.dx[j] = 0.0;
+            const double c = __ldg(P.cn2 + j);
+            const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(sg, sg), c) : 0.0;
+            P.g[j] = sg;
+            P.epsc[j] = e;
+            if (!isfinite(e)) bad = 1;
+            else emax = fmax(emax, e);
+            hh = fma(sh, sh, hh);
+        }
+    }
+    emax = block_max(emax, bs);
+    hh = block_sum(hh, bs);
+    bad = block_sum(bad, bs);
+    if (threadIdx.x == 0) {
+        P.pd[D_EMAX_C * gridDim.x + blockIdx.x] = emax;
+        P.pd[D_HH * gridDim.x + blockIdx.x] = hh;
+        P.pi[I_BAD_C * gridDim.x + blockIdx.x] = bad;
+    }
+}
+
+// t_{k+1} = b - A (x_k + dx) over the CSR rows.  Partial: ||t||^2.
+__device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs) {
+    const Grp G(P.tpr);
+    double tt = 0.0;
+    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+        const long long i = base + G.sub;
+        double s = 0.0;
+        if (i < P.m) {
+            const long long e1 = __ldg(P.rp + i + 1);
+            for (long long e = __ldg(P.rp + i) + G.sl; e < e1; e += G.L) {
+                const int j = __ldg(P.ci + e);
+                s = fma(__ldg(P.av + e), P.x[j] + P.dx[j], s);
+            }
+        }
+        s = group_sum(s, G.L);
+        if (i < P.m && G.sl == 0) {
+            const double ti = __ldg(P.b + i) - s;
+            P.t[i] = ti;
+            tt = fma(ti, ti, tt);
+        }
+    }
+    tt = block_sum(tt, bs);
+    if (threadIdx.x == 0) P.pd[D_TT * gridDim.x + blockIdx.x] = tt;
+}
+
+// ---------------------------------------------------------------------------
+// Block selection (Section 2): quantise, draw, compact
+// ---------------------------------------------------------------------------
+struct Chunk {
+    long long lo, hi, size;
+    __device__ __forceinline__ Chunk(long long len, int cta, int nct) {
+        size = (len + nct - 1) / nct;
+        lo = min(len, (long long)cta * size);
+        hi = min(len, lo + size);
+    }
+};
+
+// Random rule: q_j = floor(2^K eps_j / eps_max), K = 62 - ceil(log2 len), and
+// the chunk-local inclusive prefix of q into Q; clears the marks.  Partial:
+// the chunk total.  Greedy rule: marks {j : eps_j >= eta eps_max, eps_j > 0}.
+__device__ __forceinline__ void phase_quantize(const Params &P, const double *eps, long long len,
+                                               double emax, bool greedy, double eta,
+                                               BlockScratch &bs) {
+    const Chunk C(len, blockIdx.x, gridDim.x);
+    if (greedy) {
+        const double thr = __dmul_rn(eta, emax);
+        for (long long j = C.lo + threadIdx.x; j < C.hi; j += blockDim.x) {
+            const double e = eps[j];
+            P.flag[j] = (e >= thr && e > 0.0) ? 1 : 0;
+        }
+        return;
+    }
+    const int K = 62 - ceil_log2_ll(len);
+    unsigned long long run = 0;
+    for (long long base = C.lo; base < C.hi; base += blockDim.x) {
+        const long long j = base + threadIdx.x;
+        unsigned long long q = 0;
+        if (j < C.hi) {
+            const double ratio = __ddiv_rn(eps[j], emax);
+            q = __double2ull_rz(floor(scalbn(ratio, K)));
+            P.flag[j] = 0;
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<unsigned long long>(q, bs, &tot);
+        if (j < C.hi) P.Q[j] = run + ex + q;
+        run += tot;
+    }
+    if (threadIdx.x == 0) P.pi[I_TOT * gridDim.x + blockIdx.x] = (long long)run;
+}
+
+// s independent draws: R = word (t mod 4) of Philox4x64-10 with key
+// (seed, sysid) and counter (k, phase, t div 4, 0); target = floor(R Q_tot /
+// 2^64); the drawn index is the first j whose global inclusive prefix of q
+// exceeds target (located through the per-CTA totals, then inside the chunk).
+__device__ __forceinline__ void phase_draw(const Params &P, long long len, long long s,
+                                           unsigned long long seed, unsigned long long sysid,
+                                           unsigned long long k, unsigned long long phase,
+                                           long long *tab, BlockScratch &bs) {
+    const int nct = gridDim.x;
+    partials_prefix(P.pi + I_TOT * nct, nct, tab, bs);
+    const unsigned long long qtot = (unsigned long long)tab[nct - 1];
+    if (qtot == 0) return;
+    const long long csize = (len + nct - 1) / nct;
+    const long long nblk = (s + 3) >> 2;
+    for (long long t4 = gthread(); t4 < nblk; t4 += nthreads()) {
+        const U64x4 R = philox4x64_10(seed, sysid, k, phase, (unsigned long long)t4, 0ull);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            if (4 * t4 + w >= s) break;
+            const unsigned long long target = __umul64hi(R.v[w], qtot);
+            int lo = 0, hi = nct - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((unsigned long long)tab[mid] > target) hi = mid;
+                else lo = mid + 1;
+            }
+            const unsigned long long local = target - (lo > 0 ? (unsigned long long)tab[lo - 1] : 0ull);
+            long long a = (long long)lo * csize;
+            long long e = min(len, a + csize) - 1;
+            while (a < e) {
+                const long long mid = a + ((e - a) >> 1);
+                if (P.Q[mid] > local) e = mid;
+                else a = mid + 1;
+            }
+            P.flag[a] = 1;
+        }
+    }
+}
+
+// Count of marked indices in the chunk, and over them the sums of norm2 (the
+// block's squared Frobenius norm) and of vec^2 (for the LSQR start).
+__device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
+                                                    const double *norm2, const double *vec,
+                                                    BlockScratch &bs) {
+    const Chunk C(len, blockIdx.x, gridDim.x);
+    long long cnt = 0;
+    double fro = 0.0, ext = 0.0;
+    for (long long base = C.lo; base < C.hi; base += blockDim.x) {
+        const long long j = base + threadIdx.x;
+        const bool f = j < C.hi && P.flag[j];
+        cnt += __popc(__ballot_sync(kFull, f)) * ((threadIdx.x & 31) == 0);
+        if (f) {
+            fro += __ldg(norm2 + j);
+            const double v = vec[j];
+            ext = fma(v, v, ext);
+        }
+    }
+    cnt = block_sum(cnt, bs);
+    fro = block_sum(fro, bs);
+    ext = block_sum(ext, bs);
+    if (threadIdx.x == 0) {
+        P.pi[I_CNT * gridDim.x + blockIdx.x] = cnt;
+        P.pd[D_FRO * gridDim.x + blockIdx.x] = fro;
+        P.pd[D_EXTRA * gridDim.x + blockIdx.x] = ext;
+    }
+}
+
+// Exclusive rank of a predicate over the CTA in thread order (ballot/popc per
+// warp, then the warp counts scanned); *total gets the CTA count.
+__device__ __forceinline__ long long block_rank_pred(bool f, BlockScratch &bs, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned bal = __ballot_sync(kFull, f);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) bs.i[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+        long long s = lane < nw ? bs.i[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        bs.i[lane] = s;
+    }
+    __syncthreads();
+    *total = bs.i[nw - 1];
+    return (warp > 0 ? bs.i[warp - 1] : 0) + rank;
+}
+
+// Marked indices -> ascending list; pos[j] = position in the list or -1.
+// Returns the list length.
+__device__ __forceinline__ long long phase_compact_write(const Params &P, long long len, int *pos,
+                                                         int *list, long long *tab,
+                                                         BlockScratch &bs) {
+    const int nct = gridDim.x;
+    partials_prefix(P.pi + I_CNT * nct, nct, tab, bs);
+    const long long total = tab[nct - 1];
+    const Chunk C(len, blockIdx.x, nct);
+    long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
+    for (long long base = C.lo; base < C.hi; base += blockDim.x) {
+        const long long j = base + threadIdx.x;
+        const bool f = j < C.hi && P.flag[j];
+        long long tot;
+        const long long ex = block_rank_pred(f, bs, &tot);
+        if (j < C.hi) {
+            if (f) {
+                pos[j] = (int)(run + ex);
+                list[run + ex] = (int)j;
+            } else {
+                pos[j] = -1;
+            }
+        }
+        run += tot;
+    }
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// Block extraction: the nonzeros of `nlines` CSR rows (or CSC columns) whose
+// other index is selected (map[idx] >= 0), renumbered through map.  Output is
+// a CSR (CSC) over all nlines lines, so A_U keeps all m rows and A^J all n
+// columns, and both block products are gathers (no atomics).
+// ---------------------------------------------------------------------------
+struct Lines {
+    const long long *ptr;
+    const int *idx;
+    const double *val;
+    long long n;
+    int L;
+};
+
+__device__ __forceinline__ void phase_extract_count(const Params &P, const Lines &A, const int *map,
+                                                    BlockScratch &bs) {
+    const Grp G(A.L);
+    const Chunk C(A.n, blockIdx.x, gridDim.x);
+    const long long per_tile = (long long)(blockDim.x >> 5) * G.rpw;
+    long long cnt = 0;
+    for (long long tb = C.lo; tb < C.hi; tb += per_tile) {
+        const long long i = tb + (long long)(threadIdx.x >> 5) * G.rpw + G.sub;
+        if (i < C.hi) {
+            const long long e1 = __ldg(A.ptr + i + 1);
+            for (long long e = __ldg(A.ptr + i) + G.sl; e < e1; e += G.L)
+                cnt += map[__ldg(A.idx + e)] >= 0;
+        }
+    }
+    cnt = block_sum(cnt, bs);
+    if (threadIdx.x == 0) P.pi[I_NNZ * gridDim.x + blockIdx.x] = cnt;
+}
+
+__device__ __forceinline__ long long phase_extract_write(const Params &P, const Lines &A,
+                                                         const int *map, long long *optr,
+                                                         int *oidx, double *oval, long long *tab,
+                                                         BlockScratch &bs) {
+    const int nct = gridDim.x;
+    partials_prefix(P.pi + I_NNZ * nct, nct, tab, bs);
+    const long long total = tab[nct - 1];
+    const Grp G(A.L);
+    const Chunk C(A.n, blockIdx.x, nct);
+    const long long per_tile = (long long)(blockDim.x >> 5) * G.rpw;
+    long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
+    for (long long tb = C.lo; tb < C.hi; tb += per_tile) {
+        const long long i = tb + (long long)(threadIdx.x >> 5) * G.rpw + G.sub;
+        const bool valid = i < C.hi;
+        const long long e0 = valid ? __ldg(A.ptr + i) : 0;
+        const long long e1 = valid ? __ldg(A.ptr + i + 1) : 0;
+        int c = 0;
+        for (long long e = e0 + G.sl; e < e1; e += G.L) c += map[__ldg(A.idx + e)] >= 0;
+        c = group_sum(c, G.L);
+        long long tot;
+        const long long ex = block_excl_scan<long long>((valid && G.sl == 0) ? c : 0, bs, &tot);
+        const long long start = run + __shfl_sync(kFull, ex, G.lead);
+        if (valid && G.sl == 0) optr[i] = start;
+        int nit = valid ? (int)((e1 - e0 + G.L - 1) / G.L) : 0;
+        nit = __reduce_max_sync(kFull, (unsigned)nit);
+        long long pos = start;
+        for (int it = 0; it < nit; ++it) {
+            const long long e = e0 + (long long)it * G.L + G.sl;
+            int p = -1;
+            if (valid && e < e1) p = map[__ldg(A.idx + e)];
+            const unsigned gm = G.mine(__ballot_sync(kFull, p >= 0));
+            if (p >= 0) {
+                const long long o = pos + __popc(gm & ((1u << G.sl) - 1u));
+                oidx[o] = p;
+                oval[o] = __ldg(A.val + e);
+            }
+            pos += __popc(gm);
+        }
+        run += tot;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) optr[A.n] = total;
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// LSQR (Paige & Saunders 1982) on a block B, the inner solver of Remark 3.1.
+// Vectors are kept unnormalised: u~ = beta u, v~ = alpha v, so each step is
+// two grid phases (one barrier each):
+//   rows:  w = v~/alpha - (theta/rho_prev) w        (the w update of the
+//          previous step), u~_new = B v~ / alpha - (alpha/beta) u~
+//   cols:  v~_new = B^T u~_new / beta_new - (beta_new/alpha) v~,
+//          y += (phi/rho) w
+// `Rows` is the u-space side of B (lines of B), `Cols` the v-space side.
+// ---------------------------------------------------------------------------
+struct Side {
+    const long long *ptr;  // line pointers (indexed by line id)
+    const int *idx;        // indices into the other space
+    const double *val;
+    const int *list;       // line id of line c is list[c] (or c when null)
+    long long n;           // number of lines in this space
+    int L;
+    bool ro;               // ptr/idx/val never written during the solve
+};
+
+// this lane's share of <line, vec>; the caller sums it over the group
+__device__ __forceinline__ double side_partial(const Side &S, long long line, const Grp &G,
+                                               const double *vec) {
+    double s = 0.0;
+    if (S.ro) {
+        const long long e1 = __ldg(S.ptr + line + 1);
+        for (long long e = __ldg(S.ptr + line) + G.sl; e < e1; e += G.L)
+            s = fma(__ldg(S.val + e), vec[__ldg(S.idx + e)], s);
+    } else {
+        const long long e1 = S.ptr[line + 1];
+        for (long long e = S.ptr[line] + G.sl; e < e1; e += G.L) s = fma(S.val[e], vec[S.idx[e]], s);
+    }
+    return s;
+}
+
+// rows phase; uold is u~ of the previous step (the right-hand side c on the
+// first step).  Partial: ||u~_new||^2.
+__device__ __forceinline__ void lsqr_rows(const Params &P, const Side &R, long long nv,
+                                          const double *uold, double *unew, const double *vv,
+                                          double *ww, double alpha, double beta, bool first,
+                                          double wcoef, BlockScratch &bs) {
+    const double inv_a = 1.0 / alpha, ab = alpha / beta;
+    for (long long c = gthread(); c < nv; c += nthreads()) {
+        const double vn = vv[c] * inv_a;
+        ww[c] = first ? vn : vn - wcoef * ww[c];
+    }
+    const Grp G(R.L);
+    double uu = 0.0;
+    for (long long base = gwarp() * G.rpw; base < R.n; base += nwarps() * G.rpw) {
+        const long long c = base + G.sub;
+        double s = 0.0;
+        if (c < R.n) s = side_partial(R, R.list ? R.list[c] : c, G, vv);
+        s = group_sum(s, G.L);
+        if (c < R.n && G.sl == 0) {
+            const double u = s * inv_a - ab * uold[c];
+            unew[c] = u;
+            uu = fma(u, u, uu);
+        }
+    }
+    uu = block_sum(uu, bs);
+    if (threadIdx.x == 0) P.pd[D_UU * gridDim.x + blockIdx.x] = uu;
+}
+
+// cols phase.  With beta_new == 0 only the y update runs.  init: the first
+// v~ = B^T u~ / beta of the row block (no previous v~, no y update).
+// Partial: ||v~_new||^2.
+__device__ __forceinline__ void lsqr_cols(const Params &P, const Side &Cs, const double *uu,
+                                          double *vv, const double *ww, double *yy, double alpha,
+                                          double beta_new, double phi_rho, bool init,
+                                          BlockScratch &bs) {
+    const Grp G(Cs.L);
+    double acc = 0.0;
+    const bool mv = beta_new > 0.0;
+    const double inv_b = mv ? 1.0 / beta_new : 0.0;
+    const double ba = init ? 0.0 : beta_new / alpha;
+    for (long long base = gwarp() * G.rpw; base < Cs.n; base += nwarps() * G.rpw) {
+        const long long c = base + G.sub;
+        double s = 0.0;
+        if (mv && c < Cs.n) s = side_partial(Cs, Cs.list ? Cs.list[c] : c, G, uu);
+        s = group_sum(s, G.L);
+        if (c < Cs.n && G.sl == 0) {
+            if (mv) {
+                const double v = init ? s * inv_b : s * inv_b - ba * vv[c];
+                vv[c] = v;
+                acc = fma(v, v, acc);
+            }
+            if (!init) yy[c] = fma(phi_rho, ww[c], yy[c]);
+        }
+    }
+    acc = block_sum(acc, bs);
+    if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
+}
+
+// Scalar recurrences of LSQR, identical in every thread of every CTA.
+struct LsqrScalars {
+    double alpha, beta, rhobar, phibar, beta1, fro, wcoef;
+    double cs, sn, rho;
+    int steps;
+    bool done;
+};
+
+__device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {
+    switch (rule) {
+    case RGDBEK_STOP_REL_RES: return rel <= tol;
+    case RGDBEK_STOP_RSE: return rel * rel <= tol;
+    default: return nrm <= tol;
+    }
+}
+
+}  // namespace rgd
