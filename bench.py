@@ -315,6 +315,13 @@ def run_ours(args):
             "time_to_tol_s": statistics.median(ms) / 1e3,
             "iters_per_solve": [s.iters for s in stats],
             "final_normal_res": st0.normal_res, "final_rel_res": st0.rel_res,
+            "per_iteration": {"lsqr_steps_col": st0.inner_u / max(st0.iters, 1),
+                              "lsqr_steps_row": st0.inner_j / max(st0.iters, 1),
+                              "block_cols": st0.sum_nu / max(st0.iters, 1),
+                              "block_rows": st0.sum_nj / max(st0.iters, 1),
+                              "nnz_A_U": st0.sum_nnz_u / max(st0.iters, 1),
+                              "nnz_A_J": st0.sum_nnz_j / max(st0.iters, 1)},
+            "phase_ms": {k: round(v, 3) for k, v in st0.as_dict()["phase_ms"].items()},
             "wall_s": wall,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -63,7 +63,7 @@ typedef struct {
     double time_budget_s;  /* wall-clock cap of one solve on the device, 0 = none   */
     uint64_t system_id;    /* second word of the Philox key                         */
     int blocks_per_sm;     /* persistent grid: CTAs per SM, 0 = largest that fits   */
-    int threads_per_block; /* 0 = 512; a multiple of 32 in [64, 1024]               */
+    int threads_per_block; /* 0 = 1024; a multiple of 32 in [64, 1024]              */
 } rgdbek_options;
 
 typedef struct {
@@ -82,7 +82,17 @@ typedef struct {
     double normal_res;  /* ||A^T (b - A x)|| / ||A^T b|| of the returned x       */
     double rse;         /* rel_res^2, the paper's RSE                            */
     int status;         /* same as the return code of the solve                  */
+    /* device time (ms, globaltimer of CTA 0) spent per phase kind, in the order
+     * of RGDBEK_PHASE_NAMES: set-up, column pass, column selection, A_U
+     * extraction, LSQR on A_U, z update, row selection, A^J extraction, LSQR on
+     * A^J, residual pass */
+    double phase_ms[10];
 } rgdbek_stats;
+
+#define RGDBEK_NUM_PHASES 10
+#define RGDBEK_PHASE_NAMES                                                            \
+    "setup", "col_pass", "col_select", "col_extract", "col_lsqr", "z_update", "row_select", \
+        "row_extract", "row_lsqr", "residual_pass"
 
 typedef struct {
     int64_t m, n, nnz;

@@ -31,6 +31,8 @@ STOP_AUTO = 0
 STOP_REL_RES = 1
 STOP_NORMAL = 2
 STOP_RSE = 3
+PHASE_NAMES = ("setup", "col_pass", "col_select", "col_extract", "col_lsqr", "z_update",
+               "row_select", "row_extract", "row_lsqr", "residual_pass")
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -52,11 +54,13 @@ class rgdbek_stats(ctypes.Structure):
         ("iters", _i64), ("inner_u", _i64), ("inner_j", _i64), ("sum_nu", _i64), ("sum_nj", _i64),
         ("sum_nnz_u", _i64), ("sum_nnz_j", _i64), ("lsqr_nnz_u", _i64), ("lsqr_nnz_j", _i64),
         ("lsqr_n_u", _i64), ("lsqr_n_j", _i64), ("rel_res", _dbl), ("normal_res", _dbl),
-        ("rse", _dbl), ("status", _int),
+        ("rse", _dbl), ("status", _int), ("phase_ms", _dbl * 10),
     ]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["phase_ms"] = dict(zip(PHASE_NAMES, list(self.phase_ms)))
+        return d
 
 
 class rgdbek_info_t(ctypes.Structure):

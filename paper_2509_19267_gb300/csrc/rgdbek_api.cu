@@ -270,8 +270,8 @@ int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_
         release(h);
         return st;
     }
-    h->tpr = pick_lanes((double)nnz / (double)m);
-    h->tpc = pick_lanes((double)nnz / (double)n);
+    h->tpr = pick_lanes_int(nnz, m);
+    h->tpc = pick_lanes_int(nnz, n);
 
     Layout L;
     carve(h, L);
@@ -428,6 +428,7 @@ int rgdbek_solve(rgdbek_t h, const double *b, double *x, double tol, int64_t max
         st->normal_res = c.normal_res;
         st->rse = c.rse;
         st->status = status;
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
     }
     return status;
 }

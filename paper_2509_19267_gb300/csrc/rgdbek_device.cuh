@@ -20,7 +20,7 @@ constexpr int kMaxThreads = 1024;
 // Wait limits of the grid barrier: after either, the waiting CTA records
 // RGDBEK_ERR_TIMEOUT, raises the abort flag and returns, so no wait is endless.
 constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s
-constexpr unsigned long long kBarrierMaxSpins = 1ull << 28;
+constexpr unsigned long long kBarrierMaxSpins = 1ull << 30;
 
 // Slots of the per-CTA partial arrays (double and int64), [slot][grid].
 // Two phases separated by one barrier never write the same slot, so a slow
@@ -47,13 +47,11 @@ enum ISlot {
     I_NSLOTS
 };
 
-// Device control block, one per handle.  Barrier words sit on their own
-// 128-byte lines.
+// Device control block, one per handle.  The barrier counter sits on its
+// own 128-byte line.
 struct Ctrl {
-    unsigned bar_count;
-    unsigned pad0[31];
-    unsigned bar_gen;
-    unsigned pad1[31];
+    unsigned long long bar_count;  // arrivals since the launch (monotonic)
+    unsigned long long pad0[15];
     int abort;
     int status;
     int stop_req;
@@ -61,6 +59,7 @@ struct Ctrl {
     // results, written by CTA 0 at the end of a solve
     long long iters, inner_u, inner_j, sum_nu, sum_nj, sum_nnzu, sum_nnzj;
     long long lsqr_nnzu, lsqr_nnzj, lsqr_nu, lsqr_nj;
+    unsigned long long phase_ns[RGDBEK_NUM_PHASES];
     double rel_res, normal_res, rse;
     long long sample_count;  // block size returned by the standalone sampler
     double emax_out;         // maximum returned by the standalone weights kernel
@@ -71,13 +70,19 @@ struct Ctrl {
 // ---------------------------------------------------------------------------
 // Memory-model helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long *p,
+                                                                   unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;"
+                 : "=l"(old)
+                 : "l"(p), "l"(v)
+                 : "memory");
+    return old;
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
@@ -88,41 +93,39 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Grid-wide barrier for cooperative launches (all CTAs resident).  Returns
-// false if the wait was abandoned: another CTA raised the abort flag, or the
+// Grid-wide barrier for cooperative launches (all CTAs resident).  `epoch`
+// (read and advanced by thread 0 only) counts the barriers this CTA has
+// passed, the same number in every CTA: barrier
+// number e completes when the arrival counter reaches gridDim.x * (e + 1).
+// Arrival is a release add by thread 0 after the CTA's __syncthreads (so the
+// CTA's writes are published); the wait is an acquire load followed by a
+// __syncthreads (so every thread sees the other CTAs' writes).  Returns false
+// if the wait was abandoned: another CTA raised the abort flag, or the
 // time/spin limit ran out (then this CTA records TIMEOUT and raises abort).
-__device__ __forceinline__ bool grid_barrier(Ctrl *c) {
+__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_acquire_u32(&c->bar_gen);
-        __threadfence();
-        const unsigned prev = atomicAdd(&c->bar_count, 1u);
-        if (prev == gridDim.x - 1) {
-            c->bar_count = 0;
-            __threadfence();
-            st_release_u32(&c->bar_gen, gen + 1);
-        } else {
-            unsigned long long spins = 0;
-            const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(&c->bar_gen) == gen) {
-                ++spins;
-                if ((spins & 255) == 0) {
-                    if (ld_volatile_i32(&c->abort)) { ok = 0; break; }
-                    if (spins > kBarrierMaxSpins || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-                        atomicCAS(&c->status, kStatusRunning, RGDBEK_ERR_TIMEOUT);
-                        atomicExch(&c->abort, 1);
-                        ok = 0;
-                        break;
-                    }
+        const unsigned long long target = (unsigned long long)gridDim.x * (epoch + 1);
+        atom_add_release_u64(&c->bar_count, 1ull);
+        unsigned long long spins = 0;
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u64(&c->bar_count) < target) {
+            ++spins;
+            if ((spins & 1023) == 0) {
+                if (ld_volatile_i32(&c->abort)) { ok = 0; break; }
+                if (spins > kBarrierMaxSpins || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicCAS(&c->status, kStatusRunning, RGDBEK_ERR_TIMEOUT);
+                    atomicExch(&c->abort, 1);
+                    ok = 0;
+                    break;
                 }
-                if (spins > 64) __nanosleep(32);
             }
+            if (spins > 256) __nanosleep(20);
         }
-        __threadfence();
-        if (ld_volatile_i32(&c->abort)) ok = 0;
         s_ok = ok;
+        ++epoch;
     }
     __syncthreads();
     return s_ok != 0;
@@ -266,6 +269,46 @@ __device__ __forceinline__ long long reduce_partials_isum(const long long *p, in
     return bs.i[33];
 }
 
+// All requested partial slots reduced at once: warp w of the CTA reduces the
+// w-th requested slot (sums in a fixed order; maxima for slots in dmax), and
+// the results land in out_d[slot] / out_i[slot] for every thread.  dmask /
+// imask select double / int64 slots (bit = slot).
+__device__ __forceinline__ void collect_partials(const double *pd, const long long *pi, int nb,
+                                                 unsigned dmask, unsigned dmax, unsigned imask,
+                                                 double *out_d, long long *out_i) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int w = 0;
+    for (int slot = 0; slot < D_NSLOTS; ++slot) {
+        if (!(dmask >> slot & 1u)) continue;
+        if (warp == w) {
+            const double *p = pd + slot * nb;
+            const bool mx = dmax >> slot & 1u;
+            double s = 0.0;
+#pragma unroll 8
+            for (int i = lane; i < nb; i += 32) {
+                const double v = __ldcg(p + i);
+                s = mx ? fmax(s, v) : s + v;
+            }
+            s = mx ? warp_max(s) : warp_sum(s);
+            if (lane == 0) out_d[slot] = s;
+        }
+        ++w;
+    }
+    for (int slot = 0; slot < I_NSLOTS; ++slot) {
+        if (!(imask >> slot & 1u)) continue;
+        if (warp == w) {
+            const long long *p = pi + slot * nb;
+            long long s = 0;
+#pragma unroll 8
+            for (int i = lane; i < nb; i += 32) s += __ldcg(p + i);
+            s = warp_sum(s);
+            if (lane == 0) out_i[slot] = s;
+        }
+        ++w;
+    }
+    __syncthreads();
+}
+
 // Inclusive prefix over the per-CTA int64 partials of one slot, into smem
 // table tab[0..nb-1] (nb <= kMaxGrid).  Every thread may read tab afterwards.
 __device__ __forceinline__ void partials_prefix(const long long *p, int nb, long long *tab,
@@ -322,11 +365,12 @@ __device__ __forceinline__ int ceil_log2_ll(long long v) {
     return v <= 1 ? 0 : 64 - __clzll((unsigned long long)(v - 1));
 }
 
-// lanes to put on one row/column with `avg` nonzeros on average: the largest
-// power of two L <= 32 with 2L <= avg (at least 1)
-__host__ __device__ __forceinline__ int pick_lanes(double avg) {
+// lanes to put on one row/column of a matrix with nnz nonzeros in `lines`
+// rows/columns: the largest power of two L <= 32 with 2L <= nnz / lines
+// (at least 1); integer arithmetic only
+__host__ __device__ __forceinline__ int pick_lanes_int(long long nnz, long long lines) {
     int L = 1;
-    while (L < 32 && 4.0 * L <= avg) L *= 2;
+    while (L < 32 && 4ll * L * lines <= nnz) L *= 2;
     return L;
 }
 

@@ -9,7 +9,7 @@
 
 namespace rgd {
 
-constexpr int kSolveMaxThreads = 512;   // launch bound of the persistent kernels
+constexpr int kSolveMaxThreads = 1024;  // launch bound of the persistent kernels
 
 // control block to its pre-launch state (status = kStatusRunning)
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);

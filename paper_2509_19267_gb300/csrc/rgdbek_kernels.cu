@@ -22,20 +22,73 @@
 
 namespace rgd {
 
+// Scalars of the LSQR recurrences.  GB300's FP64 rate is low, so they are
+// computed by thread 0 of each CTA only (every CTA gets bit-identical values
+// from the identically reduced partials) and broadcast through shared memory.
+struct LsqrState {
+    double alpha, beta, rhobar, phibar, beta1, fro;
+    double rho, cs, sn;          // plane rotation of the current step
+    double inv_a, ab, wcoef;     // coefficients of the next rows phase
+    double inv_b, ba, phi_rho;   // coefficients of the next cols phase
+    int mv, done;
+};
+
+// Scalars of the outer iteration, also computed by thread 0 only.
+struct OuterState {
+    double bb, tt, zz, atb2, rel, nrm, emax_c, emax_r;
+    double beta1, alpha1, fro2, inv_beta1;
+    int verdict;                 // status to finish with, or kStatusRunning to go on
+};
+
+// per-solve counters, kept by thread 0 (only CTA 0's copy is reported)
+struct Acc {
+    long long inner_u, inner_j, sum_nu, sum_nj, sum_nnzu, sum_nnzj;
+    long long lsqr_nnzu, lsqr_nnzj, lsqr_nu, lsqr_nj;
+};
+
 struct SolveSmem {
     BlockScratch bs;
+    Acc acc;
     long long tab[kMaxGrid];
+    double red_d[D_NSLOTS];                          // reduced partials of the last barrier
+    long long red_i[I_NSLOTS];
+    LsqrState lsqr;                                  // LSQR scalars (written by thread 0)
+    OuterState o;                                    // outer-loop scalars (thread 0)
+    unsigned long long epoch;                        // grid barriers passed (thread 0 copy)
+    unsigned long long tlast;                        // phase timers (CTA 0, thread 0)
+    unsigned long long tphase[RGDBEK_NUM_PHASES];
 };
 
-struct Acc {
-    long long inner_u = 0, inner_j = 0, sum_nu = 0, sum_nj = 0, sum_nnzu = 0, sum_nnzj = 0;
-    long long lsqr_nnzu = 0, lsqr_nnzj = 0, lsqr_nu = 0, lsqr_nj = 0;
-};
+enum PhaseId { PH_SETUP = 0, PH_COL, PH_COL_SEL, PH_COL_EXT, PH_COL_LSQR, PH_ZUPD, PH_ROW_SEL,
+               PH_ROW_EXT, PH_ROW_LSQR, PH_RESID };
+
+// charges the time since the previous mark to phase `id` (CTA 0 only)
+__device__ __forceinline__ void mark(SolveSmem &S, int id) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long now = globaltimer_ns();
+        S.tphase[id] += now - S.tlast;
+        S.tlast = now;
+    }
+}
+
+#define DS(x) (1u << (x))
+
+// Grid barrier, then the requested partial slots reduced into S.red_*.
+// Returns false if the barrier was abandoned.
+__device__ __forceinline__ bool sync_collect(const Params &P, SolveSmem &S, unsigned dmask,
+                                             unsigned dmax, unsigned imask) {
+    if (!grid_barrier(P.ctrl, S.epoch)) return false;
+    if (dmask | imask)
+        collect_partials(P.pd, P.pi, gridDim.x, dmask, dmax, imask, S.red_d, S.red_i);
+    return true;
+}
 
 __device__ __forceinline__ void finish(const Params &P, int status, long long k, double rel,
-                                       double nrm, const Acc &a) {
+                                       double nrm, const SolveSmem &S) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const Acc &a = S.acc;
         Ctrl *C = P.ctrl;
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) C->phase_ns[i] = S.tphase[i];
         C->iters = k;
         C->inner_u = a.inner_u;
         C->inner_j = a.inner_j;
@@ -58,36 +111,65 @@ __device__ __forceinline__ void finish(const Params &P, int status, long long k,
 // LSQR on the block given by its row side R (u-space lines) and column side
 // Cs (v-space lines), from y = 0.  c0 = u~_1 (the right-hand side c), beta =
 // ||c||, alpha = ||B^T c|| / beta, with v~_1 already in P.vv.  The solution
-// accumulates into y (zero on entry).  Returns the number of steps, or -1 if
-// a grid barrier was abandoned.
+// accumulates into y (zero on entry); fro2 = ||B||_F^2.  Returns the number
+// of steps, or -1 if a grid barrier was abandoned.
 __device__ __forceinline__ int run_lsqr(const Params &P, const Side &R, const Side &Cs,
                                         const double *c0, double *y, double alpha, double beta,
-                                        double fro, SolveSmem &S) {
-    const int nct = gridDim.x;
-    double rhobar = alpha, phibar = beta, wcoef = 0.0;
-    const double beta1 = beta;
+                                        double fro2, SolveSmem &S) {
+    LsqrState &L = S.lsqr;
+    if (threadIdx.x == 0) {
+        L.alpha = alpha;
+        L.beta = beta;
+        L.rhobar = alpha;
+        L.phibar = beta;
+        L.beta1 = beta;
+        L.fro = sqrt(fro2);
+        L.inv_a = 1.0 / alpha;
+        L.ab = alpha / beta;
+        L.wcoef = 0.0;
+        L.done = 0;
+    }
+    __syncthreads();
     for (int it = 1;; ++it) {
-        lsqr_rows(P, R, Cs.n, it == 1 ? c0 : P.uu, P.uu, P.vv, P.ww, alpha, beta, it == 1, wcoef,
-                  S.bs);
-        if (!grid_barrier(P.ctrl)) return -1;
-        const double bn = sqrt(reduce_partials_sum(P.pd + D_UU * nct, nct, S.bs));
-        const double rho = sqrt(rhobar * rhobar + bn * bn);
-        const double cs = rhobar / rho, sn = bn / rho;
-        const double phi = cs * phibar;
-        phibar = sn * phibar;
-        lsqr_cols(P, Cs, P.uu, P.vv, P.ww, y, alpha, bn, phi / rho, false, S.bs);
-        if (!grid_barrier(P.ctrl)) return -1;
-        const double an = bn > 0.0 ? sqrt(reduce_partials_sum(P.pd + D_VV * nct, nct, S.bs)) : 0.0;
-        const double theta = sn * an;
-        rhobar = -cs * an;
-        wcoef = theta / rho;
-        const double rnorm = phibar;
-        const double arnorm = phibar * an * fabs(cs);
-        alpha = an;
-        beta = bn;
-        if (arnorm <= P.inner_tol * fro * rnorm || rnorm <= P.inner_tol * beta1 || an == 0.0 ||
-            bn == 0.0 || it >= P.inner_max)
-            return it;
+        lsqr_rows(P, R, Cs.n, it == 1 ? c0 : P.uu, P.uu, P.vv, P.ww, L.inv_a, L.ab, it == 1,
+                  L.wcoef, S.bs);
+        if (!sync_collect(P, S, DS(D_UU), 0, 0)) return -1;
+        if (threadIdx.x == 0) {
+            const double bn = sqrt(S.red_d[D_UU]);
+            const double rho = sqrt(L.rhobar * L.rhobar + bn * bn);
+            const double cs = L.rhobar / rho, sn = bn / rho;
+            const double phi = cs * L.phibar;
+            L.phibar = sn * L.phibar;
+            L.mv = bn > 0.0;
+            L.inv_b = bn > 0.0 ? 1.0 / bn : 0.0;
+            L.ba = bn / L.alpha;
+            L.phi_rho = phi / rho;
+            L.beta = bn;
+            L.rho = rho;
+            L.cs = cs;
+            L.sn = sn;
+        }
+        __syncthreads();
+        lsqr_cols(P, Cs, P.uu, P.vv, P.ww, y, L.inv_b, L.ba, L.phi_rho, L.mv != 0, false, S.bs);
+        if (!sync_collect(P, S, DS(D_VV), 0, 0)) return -1;
+        if (threadIdx.x == 0) {
+            const double rho = L.rho, cs = L.cs, sn = L.sn, bn = L.beta;
+            const double an = bn > 0.0 ? sqrt(S.red_d[D_VV]) : 0.0;
+            const double theta = sn * an;
+            L.rhobar = -cs * an;
+            L.wcoef = theta / rho;
+            const double rnorm = L.phibar;
+            const double arnorm = L.phibar * an * fabs(cs);
+            L.done = arnorm <= P.inner_tol * L.fro * rnorm || rnorm <= P.inner_tol * L.beta1 ||
+                     an == 0.0 || bn == 0.0 || it >= P.inner_max;
+            L.alpha = an;
+            if (!L.done) {
+                L.inv_a = 1.0 / an;
+                L.ab = an / bn;
+            }
+        }
+        __syncthreads();
+        if (L.done) return it;
     }
 }
 
@@ -101,10 +183,9 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
     for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
-        if (hasU && i < P.m) {
-            const long long e1 = P.srp[i + 1];
-            for (long long e = P.srp[i] + G.sl; e < e1; e += G.L) s = fma(P.sav[e], P.yy[P.sci[e]], s);
-        }
+        if (hasU && i < P.m)
+            s = lane_dot<false>(P.srp[i] + G.sl, P.srp[i + 1], G.L, P.sci, P.sav,
+                                [&](int p) { return P.yy[p]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
             const double zi = P.z[i] - s;
@@ -129,17 +210,24 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
     }
 }
 
-#define RGD_SYNC()                                 \
-    do {                                           \
-        if (!grid_barrier(P.ctrl)) return;         \
+#define RGD_SYNC(dm, dx, im)                                 \
+    do {                                                     \
+        if (!sync_collect(P, S, (dm), (dx), (im))) return;   \
     } while (0)
 
 __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
     __shared__ SolveSmem S;
     BlockScratch &bs = S.bs;
+    OuterState &O = S.o;
     const int nct = gridDim.x;
     const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
     const unsigned long long t_start = globaltimer_ns();
+    if (threadIdx.x == 0) {
+        S.epoch = 0;
+        S.acc = Acc{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        S.tlast = t_start;
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) S.tphase[i] = 0;
+    }
 
     // ---- x_0 = 0, z_0 = b, t_0 = b - A x_0 = b, dx = 0
     {
@@ -163,15 +251,21 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             P.pi[I_BAD_R * nct + blockIdx.x] = bad;
         }
     }
-    RGD_SYNC();
-    const double bb = reduce_partials_sum(P.pd + D_BB * nct, nct, bs);
-    const long long badb = reduce_partials_isum(P.pi + I_BAD_R * nct, nct, bs);
-    Acc acc;
-    if (badb != 0 || !isfinite(bb)) {
-        finish(P, RGDBEK_ERR_NONFINITE, 0, NAN, NAN, acc);
+    RGD_SYNC(DS(D_BB), 0, DS(I_BAD_R));
+    mark(S, PH_SETUP);
+    if (threadIdx.x == 0) {
+        O.bb = S.red_d[D_BB];
+        O.tt = O.bb;  // t_0 = z_0 = b
+        O.zz = O.bb;
+        O.atb2 = 0.0;
+        O.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(O.bb)) ? RGDBEK_ERR_NONFINITE
+                                                                : kStatusRunning;
+    }
+    __syncthreads();
+    if (O.verdict != kStatusRunning) {
+        finish(P, O.verdict, 0, NAN, NAN, S);
         return;
     }
-    double tt = bb, zz = bb, atb2 = 0.0;
     long long tr_off = 0;
     bool tr_full = P.tr_lists == nullptr;
 
@@ -181,27 +275,24 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             (double)(globaltimer_ns() - t_start) > P.time_budget_ns)
             P.ctrl->stop_req = 1;
         phase_col(P, bs);
-        RGD_SYNC();
-        const double emax_c = reduce_partials_max(P.pd + D_EMAX_C * nct, nct, bs);
-        const double hh = reduce_partials_sum(P.pd + D_HH * nct, nct, bs);
-        const long long badc = reduce_partials_isum(P.pi + I_BAD_C * nct, nct, bs);
-        if (k == 0) atb2 = hh;
-        const double rel = bb > 0.0 ? sqrt(tt / bb) : 0.0;
-        const double nrm = atb2 > 0.0 ? sqrt(hh / atb2) : 0.0;
-        if (badc != 0 || !isfinite(hh) || !isfinite(tt)) {
-            finish(P, RGDBEK_ERR_NONFINITE, k, rel, nrm, acc);
-            return;
+        RGD_SYNC(DS(D_EMAX_C) | DS(D_HH), DS(D_EMAX_C), DS(I_BAD_C));
+        mark(S, PH_COL);
+        if (threadIdx.x == 0) {
+            const double hh = S.red_d[D_HH];
+            O.emax_c = S.red_d[D_EMAX_C];
+            if (k == 0) O.atb2 = hh;
+            O.rel = O.bb > 0.0 ? sqrt(O.tt / O.bb) : 0.0;
+            O.nrm = O.atb2 > 0.0 ? sqrt(hh / O.atb2) : 0.0;
+            int v = kStatusRunning;
+            if (S.red_i[I_BAD_C] != 0 || !isfinite(hh) || !isfinite(O.tt)) v = RGDBEK_ERR_NONFINITE;
+            else if (stop_rule_holds(P.stop_rule, P.tol, O.rel, O.nrm)) v = RGDBEK_OK;
+            else if (k >= P.max_iter) v = RGDBEK_NOT_CONVERGED;
+            else if (ld_volatile_i32(&P.ctrl->stop_req)) v = RGDBEK_ERR_TIMEOUT;
+            O.verdict = v;
         }
-        if (stop_rule_holds(P.stop_rule, P.tol, rel, nrm)) {
-            finish(P, RGDBEK_OK, k, rel, nrm, acc);
-            return;
-        }
-        if (k >= P.max_iter) {
-            finish(P, RGDBEK_NOT_CONVERGED, k, rel, nrm, acc);
-            return;
-        }
-        if (ld_volatile_i32(&P.ctrl->stop_req)) {
-            finish(P, RGDBEK_ERR_TIMEOUT, k, rel, nrm, acc);
+        __syncthreads();
+        if (O.verdict != kStatusRunning) {
+            finish(P, O.verdict, k, O.rel, O.nrm, S);
             return;
         }
 
@@ -209,50 +300,61 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
         long long nU = 0, nnzU = 0;
         int stepsU = 0, Lsub_u = 1;
         bool rec_u = !tr_full;
-        if (emax_c > 0.0) {
-            phase_quantize(P, P.epsc, P.n, emax_c, greedy, P.eta_col, bs);
-            RGD_SYNC();
+        if (O.emax_c > 0.0) {
+            phase_quantize(P, P.epsc, P.n, O.emax_c, greedy, P.eta_col, bs);
+            RGD_SYNC(0, 0, 0);
             if (!greedy) {
                 phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
-                RGD_SYNC();
+                RGD_SYNC(0, 0, 0);
             }
             phase_compact_count(P, P.n, P.cn2, P.g, bs);
-            RGD_SYNC();
-            const double fro2 = reduce_partials_sum(P.pd + D_FRO * nct, nct, bs);
-            const double gu2 = reduce_partials_sum(P.pd + D_EXTRA * nct, nct, bs);
+            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
+            if (threadIdx.x == 0) {
+                // LSQR start on A_U with c = z_k: beta1 = ||z_k||, alpha1 = ||A_U^T z_k|| / beta1
+                O.fro2 = S.red_d[D_FRO];
+                O.beta1 = sqrt(O.zz);
+                O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
+                O.alpha1 = sqrt(S.red_d[D_EXTRA]) * O.inv_beta1;
+            }
             nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
-            RGD_SYNC();
+            RGD_SYNC(0, 0, 0);
+            mark(S, PH_COL_SEL);
             const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
             phase_extract_count(P, Arows, P.colpos, bs);
-            RGD_SYNC();
-            const double beta1 = sqrt(zz);
-            const double alpha1 = beta1 > 0.0 ? sqrt(gu2) / beta1 : 0.0;
+            RGD_SYNC(0, 0, 0);
             rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
+            const double inv_beta1 = O.inv_beta1;
             for (long long p = gthread(); p < nU; p += nthreads()) {
                 const int j = P.ulist[p];
-                P.vv[p] = beta1 > 0.0 ? P.g[j] / beta1 : 0.0;  // v~_1 = A_U^T z_k / beta1
+                P.vv[p] = P.g[j] * inv_beta1;  // v~_1 = A_U^T z_k / beta1
                 P.yy[p] = 0.0;
                 if (rec_u) P.tr_lists[tr_off + p] = j;
             }
             nnzU = phase_extract_write(P, Arows, P.colpos, P.srp, P.sci, P.sav, S.tab, bs);
-            RGD_SYNC();
-            Lsub_u = pick_lanes((double)nnzU / (double)P.m);
-            if (beta1 > 0.0 && alpha1 > 0.0) {
+            RGD_SYNC(0, 0, 0);
+            mark(S, PH_COL_EXT);
+            Lsub_u = pick_lanes_int(nnzU, P.m);
+            if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const Side rows{P.srp, P.sci, P.sav, nullptr, P.m, Lsub_u, false};
                 const Side cols{P.cp, P.ri, P.cv, P.ulist, nU, P.tpc, true};
-                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, alpha1, beta1, sqrt(fro2), S);
+                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, O.alpha1, O.beta1, O.fro2, S);
                 if (stepsU < 0) return;
+                mark(S, PH_COL_LSQR);
             }
         }
 
         // ---- z_{k+1}, row residual r = b - z_{k+1} - A x_k, row weights
         phase_zupdate(P, nU > 0, Lsub_u, bs);
-        RGD_SYNC();
-        const double emax_r = reduce_partials_max(P.pd + D_EMAX_R * nct, nct, bs);
-        zz = reduce_partials_sum(P.pd + D_ZZ * nct, nct, bs);
-        const long long badr = reduce_partials_isum(P.pi + I_BAD_R * nct, nct, bs);
-        if (badr != 0) {
-            finish(P, RGDBEK_ERR_NONFINITE, k, rel, nrm, acc);
+        RGD_SYNC(DS(D_EMAX_R) | DS(D_ZZ), DS(D_EMAX_R), DS(I_BAD_R));
+        mark(S, PH_ZUPD);
+        if (threadIdx.x == 0) {
+            O.emax_r = S.red_d[D_EMAX_R];
+            O.zz = S.red_d[D_ZZ];
+            O.verdict = S.red_i[I_BAD_R] != 0 ? RGDBEK_ERR_NONFINITE : kStatusRunning;
+        }
+        __syncthreads();
+        if (O.verdict != kStatusRunning) {
+            finish(P, O.verdict, k, O.rel, O.nrm, S);
             return;
         }
 
@@ -260,22 +362,27 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
         long long nJ = 0, nnzJ = 0;
         int stepsJ = 0;
         bool rec_j = false;
-        if (emax_r > 0.0) {
-            phase_quantize(P, P.epsr, P.m, emax_r, greedy, P.eta_row, bs);
-            RGD_SYNC();
+        if (O.emax_r > 0.0) {
+            phase_quantize(P, P.epsr, P.m, O.emax_r, greedy, P.eta_row, bs);
+            RGD_SYNC(0, 0, 0);
             if (!greedy) {
                 phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
-                RGD_SYNC();
+                RGD_SYNC(0, 0, 0);
             }
             phase_compact_count(P, P.m, P.rn2, P.r, bs);
-            RGD_SYNC();
-            const double fro2 = reduce_partials_sum(P.pd + D_FRO * nct, nct, bs);
-            const double rj2 = reduce_partials_sum(P.pd + D_EXTRA * nct, nct, bs);
+            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
+            if (threadIdx.x == 0) {
+                // LSQR start on A^J with c = r_J: beta1 = ||r_J||
+                O.fro2 = S.red_d[D_FRO];
+                O.beta1 = sqrt(S.red_d[D_EXTRA]);
+                O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
+            }
             nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
-            RGD_SYNC();
+            RGD_SYNC(0, 0, 0);
+            mark(S, PH_ROW_SEL);
             const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
             phase_extract_count(P, Acols, P.rowpos, bs);
-            RGD_SYNC();
+            RGD_SYNC(0, 0, 0);
             rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
             for (long long p = gthread(); p < nJ; p += nthreads()) {
                 const int i = P.jlist[p];
@@ -283,32 +390,38 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 if (rec_j) P.tr_lists[tr_off + nU + p] = i;
             }
             nnzJ = phase_extract_write(P, Acols, P.rowpos, P.scp, P.sri, P.scv, S.tab, bs);
-            RGD_SYNC();
-            const double beta1 = sqrt(rj2);
-            if (beta1 > 0.0) {
-                const int Lsub = pick_lanes((double)nnzJ / (double)P.n);
+            RGD_SYNC(0, 0, 0);
+            mark(S, PH_ROW_EXT);
+            if (O.beta1 > 0.0) {
+                const int Lsub = pick_lanes_int(nnzJ, P.n);
                 const Side cols{P.scp, P.sri, P.scv, nullptr, P.n, Lsub, false};
                 const Side rows{P.rp, P.ci, P.av, P.jlist, nJ, P.tpr, true};
-                lsqr_cols(P, cols, P.uu, P.vv, nullptr, nullptr, 1.0, beta1, 0.0, true, bs);
-                RGD_SYNC();
-                const double alpha1 = sqrt(reduce_partials_sum(P.pd + D_VV * nct, nct, bs));
-                if (alpha1 > 0.0) {
-                    stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, alpha1, beta1, sqrt(fro2), S);
+                lsqr_cols(P, cols, P.uu, P.vv, nullptr, nullptr, O.inv_beta1, 0.0, 0.0, true, true,
+                          bs);
+                RGD_SYNC(DS(D_VV), 0, 0);
+                if (threadIdx.x == 0) O.alpha1 = sqrt(S.red_d[D_VV]);
+                __syncthreads();
+                if (O.alpha1 > 0.0) {
+                    stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, O.alpha1, O.beta1, O.fro2, S);
                     if (stepsJ < 0) return;
                 }
+                mark(S, PH_ROW_LSQR);
             }
         }
 
-        acc.inner_u += stepsU;
-        acc.inner_j += stepsJ;
-        acc.sum_nu += nU;
-        acc.sum_nj += nJ;
-        acc.sum_nnzu += nnzU;
-        acc.sum_nnzj += nnzJ;
-        acc.lsqr_nnzu += (long long)stepsU * nnzU;
-        acc.lsqr_nnzj += (long long)stepsJ * nnzJ;
-        acc.lsqr_nu += (long long)stepsU * nU;
-        acc.lsqr_nj += (long long)stepsJ * nJ;
+        if (threadIdx.x == 0) {
+            Acc &acc = S.acc;
+            acc.inner_u += stepsU;
+            acc.inner_j += stepsJ;
+            acc.sum_nu += nU;
+            acc.sum_nj += nJ;
+            acc.sum_nnzu += nnzU;
+            acc.sum_nnzj += nnzJ;
+            acc.lsqr_nnzu += (long long)stepsU * nnzU;
+            acc.lsqr_nnzj += (long long)stepsJ * nnzJ;
+            acc.lsqr_nu += (long long)stepsU * nU;
+            acc.lsqr_nj += (long long)stepsJ * nJ;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0 && P.tr_counts && k < P.tr_count_cap) {
             P.tr_counts[4 * k + 0] = nU;
             P.tr_counts[4 * k + 1] = nJ;
@@ -322,14 +435,15 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
         }
         if (nU == 0 && nJ == 0) {
             // both blocks empty: x can no longer change
-            finish(P, RGDBEK_OK, k, rel, nrm, acc);
+            finish(P, RGDBEK_OK, k, O.rel, O.nrm, S);
             return;
         }
 
         // ---- t_{k+1} = b - A x_{k+1}
         phase_residual(P, bs);
-        RGD_SYNC();
-        tt = reduce_partials_sum(P.pd + D_TT * nct, nct, bs);
+        RGD_SYNC(DS(D_TT), 0, 0);
+        mark(S, PH_RESID);
+        if (threadIdx.x == 0) O.tt = S.red_d[D_TT];
     }
 }
 
@@ -377,6 +491,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
     __shared__ SolveSmem S;
     BlockScratch &bs = S.bs;
     const int nct = gridDim.x;
+    if (threadIdx.x == 0) S.epoch = 0;
     double emax = 0.0;
     long long bad = 0;
     for (long long j = gthread(); j < len; j += nthreads()) {
@@ -390,19 +505,19 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
         P.pd[D_EMAX_C * nct + blockIdx.x] = emax;
         P.pi[I_BAD_C * nct + blockIdx.x] = bad;
     }
-    RGD_SYNC();
-    emax = reduce_partials_max(P.pd + D_EMAX_C * nct, nct, bs);
-    bad = reduce_partials_isum(P.pi + I_BAD_C * nct, nct, bs);
+    RGD_SYNC(DS(D_EMAX_C), DS(D_EMAX_C), DS(I_BAD_C));
+    emax = S.red_d[D_EMAX_C];
+    bad = S.red_i[I_BAD_C];
     long long count = 0;
     if (bad == 0 && emax > 0.0) {
         phase_quantize(P, eps, len, emax, greedy, eta, bs);
-        RGD_SYNC();
+        RGD_SYNC(0, 0, 0);
         if (!greedy) {
             phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
-            RGD_SYNC();
+            RGD_SYNC(0, 0, 0);
         }
         phase_compact_count(P, len, eps, eps, bs);
-        RGD_SYNC();
+        RGD_SYNC(0, 0, 0);
         count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -413,16 +528,17 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
 }
 
 #undef RGD_SYNC
+#undef DS
 
 __global__ void reset_ctrl_kernel(Ctrl *c) {
     c->bar_count = 0;
-    c->bar_gen = 0;
     c->abort = 0;
     c->status = kStatusRunning;
     c->stop_req = 0;
     c->iters = c->inner_u = c->inner_j = 0;
     c->sum_nu = c->sum_nj = c->sum_nnzu = c->sum_nnzj = 0;
     c->lsqr_nnzu = c->lsqr_nnzj = c->lsqr_nu = c->lsqr_nj = 0;
+    for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) c->phase_ns[i] = 0;
     c->rel_res = c->normal_res = c->rse = 0.0;
     c->sample_count = 0;
     c->emax_out = 0.0;

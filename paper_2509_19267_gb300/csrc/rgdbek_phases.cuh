@@ -98,6 +98,88 @@ __device__ __forceinline__ long long nthreads() {
     return (long long)gridDim.x * blockDim.x;
 }
 
+// Loads through the read-only path (RO) for arrays that never change during
+// a kernel, ordinary loads otherwise.
+template <bool RO, typename T>
+__device__ __forceinline__ T ldx(const T *p) {
+    if constexpr (RO) return __ldg(p);
+    else return *p;
+}
+
+// This lane's share of sum_e val[e] * f(idx[e]) over e = e, e + L, e + 2L, ...
+// below e1, accumulated in exactly that order.  Four entries are handled per
+// trip with all their loads issued before the multiply-adds, so four
+// independent index/value loads and four gathers are in flight per lane.
+template <bool RO, typename F>
+__device__ __forceinline__ double lane_dot(long long e, long long e1, long long L, const int *idx,
+                                           const double *val, F f) {
+    double s = 0.0;
+    for (; e < e1; e += 4 * L) {
+        const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
+        const int i0 = ldx<RO>(idx + e);
+        const int i1 = v1 ? ldx<RO>(idx + e + L) : 0;
+        const int i2 = v2 ? ldx<RO>(idx + e + 2 * L) : 0;
+        const int i3 = v3 ? ldx<RO>(idx + e + 3 * L) : 0;
+        const double a0 = ldx<RO>(val + e);
+        const double a1 = v1 ? ldx<RO>(val + e + L) : 0.0;
+        const double a2 = v2 ? ldx<RO>(val + e + 2 * L) : 0.0;
+        const double a3 = v3 ? ldx<RO>(val + e + 3 * L) : 0.0;
+        const double x0 = f(i0);
+        const double x1 = v1 ? f(i1) : 0.0;
+        const double x2 = v2 ? f(i2) : 0.0;
+        const double x3 = v3 ? f(i3) : 0.0;
+        s = fma(a0, x0, s);
+        if (v1) s = fma(a1, x1, s);
+        if (v2) s = fma(a2, x2, s);
+        if (v3) s = fma(a3, x3, s);
+    }
+    return s;
+}
+
+// Two dot products sharing the index/value loads (A^T z and A^T t).
+template <typename F, typename G>
+__device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L, const int *idx,
+                                          const double *val, F f, G g, double &sf, double &sg) {
+    for (; e < e1; e += 4 * L) {
+        const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
+        const int i0 = __ldg(idx + e);
+        const int i1 = v1 ? __ldg(idx + e + L) : 0;
+        const int i2 = v2 ? __ldg(idx + e + 2 * L) : 0;
+        const int i3 = v3 ? __ldg(idx + e + 3 * L) : 0;
+        const double a0 = __ldg(val + e);
+        const double a1 = v1 ? __ldg(val + e + L) : 0.0;
+        const double a2 = v2 ? __ldg(val + e + 2 * L) : 0.0;
+        const double a3 = v3 ? __ldg(val + e + 3 * L) : 0.0;
+        const double x0 = f(i0), y0 = g(i0);
+        const double x1 = v1 ? f(i1) : 0.0, y1 = v1 ? g(i1) : 0.0;
+        const double x2 = v2 ? f(i2) : 0.0, y2 = v2 ? g(i2) : 0.0;
+        const double x3 = v3 ? f(i3) : 0.0, y3 = v3 ? g(i3) : 0.0;
+        sf = fma(a0, x0, sf);
+        sg = fma(a0, y0, sg);
+        if (v1) { sf = fma(a1, x1, sf); sg = fma(a1, y1, sg); }
+        if (v2) { sf = fma(a2, x2, sf); sg = fma(a2, y2, sg); }
+        if (v3) { sf = fma(a3, x3, sf); sg = fma(a3, y3, sg); }
+    }
+}
+
+// Number of entries e = e, e + L, ... below e1 with map[idx[e]] >= 0.
+__device__ __forceinline__ int lane_count(long long e, long long e1, long long L, const int *idx,
+                                          const int *map) {
+    int c = 0;
+    for (; e < e1; e += 4 * L) {
+        const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
+        const int i0 = __ldg(idx + e);
+        const int i1 = v1 ? __ldg(idx + e + L) : 0;
+        const int i2 = v2 ? __ldg(idx + e + 2 * L) : 0;
+        const int i3 = v3 ? __ldg(idx + e + 3 * L) : 0;
+        c += map[i0] >= 0;
+        if (v1) c += map[i1] >= 0;
+        if (v2) c += map[i2] >= 0;
+        if (v3) c += map[i3] >= 0;
+    }
+    return c;
+}
+
 // ---------------------------------------------------------------------------
 // Full-matrix products
 // ---------------------------------------------------------------------------
@@ -108,11 +190,9 @@ __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, 
     for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
-        if (i < P.m) {
-            const long long e1 = __ldg(P.rp + i + 1);
-            for (long long e = __ldg(P.rp + i) + G.sl; e < e1; e += G.L)
-                s = fma(__ldg(P.av + e), xin[__ldg(P.ci + e)], s);
-        }
+        if (i < P.m)
+            s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
+                               [&](int j) { return xin[j]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) y[i] = s;
     }
@@ -124,11 +204,9 @@ __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, 
     for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
         const long long j = base + G.sub;
         double s = 0.0;
-        if (j < P.n) {
-            const long long e1 = __ldg(P.cp + j + 1);
-            for (long long e = __ldg(P.cp + j) + G.sl; e < e1; e += G.L)
-                s = fma(__ldg(P.cv + e), zin[__ldg(P.ri + e)], s);
-        }
+        if (j < P.n)
+            s = lane_dot<true>(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
+                               [&](int i) { return zin[i]; });
         s = group_sum(s, G.L);
         if (j < P.n && G.sl == 0) gout[j] = s;
     }
@@ -146,15 +224,9 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
     for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
         const long long j = base + G.sub;
         double sg = 0.0, sh = 0.0;
-        if (j < P.n) {
-            const long long e1 = __ldg(P.cp + j + 1);
-            for (long long e = __ldg(P.cp + j) + G.sl; e < e1; e += G.L) {
-                const double a = __ldg(P.cv + e);
-                const int i = __ldg(P.ri + e);
-                sg = fma(a, P.z[i], sg);
-                sh = fma(a, P.t[i], sh);
-            }
-        }
+        if (j < P.n)
+            lane_dot2(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
+                      [&](int i) { return P.z[i]; }, [&](int i) { return P.t[i]; }, sg, sh);
         sg = group_sum(sg, G.L);
         sh = group_sum(sh, G.L);
         if (j < P.n && G.sl == 0) {
@@ -186,13 +258,9 @@ __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs
     for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
-        if (i < P.m) {
-            const long long e1 = __ldg(P.rp + i + 1);
-            for (long long e = __ldg(P.rp + i) + G.sl; e < e1; e += G.L) {
-                const int j = __ldg(P.ci + e);
-                s = fma(__ldg(P.av + e), P.x[j] + P.dx[j], s);
-            }
-        }
+        if (i < P.m)
+            s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
+                               [&](int j) { return P.x[j] + P.dx[j]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
             const double ti = __ldg(P.b + i) - s;
@@ -389,11 +457,7 @@ __device__ __forceinline__ void phase_extract_count(const Params &P, const Lines
     long long cnt = 0;
     for (long long tb = C.lo; tb < C.hi; tb += per_tile) {
         const long long i = tb + (long long)(threadIdx.x >> 5) * G.rpw + G.sub;
-        if (i < C.hi) {
-            const long long e1 = __ldg(A.ptr + i + 1);
-            for (long long e = __ldg(A.ptr + i) + G.sl; e < e1; e += G.L)
-                cnt += map[__ldg(A.idx + e)] >= 0;
-        }
+        if (i < C.hi) cnt += lane_count(__ldg(A.ptr + i) + G.sl, __ldg(A.ptr + i + 1), G.L, A.idx, map);
     }
     cnt = block_sum(cnt, bs);
     if (threadIdx.x == 0) P.pi[I_NNZ * gridDim.x + blockIdx.x] = cnt;
@@ -415,8 +479,7 @@ __device__ __forceinline__ long long phase_extract_write(const Params &P, const 
         const bool valid = i < C.hi;
         const long long e0 = valid ? __ldg(A.ptr + i) : 0;
         const long long e1 = valid ? __ldg(A.ptr + i + 1) : 0;
-        int c = 0;
-        for (long long e = e0 + G.sl; e < e1; e += G.L) c += map[__ldg(A.idx + e)] >= 0;
+        int c = lane_count(e0 + G.sl, e1, G.L, A.idx, map);
         c = group_sum(c, G.L);
         long long tot;
         const long long ex = block_excl_scan<long long>((valid && G.sl == 0) ? c : 0, bs, &tot);
@@ -466,25 +529,20 @@ struct Side {
 // this lane's share of <line, vec>; the caller sums it over the group
 __device__ __forceinline__ double side_partial(const Side &S, long long line, const Grp &G,
                                                const double *vec) {
-    double s = 0.0;
-    if (S.ro) {
-        const long long e1 = __ldg(S.ptr + line + 1);
-        for (long long e = __ldg(S.ptr + line) + G.sl; e < e1; e += G.L)
-            s = fma(__ldg(S.val + e), vec[__ldg(S.idx + e)], s);
-    } else {
-        const long long e1 = S.ptr[line + 1];
-        for (long long e = S.ptr[line] + G.sl; e < e1; e += G.L) s = fma(S.val[e], vec[S.idx[e]], s);
-    }
-    return s;
+    const auto gat = [&](int i) { return vec[i]; };
+    if (S.ro)
+        return lane_dot<true>(__ldg(S.ptr + line) + G.sl, __ldg(S.ptr + line + 1), G.L, S.idx,
+                              S.val, gat);
+    return lane_dot<false>(S.ptr[line] + G.sl, S.ptr[line + 1], G.L, S.idx, S.val, gat);
 }
 
 // rows phase; uold is u~ of the previous step (the right-hand side c on the
-// first step).  Partial: ||u~_new||^2.
+// first step).  inv_a = 1/alpha, ab = alpha/beta (precomputed once per CTA).
+// Partial: ||u~_new||^2.
 __device__ __forceinline__ void lsqr_rows(const Params &P, const Side &R, long long nv,
                                           const double *uold, double *unew, const double *vv,
-                                          double *ww, double alpha, double beta, bool first,
+                                          double *ww, double inv_a, double ab, bool first,
                                           double wcoef, BlockScratch &bs) {
-    const double inv_a = 1.0 / alpha, ab = alpha / beta;
     for (long long c = gthread(); c < nv; c += nthreads()) {
         const double vn = vv[c] * inv_a;
         ww[c] = first ? vn : vn - wcoef * ww[c];
@@ -506,18 +564,16 @@ __device__ __forceinline__ void lsqr_rows(const Params &P, const Side &R, long l
     if (threadIdx.x == 0) P.pd[D_UU * gridDim.x + blockIdx.x] = uu;
 }
 
-// cols phase.  With beta_new == 0 only the y update runs.  init: the first
+// cols phase.  mv = (beta_new > 0): with beta_new == 0 only the y update
+// runs.  inv_b = 1/beta_new, ba = beta_new/alpha.  init: the first
 // v~ = B^T u~ / beta of the row block (no previous v~, no y update).
 // Partial: ||v~_new||^2.
 __device__ __forceinline__ void lsqr_cols(const Params &P, const Side &Cs, const double *uu,
-                                          double *vv, const double *ww, double *yy, double alpha,
-                                          double beta_new, double phi_rho, bool init,
+                                          double *vv, const double *ww, double *yy, double inv_b,
+                                          double ba, double phi_rho, bool mv, bool init,
                                           BlockScratch &bs) {
     const Grp G(Cs.L);
     double acc = 0.0;
-    const bool mv = beta_new > 0.0;
-    const double inv_b = mv ? 1.0 / beta_new : 0.0;
-    const double ba = init ? 0.0 : beta_new / alpha;
     for (long long base = gwarp() * G.rpw; base < Cs.n; base += nwarps() * G.rpw) {
         const long long c = base + G.sub;
         double s = 0.0;
@@ -535,14 +591,6 @@ __device__ __forceinline__ void lsqr_cols(const Params &P, const Side &Cs, const
     acc = block_sum(acc, bs);
     if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
 }
-
-// Scalar recurrences of LSQR, identical in every thread of every CTA.
-struct LsqrScalars {
-    double alpha, beta, rhobar, phibar, beta1, fro, wcoef;
-    double cs, sn, rho;
-    int steps;
-    bool done;
-};
 
 __device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {
     switch (rule) {
