@@ -30,6 +30,7 @@ struct rgdbek_s {
     long long *srp, *scp;
     int *sci, *sri;
     double *sav, *scv;
+    double *dots, *dots2;
     double *pd;
     long long *pi;
     Ctrl *ctrl;
@@ -91,6 +92,8 @@ void carve(rgdbek_s *h, Layout &L) {
     h->scp = L.take<long long>(n + 1);
     h->sri = L.take<int>(nnz);
     h->scv = L.take<double>(nnz);
+    h->dots = L.take<double>(mx);
+    h->dots2 = L.take<double>(mx);
     h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
     h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
     h->ctrl = L.take<Ctrl>(1);
@@ -168,6 +171,8 @@ Params make_params(const rgdbek_s *h) {
     P.scp = h->scp;
     P.sri = h->sri;
     P.scv = h->scv;
+    P.dots = h->dots;
+    P.dots2 = h->dots2;
     P.pd = h->pd;
     P.pi = h->pi;
     P.ctrl = h->ctrl;
@@ -185,6 +190,7 @@ Params make_params(const rgdbek_s *h) {
     P.time_budget_ns = h->opt.time_budget_s * 1e9;
     P.tpr = h->tpr;
     P.tpc = h->tpc;
+    P.dsmem_bytes = kSolveDsmemBytes;
     return P;
 }
 

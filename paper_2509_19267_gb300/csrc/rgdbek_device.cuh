@@ -44,6 +44,7 @@ enum ISlot {
     I_TOT,        // chunk total of quantised weights
     I_CNT,        // chunk count of flagged indices
     I_NNZ,        // chunk count of extracted nonzeros
+    I_LEN,        // chunk sum of the lengths of the flagged lines (compact copies)
     I_NSLOTS
 };
 

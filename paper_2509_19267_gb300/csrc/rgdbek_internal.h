@@ -10,6 +10,8 @@
 namespace rgd {
 
 constexpr int kSolveMaxThreads = 1024;  // launch bound of the persistent kernels
+// dynamic shared memory of a solve CTA: its chunk of the inner-solve block
+constexpr int kSolveDsmemBytes = 96 * 1024;
 
 // control block to its pre-launch state (status = kStatusRunning)
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);

@@ -50,6 +50,7 @@ struct SolveSmem {
     BlockScratch bs;
     Acc acc;
     long long tab[kMaxGrid];
+    long long tab2[kMaxGrid];
     double red_d[D_NSLOTS];                          // reduced partials of the last barrier
     long long red_i[I_NSLOTS];
     LsqrState lsqr;                                  // LSQR scalars (written by thread 0)
@@ -108,68 +109,286 @@ __device__ __forceinline__ void finish(const Params &P, int status, long long k,
     }
 }
 
-// LSQR on the block given by its row side R (u-space lines) and column side
-// Cs (v-space lines), from y = 0.  c0 = u~_1 (the right-hand side c), beta =
-// ||c||, alpha = ||B^T c|| / beta, with v~_1 already in P.vv.  The solution
-// accumulates into y (zero on entry); fro2 = ||B||_F^2.  Returns the number
-// of steps, or -1 if a grid barrier was abandoned.
-__device__ __forceinline__ int run_lsqr(const Params &P, const Side &R, const Side &Cs,
-                                        const double *c0, double *y, double alpha, double beta,
-                                        double fro2, SolveSmem &S) {
+// ---------------------------------------------------------------------------
+// LSQR (Paige & Saunders 1982) on a block B, the inner solver of Remark 3.1.
+//
+// B is given by its two sides in contiguous line order: R, the lines of B
+// (u-space), and C, the lines of B^T (v-space).  CTA b owns the contiguous
+// chunk b of R's lines and of C's lines for the whole inner solve; at the
+// start it copies its chunks (line pointers, indices, values) and its slices
+// of u~ (previous value), v~, w and y into shared memory, so that each phase
+// reads the block from shared memory and only gathers the other side's
+// vector from L2.  A chunk that does not fit stays in global memory.
+//
+// Vectors are kept unnormalised, u~ = beta u and v~ = alpha v, and each step
+// is two grid phases:
+//   rows:  w = v~/alpha - (theta/rho_prev) w   (own columns; the w update of
+//          the previous step), u~_new = B v~ / alpha - (alpha/beta) u~
+//   cols:  v~_new = B^T u~_new / beta_new - (beta_new/alpha) v~,
+//          y += (phi/rho) w
+// ---------------------------------------------------------------------------
+struct SideC {
+    const long long *ptr;  // line pointers [0, n]
+    const int *idx;        // indices into the other space
+    const double *val;
+    long long n;           // lines
+    int L;                 // lanes per line
+};
+
+// this CTA's chunk of a side: line li (local) spans ptr[li] .. ptr[li+1] of
+// idx / val (shared memory, or the global arrays with absolute pointers)
+struct CtaSide {
+    const long long *ptr;
+    const int *idx;
+    const double *val;
+    int nl;
+    long long lo;
+    int L;
+};
+
+// bump allocation in dynamic shared memory (8-byte granules)
+struct SmemArena {
+    unsigned char *base;
+    long long left, used;
+    template <typename T>
+    __device__ __forceinline__ T *take(long long count) {
+        const long long bytes = ((count * (long long)sizeof(T)) + 15) & ~15ll;
+        if (bytes > left) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        left -= bytes;
+        return p;
+    }
+};
+
+__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A) {
+    const Chunk C(S.n, blockIdx.x, gridDim.x);
+    CtaSide out;
+    out.nl = (int)(C.hi - C.lo);
+    out.lo = C.lo;
+    out.L = S.L;
+    const long long b0 = S.ptr[C.lo], ne = S.ptr[C.hi] - b0;
+    const SmemArena save = A;
+    long long *ps = A.take<long long>(out.nl + 1);
+    int *is = ps ? A.take<int>(ne) : nullptr;
+    double *vs = is ? A.take<double>(ne) : nullptr;
+    if (!vs) {
+        A = save;
+        out.ptr = S.ptr + C.lo;
+        out.idx = S.idx;
+        out.val = S.val;
+        return out;
+    }
+    for (int i = threadIdx.x; i <= out.nl; i += blockDim.x) ps[i] = S.ptr[C.lo + i] - b0;
+    for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
+        is[e] = S.idx[b0 + e];
+        vs[e] = S.val[b0 + e];
+    }
+    out.ptr = ps;
+    out.idx = is;
+    out.val = vs;
+    return out;
+}
+
+// Dot products of this CTA's lines with a gathered vector, into dots[li].
+// Warp 0 is left out: it reduces the partials of the previous barrier and
+// computes the LSQR scalars meanwhile.
+__device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, double *dots) {
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) return;
+    const Grp G(C.L);
+    const int per = ((blockDim.x >> 5) - 1) * G.rpw;
+    for (int base = 0; base < C.nl; base += per) {
+        const int li = base + (warp - 1) * G.rpw + G.sub;
+        double s = 0.0;
+        if (li < C.nl)
+            s = lane_dot<false>(C.ptr[li] + G.sl, C.ptr[li + 1], G.L, C.idx, C.val,
+                                [&](int j) { return vec[j]; });
+        s = group_sum(s, G.L);
+        if (li < C.nl && G.sl == 0) dots[li] = s;
+    }
+}
+
+// Warp 0: sum of the per-CTA partials of one slot (fixed order), for lane 0.
+__device__ __forceinline__ double warp0_collect(const double *pd, int slot) {
+    const int nb = gridDim.x;
+    const double *p = pd + slot * nb;
+    double s = 0.0;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
+    return warp_sum(s);
+}
+
+// LSQR from y = 0 on the block (R, C) with right-hand side c0 (u-space,
+// global), beta1 = ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in
+// P.vv and alpha1 is passed; otherwise it is computed first (one more
+// phase).  fro2 = ||B||_F^2.  y_g (v-space, zero on entry) receives the
+// solution.  Returns the number of steps (0 if alpha1 == 0), or -1 if a grid
+// barrier was abandoned.
+//
+// Per phase: grid barrier | warp 0 reduces the partials and updates the
+// scalars while warps 1.. compute the dot products of the CTA's lines |
+// __syncthreads | all threads combine element-wise and form the partial.
+__device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
+                                        const double *c0, double *y_g, bool v_given,
+                                        double alpha1, double beta1, double fro2,
+                                        unsigned char *dsmem, long long dsmem_bytes,
+                                        SolveSmem &S) {
     LsqrState &L = S.lsqr;
+    SmemArena A{dsmem, dsmem_bytes, 0};
+    const Chunk RC(Rs.n, blockIdx.x, gridDim.x), CC(Cs.n, blockIdx.x, gridDim.x);
+    const int nrl = (int)(RC.hi - RC.lo), ncl = (int)(CC.hi - CC.lo);
+    // per-CTA vector slices and dot buffers
+    double *uold = A.take<double>(nrl);
+    double *dr = uold ? A.take<double>(nrl) : nullptr;
+    double *vown = dr ? A.take<double>(ncl) : nullptr;
+    double *wown = vown ? A.take<double>(ncl) : nullptr;
+    double *yown = wown ? A.take<double>(ncl) : nullptr;
+    double *dc = yown ? A.take<double>(ncl) : nullptr;
+    const bool st_smem = dc != nullptr;
+    if (!st_smem) {
+        A = SmemArena{dsmem, dsmem_bytes, 0};
+        uold = nullptr;
+        dr = P.dots + RC.lo;
+        vown = P.vv + CC.lo;
+        wown = P.ww + CC.lo;
+        yown = y_g + CC.lo;
+        dc = P.dots2 + CC.lo;
+    } else {
+        for (int i = threadIdx.x; i < nrl; i += blockDim.x) uold[i] = c0[RC.lo + i];
+        for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
+            vown[i] = v_given ? P.vv[CC.lo + i] : 0.0;
+            yown[i] = 0.0;
+        }
+    }
+    const CtaSide R = cache_side(Rs, A);
+    const CtaSide C = cache_side(Cs, A);
     if (threadIdx.x == 0) {
-        L.alpha = alpha;
-        L.beta = beta;
-        L.rhobar = alpha;
-        L.phibar = beta;
-        L.beta1 = beta;
-        L.fro = sqrt(fro2);
-        L.inv_a = 1.0 / alpha;
-        L.ab = alpha / beta;
-        L.wcoef = 0.0;
+        L.inv_b = 1.0 / beta1;
         L.done = 0;
     }
     __syncthreads();
-    for (int it = 1;; ++it) {
-        lsqr_rows(P, R, Cs.n, it == 1 ? c0 : P.uu, P.uu, P.vv, P.ww, L.inv_a, L.ab, it == 1,
-                  L.wcoef, S.bs);
-        if (!sync_collect(P, S, DS(D_UU), 0, 0)) return -1;
-        if (threadIdx.x == 0) {
-            const double bn = sqrt(S.red_d[D_UU]);
-            const double rho = sqrt(L.rhobar * L.rhobar + bn * bn);
-            const double cs = L.rhobar / rho, sn = bn / rho;
-            const double phi = cs * L.phibar;
-            L.phibar = sn * L.phibar;
-            L.mv = bn > 0.0;
-            L.inv_b = bn > 0.0 ? 1.0 / bn : 0.0;
-            L.ba = bn / L.alpha;
-            L.phi_rho = phi / rho;
-            L.beta = bn;
-            L.rho = rho;
-            L.cs = cs;
-            L.sn = sn;
+
+    if (!v_given) {
+        // v~_1 = B^T c0 / beta1 (warp 0 has no scalars to update in this phase)
+        cta_dots(C, c0, dc);
+        __syncthreads();
+        double acc = 0.0;
+        for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
+            const double v = dc[li] * L.inv_b;
+            vown[li] = v;
+            P.vv[CC.lo + li] = v;
+            acc = fma(v, v, acc);
+        }
+        acc = block_sum(acc, S.bs);
+        if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
+        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
+        if (threadIdx.x < 32) {
+            const double vv = warp0_collect(P.pd, D_VV);
+            if (threadIdx.x == 0) L.alpha = sqrt(vv);
         }
         __syncthreads();
-        lsqr_cols(P, Cs, P.uu, P.vv, P.ww, y, L.inv_b, L.ba, L.phi_rho, L.mv != 0, false, S.bs);
-        if (!sync_collect(P, S, DS(D_VV), 0, 0)) return -1;
-        if (threadIdx.x == 0) {
-            const double rho = L.rho, cs = L.cs, sn = L.sn, bn = L.beta;
-            const double an = bn > 0.0 ? sqrt(S.red_d[D_VV]) : 0.0;
-            const double theta = sn * an;
-            L.rhobar = -cs * an;
-            L.wcoef = theta / rho;
-            const double rnorm = L.phibar;
-            const double arnorm = L.phibar * an * fabs(cs);
-            L.done = arnorm <= P.inner_tol * L.fro * rnorm || rnorm <= P.inner_tol * L.beta1 ||
-                     an == 0.0 || bn == 0.0 || it >= P.inner_max;
-            L.alpha = an;
-            if (!L.done) {
-                L.inv_a = 1.0 / an;
-                L.ab = an / bn;
+        alpha1 = L.alpha;
+        if (!(alpha1 > 0.0)) return 0;
+    }
+    if (threadIdx.x == 0) {
+        L.alpha = alpha1;
+        L.beta = beta1;
+        L.rhobar = alpha1;
+        L.phibar = beta1;
+        L.beta1 = beta1;
+        L.fro = sqrt(fro2);
+        L.inv_a = 1.0 / alpha1;
+        L.ab = alpha1 / beta1;
+        L.wcoef = 0.0;
+    }
+    __syncthreads();
+    for (int it = 1;; ++it) {
+        const bool first = it == 1;
+        // ---- rows phase: u~_new = B v~ / alpha - (alpha/beta) u~, w update
+        cta_dots(R, P.vv, dr);
+        if (threadIdx.x < 32 && !first) {
+            // scalars from ||v~||^2 of the previous cols phase
+            const double vv = warp0_collect(P.pd, D_VV);
+            if (threadIdx.x == 0) {
+                const double rho = L.rho, cs = L.cs, sn = L.sn, bn = L.beta;
+                const double an = bn > 0.0 ? sqrt(vv) : 0.0;
+                const double theta = sn * an;
+                L.rhobar = -cs * an;
+                L.wcoef = theta / rho;
+                const double rnorm = L.phibar;
+                const double arnorm = L.phibar * an * fabs(cs);
+                L.done = arnorm <= P.inner_tol * L.fro * rnorm ||
+                         rnorm <= P.inner_tol * L.beta1 || an == 0.0 || bn == 0.0 ||
+                         it - 1 >= P.inner_max;
+                L.alpha = an;
+                if (!L.done) {
+                    L.inv_a = 1.0 / an;
+                    L.ab = an / bn;
+                }
             }
         }
         __syncthreads();
-        if (L.done) return it;
+        if (L.done) return it - 1;
+        {
+            const double inv_a = L.inv_a, ab = L.ab, wcoef = L.wcoef;
+            for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
+                const double vn = vown[li] * inv_a;
+                wown[li] = first ? vn : vn - wcoef * wown[li];
+            }
+            const double *uo = st_smem ? uold : (first ? c0 : P.uu) + RC.lo;
+            double acc = 0.0;
+            for (int li = threadIdx.x; li < nrl; li += blockDim.x) {
+                const double u = dr[li] * inv_a - ab * uo[li];
+                P.uu[RC.lo + li] = u;
+                if (st_smem) uold[li] = u;
+                acc = fma(u, u, acc);
+            }
+            acc = block_sum(acc, S.bs);
+            if (threadIdx.x == 0) P.pd[D_UU * gridDim.x + blockIdx.x] = acc;
+        }
+        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
+
+        // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
+        cta_dots(C, P.uu, dc);
+        if (threadIdx.x < 32) {
+            const double uu = warp0_collect(P.pd, D_UU);
+            if (threadIdx.x == 0) {
+                const double bn = sqrt(uu);
+                const double rho = sqrt(L.rhobar * L.rhobar + bn * bn);
+                const double cs = L.rhobar / rho, sn = bn / rho;
+                const double phi = cs * L.phibar;
+                L.phibar = sn * L.phibar;
+                L.mv = bn > 0.0;
+                L.inv_b = bn > 0.0 ? 1.0 / bn : 0.0;
+                L.ba = bn / L.alpha;
+                L.phi_rho = phi / rho;
+                L.beta = bn;
+                L.rho = rho;
+                L.cs = cs;
+                L.sn = sn;
+            }
+        }
+        __syncthreads();
+        {
+            const double inv_b = L.inv_b, ba = L.ba, phi_rho = L.phi_rho;
+            const bool mv = L.mv != 0;
+            double acc = 0.0;
+            for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
+                if (mv) {
+                    const double v = dc[li] * inv_b - ba * vown[li];
+                    vown[li] = v;
+                    P.vv[CC.lo + li] = v;
+                    acc = fma(v, v, acc);
+                }
+                const double y = fma(phi_rho, wown[li], yown[li]);
+                yown[li] = y;
+                y_g[CC.lo + li] = y;
+            }
+            acc = block_sum(acc, S.bs);
+            if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
+        }
+        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
     }
 }
 
@@ -217,6 +436,7 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
 
 __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
     __shared__ SolveSmem S;
+    extern __shared__ __align__(16) unsigned char dsmem[];
     BlockScratch &bs = S.bs;
     OuterState &O = S.o;
     const int nct = gridDim.x;
@@ -307,7 +527,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.n, P.cn2, P.g, bs);
+            phase_compact_count(P, P.n, P.cn2, P.g, P.cp, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on A_U with c = z_k: beta1 = ||z_k||, alpha1 = ||A_U^T z_k|| / beta1
@@ -316,7 +536,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
                 O.alpha1 = sqrt(S.red_d[D_EXTRA]) * O.inv_beta1;
             }
-            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
+            // U_k, and A_U's columns copied contiguously (the v-space side of LSQR)
+            const LineCopy ucopy{P.cp, P.ri, P.cv, P.scp, P.sri, P.scv};
+            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, &ucopy, S.tab, S.tab2, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_COL_SEL);
             const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
@@ -335,9 +557,10 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             mark(S, PH_COL_EXT);
             Lsub_u = pick_lanes_int(nnzU, P.m);
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
-                const Side rows{P.srp, P.sci, P.sav, nullptr, P.m, Lsub_u, false};
-                const Side cols{P.cp, P.ri, P.cv, P.ulist, nU, P.tpc, true};
-                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, O.alpha1, O.beta1, O.fro2, S);
+                const SideC rows{P.srp, P.sci, P.sav, P.m, Lsub_u};
+                const SideC cols{P.scp, P.sri, P.scv, nU, P.tpc};
+                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, true, O.alpha1, O.beta1, O.fro2, dsmem,
+                                  P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
             }
@@ -369,7 +592,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.m, P.rn2, P.r, bs);
+            phase_compact_count(P, P.m, P.rn2, P.r, P.rp, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on A^J with c = r_J: beta1 = ||r_J||
@@ -377,7 +600,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 O.beta1 = sqrt(S.red_d[D_EXTRA]);
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
             }
-            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
+            // J_k, and A^J's rows copied contiguously (the u-space side of LSQR)
+            const LineCopy jcopy{P.rp, P.ci, P.av, P.srp, P.sci, P.sav};
+            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, &jcopy, S.tab, S.tab2, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
             const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
@@ -393,18 +618,11 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_EXT);
             if (O.beta1 > 0.0) {
-                const int Lsub = pick_lanes_int(nnzJ, P.n);
-                const Side cols{P.scp, P.sri, P.scv, nullptr, P.n, Lsub, false};
-                const Side rows{P.rp, P.ci, P.av, P.jlist, nJ, P.tpr, true};
-                lsqr_cols(P, cols, P.uu, P.vv, nullptr, nullptr, O.inv_beta1, 0.0, 0.0, true, true,
-                          bs);
-                RGD_SYNC(DS(D_VV), 0, 0);
-                if (threadIdx.x == 0) O.alpha1 = sqrt(S.red_d[D_VV]);
-                __syncthreads();
-                if (O.alpha1 > 0.0) {
-                    stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, O.alpha1, O.beta1, O.fro2, S);
-                    if (stepsJ < 0) return;
-                }
+                const SideC rows{P.srp, P.sci, P.sav, nJ, P.tpr};
+                const SideC cols{P.scp, P.sri, P.scv, P.n, pick_lanes_int(nnzJ, P.n)};
+                stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, false, 0.0, O.beta1, O.fro2, dsmem,
+                                  P.dsmem_bytes, S);
+                if (stepsJ < 0) return;
                 mark(S, PH_ROW_LSQR);
             }
         }
@@ -516,9 +734,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
             phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
             RGD_SYNC(0, 0, 0);
         }
-        phase_compact_count(P, len, eps, eps, bs);
+        phase_compact_count(P, len, eps, eps, nullptr, bs);
         RGD_SYNC(0, 0, 0);
-        count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
+        count = phase_compact_write(P, len, P.rowpos, idx, nullptr, S.tab, S.tab2, bs);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctrl->sample_count = bad ? -1 : count;
@@ -556,7 +774,8 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
 cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s) {
     Params p = P;
     void *args[] = {&p};
-    return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args,
+                                       (size_t)P.dsmem_bytes, s);
 }
 
 cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
@@ -588,8 +807,12 @@ cudaError_t launch_weights(const double *v, const double *norm2, long long len, 
 }
 
 int solve_blocks_per_sm(int block) {
+    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSolveDsmemBytes) != cudaSuccess)
+        return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel, block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel, block, kSolveDsmemBytes) !=
+        cudaSuccess)
         return 0;
     return nb;
 }

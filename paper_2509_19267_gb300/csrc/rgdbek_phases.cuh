@@ -50,6 +50,8 @@ struct Params {
     long long *scp;         // A^J as CSC over all n columns, rows renumbered 0..|J|-1
     int *sri;
     double *scv;
+    double *dots, *dots2;   // per-line dot products of the inner solve when a CTA's
+                            // chunk does not fit in shared memory (max(m, n) each)
     double *pd;             // double partials [D_NSLOTS][grid]
     long long *pi;          // int64 partials [I_NSLOTS][grid]
     Ctrl *ctrl;
@@ -64,6 +66,7 @@ struct Params {
     unsigned long long seed, sysid;
     int inner_max, stop_rule, selection;
     int tpr, tpc;           // lanes per row of A (CSR) and per column (CSC)
+    long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
 };
 
 // Lane geometry of a group of L lanes inside a warp.
@@ -357,12 +360,14 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 }
 
 // Count of marked indices in the chunk, and over them the sums of norm2 (the
-// block's squared Frobenius norm) and of vec^2 (for the LSQR start).
+// block's squared Frobenius norm), of vec^2 (for the LSQR start) and, when
+// lptr is given, of the line lengths lptr[j+1] - lptr[j] (for the compact
+// copy of the selected lines).
 __device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
                                                     const double *norm2, const double *vec,
-                                                    BlockScratch &bs) {
+                                                    const long long *lptr, BlockScratch &bs) {
     const Chunk C(len, blockIdx.x, gridDim.x);
-    long long cnt = 0;
+    long long cnt = 0, lsum = 0;
     double fro = 0.0, ext = 0.0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
@@ -372,17 +377,30 @@ __device__ __forceinline__ void phase_compact_count(const Params &P, long long l
             fro += __ldg(norm2 + j);
             const double v = vec[j];
             ext = fma(v, v, ext);
+            if (lptr) lsum += __ldg(lptr + j + 1) - __ldg(lptr + j);
         }
     }
     cnt = block_sum(cnt, bs);
     fro = block_sum(fro, bs);
     ext = block_sum(ext, bs);
+    if (lptr) lsum = block_sum(lsum, bs);
     if (threadIdx.x == 0) {
         P.pi[I_CNT * gridDim.x + blockIdx.x] = cnt;
+        P.pi[I_LEN * gridDim.x + blockIdx.x] = lsum;
         P.pd[D_FRO * gridDim.x + blockIdx.x] = fro;
         P.pd[D_EXTRA * gridDim.x + blockIdx.x] = ext;
     }
 }
+
+// Source lines and destination of a compact copy of the selected lines.
+struct LineCopy {
+    const long long *sptr;
+    const int *sidx;
+    const double *sval;
+    long long *dptr;
+    int *didx;
+    double *dval;
+};
 
 // Exclusive rank of a predicate over the CTA in thread order (ballot/popc per
 // warp, then the warp counts scanned); *total gets the CTA count.
@@ -408,15 +426,20 @@ __device__ __forceinline__ long long block_rank_pred(bool f, BlockScratch &bs, l
 }
 
 // Marked indices -> ascending list; pos[j] = position in the list or -1.
-// Returns the list length.
+// With cp given, the selected lines are also copied, in list order, into a
+// compact CSR-like array (dptr over list positions).  tab and tab2 are
+// kMaxGrid-long smem tables.  Returns the list length.
 __device__ __forceinline__ long long phase_compact_write(const Params &P, long long len, int *pos,
-                                                         int *list, long long *tab,
+                                                         int *list, const LineCopy *cp,
+                                                         long long *tab, long long *tab2,
                                                          BlockScratch &bs) {
     const int nct = gridDim.x;
     partials_prefix(P.pi + I_CNT * nct, nct, tab, bs);
+    if (cp) partials_prefix(P.pi + I_LEN * nct, nct, tab2, bs);
     const long long total = tab[nct - 1];
     const Chunk C(len, blockIdx.x, nct);
     long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
+    long long erun = (cp && blockIdx.x > 0) ? tab2[blockIdx.x - 1] : 0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
         const bool f = j < C.hi && P.flag[j];
@@ -430,8 +453,43 @@ __device__ __forceinline__ long long phase_compact_write(const Params &P, long l
                 pos[j] = -1;
             }
         }
+        if (cp) {
+            long long s0 = 0, s1 = 0;
+            if (f) {
+                s0 = __ldg(cp->sptr + j);
+                s1 = __ldg(cp->sptr + j + 1);
+            }
+            long long etot;
+            const long long eex = block_excl_scan<long long>(s1 - s0, bs, &etot);
+            if (f) {
+                const long long o = erun + eex;
+                cp->dptr[run + ex] = o;
+                long long e = s0;
+                for (; e + 3 < s1; e += 4) {
+                    const int i0 = __ldg(cp->sidx + e), i1 = __ldg(cp->sidx + e + 1);
+                    const int i2 = __ldg(cp->sidx + e + 2), i3 = __ldg(cp->sidx + e + 3);
+                    const double a0 = __ldg(cp->sval + e), a1 = __ldg(cp->sval + e + 1);
+                    const double a2 = __ldg(cp->sval + e + 2), a3 = __ldg(cp->sval + e + 3);
+                    const long long d = o + (e - s0);
+                    cp->didx[d] = i0;
+                    cp->didx[d + 1] = i1;
+                    cp->didx[d + 2] = i2;
+                    cp->didx[d + 3] = i3;
+                    cp->dval[d] = a0;
+                    cp->dval[d + 1] = a1;
+                    cp->dval[d + 2] = a2;
+                    cp->dval[d + 3] = a3;
+                }
+                for (; e < s1; ++e) {
+                    cp->didx[o + (e - s0)] = __ldg(cp->sidx + e);
+                    cp->dval[o + (e - s0)] = __ldg(cp->sval + e);
+                }
+            }
+            erun += etot;
+        }
         run += tot;
     }
+    if (cp && blockIdx.x == 0 && threadIdx.x == 0) cp->dptr[total] = tab2[nct - 1];
     return total;
 }
 
@@ -504,92 +562,6 @@ __device__ __forceinline__ long long phase_extract_write(const Params &P, const 
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) optr[A.n] = total;
     return total;
-}
-
-// ---------------------------------------------------------------------------
-// LSQR (Paige & Saunders 1982) on a block B, the inner solver of Remark 3.1.
-// Vectors are kept unnormalised: u~ = beta u, v~ = alpha v, so each step is
-// two grid phases (one barrier each):
-//   rows:  w = v~/alpha - (theta/rho_prev) w        (the w update of the
-//          previous step), u~_new = B v~ / alpha - (alpha/beta) u~
-//   cols:  v~_new = B^T u~_new / beta_new - (beta_new/alpha) v~,
-//          y += (phi/rho) w
-// `Rows` is the u-space side of B (lines of B), `Cols` the v-space side.
-// ---------------------------------------------------------------------------
-struct Side {
-    const long long *ptr;  // line pointers (indexed by line id)
-    const int *idx;        // indices into the other space
-    const double *val;
-    const int *list;       // line id of line c is list[c] (or c when null)
-    long long n;           // number of lines in this space
-    int L;
-    bool ro;               // ptr/idx/val never written during the solve
-};
-
-// this lane's share of <line, vec>; the caller sums it over the group
-__device__ __forceinline__ double side_partial(const Side &S, long long line, const Grp &G,
-                                               const double *vec) {
-    const auto gat = [&](int i) { return vec[i]; };
-    if (S.ro)
-        return lane_dot<true>(__ldg(S.ptr + line) + G.sl, __ldg(S.ptr + line + 1), G.L, S.idx,
-                              S.val, gat);
-    return lane_dot<false>(S.ptr[line] + G.sl, S.ptr[line + 1], G.L, S.idx, S.val, gat);
-}
-
-// rows phase; uold is u~ of the previous step (the right-hand side c on the
-// first step).  inv_a = 1/alpha, ab = alpha/beta (precomputed once per CTA).
-// Partial: ||u~_new||^2.
-__device__ __forceinline__ void lsqr_rows(const Params &P, const Side &R, long long nv,
-                                          const double *uold, double *unew, const double *vv,
-                                          double *ww, double inv_a, double ab, bool first,
-                                          double wcoef, BlockScratch &bs) {
-    for (long long c = gthread(); c < nv; c += nthreads()) {
-        const double vn = vv[c] * inv_a;
-        ww[c] = first ? vn : vn - wcoef * ww[c];
-    }
-    const Grp G(R.L);
-    double uu = 0.0;
-    for (long long base = gwarp() * G.rpw; base < R.n; base += nwarps() * G.rpw) {
-        const long long c = base + G.sub;
-        double s = 0.0;
-        if (c < R.n) s = side_partial(R, R.list ? R.list[c] : c, G, vv);
-        s = group_sum(s, G.L);
-        if (c < R.n && G.sl == 0) {
-            const double u = s * inv_a - ab * uold[c];
-            unew[c] = u;
-            uu = fma(u, u, uu);
-        }
-    }
-    uu = block_sum(uu, bs);
-    if (threadIdx.x == 0) P.pd[D_UU * gridDim.x + blockIdx.x] = uu;
-}
-
-// cols phase.  mv = (beta_new > 0): with beta_new == 0 only the y update
-// runs.  inv_b = 1/beta_new, ba = beta_new/alpha.  init: the first
-// v~ = B^T u~ / beta of the row block (no previous v~, no y update).
-// Partial: ||v~_new||^2.
-__device__ __forceinline__ void lsqr_cols(const Params &P, const Side &Cs, const double *uu,
-                                          double *vv, const double *ww, double *yy, double inv_b,
-                                          double ba, double phi_rho, bool mv, bool init,
-                                          BlockScratch &bs) {
-    const Grp G(Cs.L);
-    double acc = 0.0;
-    for (long long base = gwarp() * G.rpw; base < Cs.n; base += nwarps() * G.rpw) {
-        const long long c = base + G.sub;
-        double s = 0.0;
-        if (mv && c < Cs.n) s = side_partial(Cs, Cs.list ? Cs.list[c] : c, G, uu);
-        s = group_sum(s, G.L);
-        if (c < Cs.n && G.sl == 0) {
-            if (mv) {
-                const double v = init ? s * inv_b : s * inv_b - ba * vv[c];
-                vv[c] = v;
-                acc = fma(v, v, acc);
-            }
-            if (!init) yy[c] = fma(phi_rho, ww[c], yy[c]);
-        }
-    }
-    acc = block_sum(acc, bs);
-    if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
 }
 
 __device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {
