@@ -203,6 +203,37 @@ int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *
 int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_t seed,
                   uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count);
 
+/* Largest len accepted by rgdbek_sample_noalloc. */
+#define RGDBEK_NOALLOC_MAX_LEN 262144
+
+/* The block selection of rgdbek_sample (random rule only) for callers that
+ * cannot allocate device memory when they draw a block: an application whose
+ * memory pool already holds the GPU's memory, a latency-critical loop that
+ * cannot accept the device synchronisation cudaMalloc / cudaFree may cause,
+ * or a plugin whose host forbids allocation after start-up.  The paper has no
+ * counterpart; this is an entry point for deploying the sampler.
+ *   eps    device double[len], nonnegative and finite, 1 <= len <=
+ *          RGDBEK_NOALLOC_MAX_LEN (larger len: INVALID_ARG, nothing launched)
+ *   idx    device int32[len] output: the sorted distinct drawn indices
+ *   count  device int64 output: their number, -1 if a weight is negative or
+ *          not finite, -2 if the kernel gave up a device wait
+ *   stream cudaStream_t the work is queued on (NULL = legacy default stream)
+ * The draws are those of rgdbek_sample with the same (s, seed, sysid, k,
+ * phase).  The call only queues work and returns (no host synchronisation);
+ * results are valid once the stream has reached them.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch memory (about 3.4 MB) is
+ * one static device array that every GPU loading the library holds until the
+ * process exits.  All calls on a device share that array, which keeps the
+ * last call's contents; each call resets what must start from zero.  Calls
+ * whose work overlaps on the GPU (e.g. on two streams) race on the array and
+ * must be ordered by the caller.  The first call on a device, with that
+ * device current, looks up the array's device address and the launch shape
+ * (cudaGetSymbolAddress, occupancy queries); make that first call before any
+ * stream capture.  Returns OK, INVALID_ARG or CUDA. */
+int rgdbek_sample_noalloc(const double *eps, int64_t len, int64_t s, uint64_t seed,
+                          uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count,
+                          void *stream);
+
 /* Copies the squared row norms (device double[m]) and squared column norms
  * (device double[n]) computed at creation; either may be NULL. */
 int rgdbek_get_norms(rgdbek_t h, double *row_norms2, double *col_norms2);

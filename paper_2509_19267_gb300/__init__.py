@@ -91,6 +91,7 @@ SIGNATURES = [
     ("rgdbek_weights", _int, [_ptr, _int, _ptr, _ptr, ctypes.POINTER(_dbl)]),
     ("rgdbek_sample", _int, [_ptr, _ptr, _i64, _i64, _u64, _u64, _i64, _int, _ptr,
                              ctypes.POINTER(_i64)]),
+    ("rgdbek_sample_noalloc", _int, [_ptr, _i64, _i64, _u64, _u64, _i64, _int, _ptr, _ptr, _ptr]),
     ("rgdbek_get_norms", _int, [_ptr, _ptr, _ptr]),
     ("rgdbek_get_csc", _int, [_ptr, _ptr, _ptr, _ptr]),
     ("rgdbek_status_string", ctypes.c_char_p, [_int]),
@@ -262,6 +263,15 @@ def rgdbek_sample(h: int, eps, s: int, seed: int, sysid: int, k: int, phase: int
     _check(_lib.rgdbek_sample(h, _dptr(eps), eps.shape[0], s, seed, sysid, k, phase, _dptr(idx),
                               ctypes.byref(cnt)), "rgdbek_sample")
     return cnt.value
+
+
+def rgdbek_sample_noalloc(eps, s: int, seed: int, sysid: int, k: int, phase: int, idx, count,
+                          stream=None) -> None:
+    """Queue the allocation-free sampler; idx (int32) and count (int64, one
+    element) are CUDA tensors that receive the block and its size."""
+    _check(_lib.rgdbek_sample_noalloc(_dptr(eps), eps.shape[0], s, seed, sysid, k, phase,
+                                      _dptr(idx), _dptr(count), _stream_ptr(stream)),
+           "rgdbek_sample_noalloc")
 
 
 def rgdbek_get_norms(h: int, row_norms2=None, col_norms2=None) -> None:
