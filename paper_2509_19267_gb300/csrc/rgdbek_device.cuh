@@ -142,10 +142,18 @@ __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+// running maximum of a nonnegative finite double, on bit patterns
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+
+// maximum over the warp of nonnegative finite doubles (integer compare of the
+// bit patterns, which order like the values; no FP64 instructions)
 __device__ __forceinline__ double warp_max(double v) {
+    long long b = __double_as_longlong(v);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    return v;
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(kFull, b, o));
+    return __longlong_as_double(b);
 }
 // sum over the L consecutive lanes of a group (L a power of two, <= 32); all
 // 32 lanes must call it
@@ -159,6 +167,8 @@ struct BlockScratch {
     double d[34];
     long long i[34];
     unsigned long long u[34];
+    double big[kMaxThreads];      // one partial per thread (FP64 block sums)
+    double mid[kMaxThreads / 4];  // first level of the FP64 block-sum tree
 };
 
 template <typename T>
@@ -172,6 +182,7 @@ __device__ __forceinline__ unsigned long long *scratch_of<unsigned long long>(Bl
     return s.u;
 }
 
+// Integer block sum: warp shuffles, then warp 0 over the warp totals.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, BlockScratch &bs) {
     T *sm = scratch_of<T>(bs);
@@ -189,19 +200,51 @@ __device__ __forceinline__ T block_sum(T v, BlockScratch &bs) {
     return sm[32];
 }
 
-__device__ __forceinline__ double block_max(double v, BlockScratch &bs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_max(v);
+// FP64 block sum.  GB300 issues one warp-wide FP64 add per SM every ~17
+// cycles, so a shuffle tree in every warp (5 adds x 32 warps) costs more than
+// the work it reduces; instead the partials go through shared memory: blockDim/4
+// threads add four each, then warp 0 adds the rest and finishes with one
+// shuffle tree (about blockDim/32 + 13 warp-wide adds).  Fixed order, so every
+// CTA reducing the same values gets the same bits.  blockDim % 64 == 0.
+template <>
+__device__ __forceinline__ double block_sum<double>(double v, BlockScratch &bs) {
+    const int t = threadIdx.x, n = blockDim.x, c1 = n >> 2;
     __syncthreads();
-    if (lane == 0) bs.d[warp] = v;
+    bs.big[t] = v;
     __syncthreads();
-    if (warp == 0) {
-        double r = lane < nw ? bs.d[lane] : 0.0;
-        r = warp_max(r);
-        if (lane == 0) bs.d[32] = r;
+    if (t < c1) {
+        const double *p = bs.big + 4 * t;
+        bs.mid[t] = (p[0] + p[1]) + (p[2] + p[3]);
+    }
+    __syncthreads();
+    if (t < 32) {
+        double r = 0.0;
+        for (int i = t; i < c1; i += 32) r += bs.mid[i];
+        r = warp_sum(r);
+        if (t == 0) bs.d[32] = r;
     }
     __syncthreads();
     return bs.d[32];
+}
+
+// Maximum of nonnegative finite doubles, taken on their bit patterns (which
+// order like the values) with integer instructions.
+__device__ __forceinline__ double block_max(double v, BlockScratch &bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(kFull, b, o));
+    __syncthreads();
+    if (lane == 0) bs.i[warp] = b;
+    __syncthreads();
+    if (warp == 0) {
+        long long r = lane < nw ? bs.i[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(kFull, r, o));
+        if (lane == 0) bs.i[32] = r;
+    }
+    __syncthreads();
+    return __longlong_as_double(bs.i[32]);
 }
 
 // Exclusive scan of one value per thread in thread order; *total gets the sum.
@@ -233,43 +276,6 @@ __device__ __forceinline__ T block_excl_scan(T v, BlockScratch &bs, T *total) {
     return off + x - v;
 }
 
-// Sum over the per-CTA partials of one slot, computed by warp 0 in a fixed
-// order; the result is returned to every thread of the CTA.
-__device__ __forceinline__ double reduce_partials_sum(const double *p, int nb, BlockScratch &bs) {
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
-        s = warp_sum(s);
-        if (threadIdx.x == 0) bs.d[33] = s;
-    }
-    __syncthreads();
-    return bs.d[33];
-}
-__device__ __forceinline__ double reduce_partials_max(const double *p, int nb, BlockScratch &bs) {
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nb; i += 32) s = fmax(s, __ldcg(p + i));
-        s = warp_max(s);
-        if (threadIdx.x == 0) bs.d[33] = s;
-    }
-    __syncthreads();
-    return bs.d[33];
-}
-__device__ __forceinline__ long long reduce_partials_isum(const long long *p, int nb,
-                                                          BlockScratch &bs) {
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        long long s = 0;
-        for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
-        s = warp_sum(s);
-        if (threadIdx.x == 0) bs.i[33] = s;
-    }
-    __syncthreads();
-    return bs.i[33];
-}
-
 // All requested partial slots reduced at once: warp w of the CTA reduces the
 // w-th requested slot (sums in a fixed order; maxima for slots in dmax), and
 // the results land in out_d[slot] / out_i[slot] for every thread.  dmask /
@@ -288,7 +294,7 @@ __device__ __forceinline__ void collect_partials(const double *pd, const long lo
 #pragma unroll 8
             for (int i = lane; i < nb; i += 32) {
                 const double v = __ldcg(p + i);
-                s = mx ? fmax(s, v) : s + v;
+                s = mx ? max_nonneg(s, v) : s + v;
             }
             s = mx ? warp_max(s) : warp_sum(s);
             if (lane == 0) out_d[slot] = s;

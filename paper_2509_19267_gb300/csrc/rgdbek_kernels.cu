@@ -27,7 +27,7 @@ namespace rgd {
 // from the identically reduced partials) and broadcast through shared memory.
 struct LsqrState {
     double alpha, beta, rhobar, phibar, beta1, fro;
-    double rho, cs, sn;          // plane rotation of the current step
+    double irho, cs, sn;         // plane rotation of the current step (1/rho, c, s)
     double inv_a, ab, wcoef;     // coefficients of the next rows phase
     double inv_b, ba, phi_rho;   // coefficients of the next cols phase
     int mv, done;
@@ -311,21 +311,22 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             // scalars from ||v~||^2 of the previous cols phase
             const double vv = warp0_collect(P.pd, D_VV);
             if (threadIdx.x == 0) {
-                const double rho = L.rho, cs = L.cs, sn = L.sn, bn = L.beta;
+                // alpha_{i+1} = ||v~||; the divisions of the recurrence are
+                // multiplications by reciprocals formed with rsqrt, which keeps
+                // the dependent FP64 chain of this single thread short
+                const double cs = L.cs, sn = L.sn, bn = L.beta;
                 const double an = bn > 0.0 ? sqrt(vv) : 0.0;
-                const double theta = sn * an;
+                const double ian = an > 0.0 ? rsqrt(vv) : 0.0;
                 L.rhobar = -cs * an;
-                L.wcoef = theta / rho;
+                L.wcoef = sn * an * L.irho;   // theta / rho
                 const double rnorm = L.phibar;
                 const double arnorm = L.phibar * an * fabs(cs);
                 L.done = arnorm <= P.inner_tol * L.fro * rnorm ||
                          rnorm <= P.inner_tol * L.beta1 || an == 0.0 || bn == 0.0 ||
                          it - 1 >= P.inner_max;
                 L.alpha = an;
-                if (!L.done) {
-                    L.inv_a = 1.0 / an;
-                    L.ab = an / bn;
-                }
+                L.inv_a = ian;
+                L.ab = an * L.inv_b;           // alpha / beta
             }
         }
         __syncthreads();
@@ -354,17 +355,19 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         if (threadIdx.x < 32) {
             const double uu = warp0_collect(P.pd, D_UU);
             if (threadIdx.x == 0) {
+                // beta_{i+1} = ||u~||, rho = sqrt(rhobar^2 + beta^2); 1/rho from
+                // rsqrt of rho^2 directly, in parallel with sqrt(||u~||^2)
                 const double bn = sqrt(uu);
-                const double rho = sqrt(L.rhobar * L.rhobar + bn * bn);
-                const double cs = L.rhobar / rho, sn = bn / rho;
+                const double irho = rsqrt(fma(L.rhobar, L.rhobar, uu));
+                const double cs = L.rhobar * irho, sn = bn * irho;
                 const double phi = cs * L.phibar;
                 L.phibar = sn * L.phibar;
                 L.mv = bn > 0.0;
-                L.inv_b = bn > 0.0 ? 1.0 / bn : 0.0;
-                L.ba = bn / L.alpha;
-                L.phi_rho = phi / rho;
+                L.inv_b = bn > 0.0 ? rsqrt(uu) : 0.0;
+                L.ba = bn * L.inv_a;           // beta / alpha
+                L.phi_rho = phi * irho;
                 L.beta = bn;
-                L.rho = rho;
+                L.irho = irho;
                 L.cs = cs;
                 L.sn = sn;
             }
@@ -415,7 +418,7 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
             const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(ri, ri), c) : 0.0;
             P.epsr[i] = e;
             if (!isfinite(e)) bad = 1;
-            else emax = fmax(emax, e);
+            else emax = max_nonneg(emax, e);
             zz = fma(zi, zi, zz);
         }
     }
@@ -690,7 +693,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads) weights_kernel(const double 
         const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(x, x), c) : 0.0;
         eps[j] = e;
         if (!isfinite(e)) bad = 1;
-        else emax = fmax(emax, e);
+        else emax = max_nonneg(emax, e);
     }
     emax = block_max(emax, bs);
     bad = block_sum(bad, bs);
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
     for (long long j = gthread(); j < len; j += nthreads()) {
         const double e = eps[j];
         if (!isfinite(e) || e < 0.0) bad = 1;
-        else emax = fmax(emax, e);
+        else emax = max_nonneg(emax, e);
     }
     emax = block_max(emax, bs);
     bad = block_sum(bad, bs);

@@ -240,7 +240,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
             P.g[j] = sg;
             P.epsc[j] = e;
             if (!isfinite(e)) bad = 1;
-            else emax = fmax(emax, e);
+            else emax = max_nonneg(emax, e);
             hh = fma(sh, sh, hh);
         }
     }
