@@ -23,7 +23,7 @@ struct rgdbek_s {
     int *ci = nullptr, *ri = nullptr;
     double *av = nullptr, *cv = nullptr, *rn2 = nullptr, *cn2 = nullptr;
     // work
-    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx;
+    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx, *xt;
     unsigned long long *Q;
     unsigned char *flag;
     int *colpos, *rowpos, *ulist, *jlist;
@@ -36,7 +36,7 @@ struct rgdbek_s {
     Ctrl *ctrl;
     double *b_stage, *x_stage;
     // launch shape
-    int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1;
+    int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
     // trace
     long long *tr_counts = nullptr;
     long long tr_count_cap = 0;
@@ -80,6 +80,7 @@ void carve(rgdbek_s *h, Layout &L) {
     h->ww = L.take<double>(n);
     h->yy = L.take<double>(n);
     h->dx = L.take<double>(n);
+    h->xt = L.take<double>(n);
     h->Q = L.take<unsigned long long>(mx);
     h->flag = L.take<unsigned char>(mx);
     h->colpos = L.take<int>(n);
@@ -159,6 +160,7 @@ Params make_params(const rgdbek_s *h) {
     P.ww = h->ww;
     P.yy = h->yy;
     P.dx = h->dx;
+    P.xt = h->xt;
     P.Q = h->Q;
     P.flag = h->flag;
     P.colpos = h->colpos;
@@ -190,6 +192,8 @@ Params make_params(const rgdbek_s *h) {
     P.time_budget_ns = h->opt.time_budget_s * 1e9;
     P.tpr = h->tpr;
     P.tpc = h->tpc;
+    P.ipr = h->ipr;
+    P.ipc = h->ipc;
     P.dsmem_bytes = kSolveDsmemBytes;
     return P;
 }
@@ -276,8 +280,10 @@ int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_
         release(h);
         return st;
     }
-    h->tpr = pick_lanes_int(nnz, m);
-    h->tpc = pick_lanes_int(nnz, n);
+    h->tpr = pick_lanes_fp64(nnz, m);
+    h->tpc = pick_lanes_fp64(nnz, n);
+    h->ipr = pick_lanes_int(nnz, m);
+    h->ipc = pick_lanes_int(nnz, n);
 
     Layout L;
     carve(h, L);

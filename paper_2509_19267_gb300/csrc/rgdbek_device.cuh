@@ -372,12 +372,21 @@ __device__ __forceinline__ int ceil_log2_ll(long long v) {
     return v <= 1 ? 0 : 64 - __clzll((unsigned long long)(v - 1));
 }
 
-// lanes to put on one row/column of a matrix with nnz nonzeros in `lines`
-// rows/columns: the largest power of two L <= 32 with 2L <= nnz / lines
-// (at least 1); integer arithmetic only
+// Lanes to put on one row/column of a matrix with nnz nonzeros in `lines`
+// rows/columns, integer arithmetic only.
+// pick_lanes_int: for integer-only passes (counting, extraction), where only
+// latency matters: the largest power of two L <= 32 with 2L <= nnz / lines.
+// pick_lanes_fp64: for passes with FP64 multiply-adds, where GB300's low FP64
+// issue rate makes idle lanes and group shuffle-adds expensive: about eight
+// entries per lane (the largest power of two L <= 32 with 8L <= nnz / lines).
 __host__ __device__ __forceinline__ int pick_lanes_int(long long nnz, long long lines) {
     int L = 1;
     while (L < 32 && 4ll * L * lines <= nnz) L *= 2;
+    return L;
+}
+__host__ __device__ __forceinline__ int pick_lanes_fp64(long long nnz, long long lines) {
+    int L = 1;
+    while (L < 32 && 16ll * L * lines <= nnz) L *= 2;
     return L;
 }
 

@@ -222,15 +222,16 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot) {
 // LSQR from y = 0 on the block (R, C) with right-hand side c0 (u-space,
 // global), beta1 = ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in
 // P.vv and alpha1 is passed; otherwise it is computed first (one more
-// phase).  fro2 = ||B||_F^2.  y_g (v-space, zero on entry) receives the
-// solution.  Returns the number of steps (0 if alpha1 == 0), or -1 if a grid
-// barrier was abandoned.
+// phase).  fro2 = ||B||_F^2.  y_g (v-space) receives the solution; with xt
+// given (the row step, v-space = x-space) also xt = x + y, so the residual
+// pass gathers x_{k+1} without an addition per nonzero.  Returns the number
+// of steps (0 if alpha1 == 0), or -1 if a grid barrier was abandoned.
 //
 // Per phase: grid barrier | warp 0 reduces the partials and updates the
 // scalars while warps 1.. compute the dot products of the CTA's lines |
 // __syncthreads | all threads combine element-wise and form the partial.
 __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
-                                        const double *c0, double *y_g, bool v_given,
+                                        const double *c0, double *y_g, double *xt, bool v_given,
                                         double alpha1, double beta1, double fro2,
                                         unsigned char *dsmem, long long dsmem_bytes,
                                         SolveSmem &S) {
@@ -254,6 +255,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         wown = P.ww + CC.lo;
         yown = y_g + CC.lo;
         dc = P.dots2 + CC.lo;
+        for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = 0.0;
     } else {
         for (int i = threadIdx.x; i < nrl; i += blockDim.x) uold[i] = c0[RC.lo + i];
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
@@ -387,6 +389,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 const double y = fma(phi_rho, wown[li], yown[li]);
                 yown[li] = y;
                 y_g[CC.lo + li] = y;
+                if (xt) xt[CC.lo + li] = P.x[CC.lo + li] + y;
             }
             acc = block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
         }
         for (long long j = gthread(); j < P.n; j += nthreads()) {
             P.x[j] = 0.0;
-            P.dx[j] = 0.0;
+            P.xt[j] = 0.0;
         }
         bb = block_sum(bb, bs);
         bad = block_sum(bad, bs);
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             nU = phase_compact_write(P, P.n, P.colpos, P.ulist, &ucopy, S.tab, S.tab2, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_COL_SEL);
-            const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
+            const Lines Arows{P.rp, P.ci, P.av, P.m, P.ipr};
             phase_extract_count(P, Arows, P.colpos, bs);
             RGD_SYNC(0, 0, 0);
             rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
@@ -558,12 +561,12 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             nnzU = phase_extract_write(P, Arows, P.colpos, P.srp, P.sci, P.sav, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_COL_EXT);
-            Lsub_u = pick_lanes_int(nnzU, P.m);
+            Lsub_u = pick_lanes_fp64(nnzU, P.m);
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const SideC rows{P.srp, P.sci, P.sav, P.m, Lsub_u};
-                const SideC cols{P.scp, P.sri, P.scv, nU, P.tpc};
-                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, true, O.alpha1, O.beta1, O.fro2, dsmem,
-                                  P.dsmem_bytes, S);
+                const SideC cols{P.scp, P.sri, P.scv, nU, P.tpc};   // columns of A
+                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, nullptr, true, O.alpha1, O.beta1,
+                                  O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
             }
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, &jcopy, S.tab, S.tab2, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
-            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
+            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.ipc};
             phase_extract_count(P, Acols, P.rowpos, bs);
             RGD_SYNC(0, 0, 0);
             rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
@@ -622,9 +625,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             mark(S, PH_ROW_EXT);
             if (O.beta1 > 0.0) {
                 const SideC rows{P.srp, P.sci, P.sav, nJ, P.tpr};
-                const SideC cols{P.scp, P.sri, P.scv, P.n, pick_lanes_int(nnzJ, P.n)};
-                stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, false, 0.0, O.beta1, O.fro2, dsmem,
-                                  P.dsmem_bytes, S);
+                const SideC cols{P.scp, P.sri, P.scv, P.n, pick_lanes_fp64(nnzJ, P.n)};
+                stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, P.xt, false, 0.0, O.beta1, O.fro2,
+                                  dsmem, P.dsmem_bytes, S);
                 if (stepsJ < 0) return;
                 mark(S, PH_ROW_LSQR);
             }

@@ -38,8 +38,9 @@ struct Params {
     const double *b;
     double *x;
     // work vectors: z (m), t = b - A x (m), r (m), g = A^T z (n), weights,
-    // LSQR vectors u (m), v, w, y (n), the pending x update dx (n)
-    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx;
+    // LSQR vectors u (m), v, w, y (n), the row-step solution dx (n) and the
+    // trial iterate xt = x + dx (n) that the next column pass adopts
+    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx, *xt;
     unsigned long long *Q;  // chunk-local inclusive prefix of quantised weights
     unsigned char *flag;    // drawn / selected marks
     int *colpos, *rowpos;   // position of a column in U / of a row in J, or -1
@@ -65,7 +66,8 @@ struct Params {
     long long max_iter, s_col, s_row;
     unsigned long long seed, sysid;
     int inner_max, stop_rule, selection;
-    int tpr, tpc;           // lanes per row of A (CSR) and per column (CSC)
+    int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
+    int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
 };
 
@@ -216,7 +218,7 @@ __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, 
 }
 
 // Column pass of iteration k (Algorithm 1, first half; Section 2 weights):
-//   x_k = x_{k-1} + dx (the row update of the previous iteration), dx = 0,
+//   x_k = xt (x_{k-1} plus the row update of the previous iteration),
 //   g = A^T z_k, h = A^T t_k with t_k = b - A x_k (for the stopping test),
 //   eps^z_j = g_j^2 / ||A_j||^2.
 // Partials: max eps^z, ||h||^2, non-finite flag.
@@ -233,8 +235,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
         sg = group_sum(sg, G.L);
         sh = group_sum(sh, G.L);
         if (j < P.n && G.sl == 0) {
-            P.x[j] = P.x[j] + P.dx[j];
-            P.dx[j] = 0.0;
+            P.x[j] = P.xt[j];
             const double c = __ldg(P.cn2 + j);
             const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(sg, sg), c) : 0.0;
             P.g[j] = sg;
@@ -254,7 +255,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
     }
 }
 
-// t_{k+1} = b - A (x_k + dx) over the CSR rows.  Partial: ||t||^2.
+// t_{k+1} = b - A x_{k+1} over the CSR rows, x_{k+1} = xt.  Partial: ||t||^2.
 __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs) {
     const Grp G(P.tpr);
     double tt = 0.0;
@@ -263,7 +264,7 @@ __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs
         double s = 0.0;
         if (i < P.m)
             s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
-                               [&](int j) { return P.x[j] + P.dx[j]; });
+                               [&](int j) { return P.xt[j]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
             const double ti = __ldg(P.b + i) - s;
