@@ -76,19 +76,22 @@ def make_system(rank: int):
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(st, m: int, n: int, nnz: int) -> float:
     it = st.iters
-    full_passes = it * ((12 * nnz + 16 * m + 64 * n)        # column pass (A^T z, A^T t, x update)
-                        + (12 * nnz + 24 * m + 16 * n))     # residual pass t = b - A x
+    full_passes = it * ((12 * nnz + 16 * m + 56 * n)        # column pass (A^T z, A^T t, x = xt)
+                        + (12 * nnz + 24 * m + 8 * n))      # residual pass t = b - A xt
     # the last column pass (the converged test) has no residual pass after it
-    full_passes += 12 * nnz + 16 * m + 64 * n
+    full_passes += 12 * nnz + 16 * m + 56 * n
     selection = it * (23 * n + 23 * m)                      # quantise, marks, compaction
-    extraction = it * (2 * (8 * m + 4 * nnz + 4 * n) + 8 * m     # A_U: count + write over CSR
-                       + 2 * (8 * n + 4 * nnz + 4 * m) + 8 * n)  # A^J: count + write over CSC
+    # one-pass extraction of A_U (over CSR) and A^J (over CSC): pointers,
+    # indices, the selection map once, kept entries and per-line counts
+    extraction = it * ((8 * m + 4 * nnz + 4 * n + 4 * m) + (8 * n + 4 * nnz + 4 * m + 4 * n))
     extraction += 12 * st.sum_nnz_u + 12 * st.sum_nnz_j + 24 * st.sum_nu + 16 * st.sum_nj
-    zstep = it * 56 * m + 12 * st.sum_nnz_u + 8 * st.sum_nu
+    # each inner solve first copies both sides of its block into shared memory
+    caching = 24 * st.sum_nnz_u + 24 * st.sum_nnz_j + 16 * it * (m + n)
+    zstep = it * 52 * m + 12 * st.sum_nnz_u + 8 * st.sum_nu
     lsqr_u = 24 * st.lsqr_nnz_u + 32 * m * st.inner_u + 90 * st.lsqr_n_u
     lsqr_j = (12 * st.sum_nnz_j + 16 * n * it + 8 * st.sum_nj        # first v of each row block
-              + 24 * st.lsqr_nnz_j + 80 * n * st.inner_j + 44 * st.lsqr_n_j)
-    return float(full_passes + selection + extraction + zstep + lsqr_u + lsqr_j)
+              + 24 * st.lsqr_nnz_j + 88 * n * st.inner_j + 44 * st.lsqr_n_j)
+    return float(full_passes + selection + extraction + caching + zstep + lsqr_u + lsqr_j)
 
 
 class ClockSampler:

@@ -27,7 +27,7 @@ struct rgdbek_s {
     unsigned long long *Q;
     unsigned char *flag;
     int *colpos, *rowpos, *ulist, *jlist;
-    long long *srp, *scp;
+    int *srn, *scn;
     int *sci, *sri;
     double *sav, *scv;
     double *dots, *dots2;
@@ -87,10 +87,10 @@ void carve(rgdbek_s *h, Layout &L) {
     h->rowpos = L.take<int>(mx);
     h->ulist = L.take<int>(n);
     h->jlist = L.take<int>(m);
-    h->srp = L.take<long long>(m + 1);
+    h->srn = L.take<int>(m);
     h->sci = L.take<int>(nnz);
     h->sav = L.take<double>(nnz);
-    h->scp = L.take<long long>(n + 1);
+    h->scn = L.take<int>(n);
     h->sri = L.take<int>(nnz);
     h->scv = L.take<double>(nnz);
     h->dots = L.take<double>(mx);
@@ -167,10 +167,10 @@ Params make_params(const rgdbek_s *h) {
     P.rowpos = h->rowpos;
     P.ulist = h->ulist;
     P.jlist = h->jlist;
-    P.srp = h->srp;
+    P.srn = h->srn;
     P.sci = h->sci;
     P.sav = h->sav;
-    P.scp = h->scp;
+    P.scn = h->scn;
     P.sri = h->sri;
     P.scv = h->scv;
     P.dots = h->dots;

@@ -43,8 +43,7 @@ enum ISlot {
     I_BAD_R,      // non-finite row weight / b entry seen
     I_TOT,        // chunk total of quantised weights
     I_CNT,        // chunk count of flagged indices
-    I_NNZ,        // chunk count of extracted nonzeros
-    I_LEN,        // chunk sum of the lengths of the flagged lines (compact copies)
+    I_NNZ,        // count of extracted nonzeros
     I_NSLOTS
 };
 

@@ -50,7 +50,6 @@ struct SolveSmem {
     BlockScratch bs;
     Acc acc;
     long long tab[kMaxGrid];
-    long long tab2[kMaxGrid];
     double red_d[D_NSLOTS];                          // reduced partials of the last barrier
     long long red_i[I_NSLOTS];
     LsqrState lsqr;                                  // LSQR scalars (written by thread 0)
@@ -127,16 +126,29 @@ __device__ __forceinline__ void finish(const Params &P, int status, long long k,
 //   cols:  v~_new = B^T u~_new / beta_new - (beta_new/alpha) v~,
 //          y += (phi/rho) w
 // ---------------------------------------------------------------------------
+// One side of a block: n lines, line l spanning idx/val[b, e) with
+//   b = ptr[src], e = cnt ? b + cnt[src] : ptr[src + 1],  src = list ? list[l] : l
+// (an extracted block keeps its lines in place with counts; a block made of
+// selected rows/columns of A reads them through the selection list).
 struct SideC {
-    const long long *ptr;  // line pointers [0, n]
+    const long long *ptr;
+    const int *cnt;
+    const int *list;
     const int *idx;        // indices into the other space
     const double *val;
     long long n;           // lines
     int L;                 // lanes per line
 };
 
-// this CTA's chunk of a side: line li (local) spans ptr[li] .. ptr[li+1] of
-// idx / val (shared memory, or the global arrays with absolute pointers)
+__device__ __forceinline__ void line_span(const SideC &S, long long l, long long &b, long long &e) {
+    const long long src = S.list ? S.list[l] : l;
+    b = __ldg(S.ptr + src);
+    e = S.cnt ? b + S.cnt[src] : __ldg(S.ptr + src + 1);
+}
+
+// This CTA's chunk [lo, lo + nl) of a side.  Cached: local line li spans
+// idx/val[ptr[li], ptr[li+1]) in shared memory.  Otherwise the lines are read
+// from the global arrays through line_span.
 struct CtaSide {
     const long long *ptr;
     const int *idx;
@@ -144,9 +156,11 @@ struct CtaSide {
     int nl;
     long long lo;
     int L;
+    bool cached;
+    SideC g;
 };
 
-// bump allocation in dynamic shared memory (8-byte granules)
+// bump allocation in dynamic shared memory (16-byte granules)
 struct SmemArena {
     unsigned char *base;
     long long left, used;
@@ -161,29 +175,59 @@ struct SmemArena {
     }
 };
 
-__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A) {
+// Copies this CTA's chunk of a side into shared memory (compacting the
+// lines), if it fits.  All threads of the CTA call it.
+__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, BlockScratch &bs) {
     const Chunk C(S.n, blockIdx.x, gridDim.x);
     CtaSide out;
     out.nl = (int)(C.hi - C.lo);
     out.lo = C.lo;
     out.L = S.L;
-    const long long b0 = S.ptr[C.lo], ne = S.ptr[C.hi] - b0;
+    out.g = S;
+    out.cached = false;
+    out.ptr = nullptr;
+    out.idx = nullptr;
+    out.val = nullptr;
     const SmemArena save = A;
     long long *ps = A.take<long long>(out.nl + 1);
-    int *is = ps ? A.take<int>(ne) : nullptr;
-    double *vs = is ? A.take<double>(ne) : nullptr;
+    if (!ps) return out;
+    // line lengths -> local offsets (exclusive scan in line order)
+    long long run = 0;
+    for (int base = 0; base < out.nl; base += blockDim.x) {
+        const int li = base + threadIdx.x;
+        long long len = 0;
+        if (li < out.nl) {
+            long long b, e;
+            line_span(S, C.lo + li, b, e);
+            len = e - b;
+        }
+        long long tot;
+        const long long ex = block_excl_scan<long long>(len, bs, &tot);
+        if (li < out.nl) ps[li] = run + ex;
+        run += tot;
+    }
+    if (threadIdx.x == 0) ps[out.nl] = run;
+    int *is = A.take<int>(run);
+    double *vs = is ? A.take<double>(run) : nullptr;
     if (!vs) {
         A = save;
-        out.ptr = S.ptr + C.lo;
-        out.idx = S.idx;
-        out.val = S.val;
+        __syncthreads();
         return out;
     }
-    for (int i = threadIdx.x; i <= out.nl; i += blockDim.x) ps[i] = S.ptr[C.lo + i] - b0;
-    for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
-        is[e] = S.idx[b0 + e];
-        vs[e] = S.val[b0 + e];
+    __syncthreads();
+    // warp per line, lanes over entries
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int li = warp; li < out.nl; li += blockDim.x >> 5) {
+        long long b, e;
+        line_span(S, C.lo + li, b, e);
+        const long long o = ps[li];
+        for (long long k = lane; k < e - b; k += 32) {
+            is[o + k] = S.idx[b + k];
+            vs[o + k] = S.val[b + k];
+        }
     }
+    __syncthreads();
+    out.cached = true;
     out.ptr = ps;
     out.idx = is;
     out.val = vs;
@@ -198,12 +242,19 @@ __device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, do
     if (warp == 0) return;
     const Grp G(C.L);
     const int per = ((blockDim.x >> 5) - 1) * G.rpw;
+    const auto gat = [&](int j) { return vec[j]; };
     for (int base = 0; base < C.nl; base += per) {
         const int li = base + (warp - 1) * G.rpw + G.sub;
         double s = 0.0;
-        if (li < C.nl)
-            s = lane_dot<false>(C.ptr[li] + G.sl, C.ptr[li + 1], G.L, C.idx, C.val,
-                                [&](int j) { return vec[j]; });
+        if (li < C.nl) {
+            if (C.cached) {
+                s = lane_dot<false>(C.ptr[li] + G.sl, C.ptr[li + 1], G.L, C.idx, C.val, gat);
+            } else {
+                long long b, e;
+                line_span(C.g, C.lo + li, b, e);
+                s = lane_dot<false>(b + G.sl, e, G.L, C.g.idx, C.g.val, gat);
+            }
+        }
         s = group_sum(s, G.L);
         if (li < C.nl && G.sl == 0) dots[li] = s;
     }
@@ -263,8 +314,8 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             yown[i] = 0.0;
         }
     }
-    const CtaSide R = cache_side(Rs, A);
-    const CtaSide C = cache_side(Cs, A);
+    const CtaSide R = cache_side(Rs, A, S.bs);
+    const CtaSide C = cache_side(Cs, A, S.bs);
     if (threadIdx.x == 0) {
         L.inv_b = 1.0 / beta1;
         L.done = 0;
@@ -409,7 +460,7 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
         const long long i = base + G.sub;
         double s = 0.0;
         if (hasU && i < P.m)
-            s = lane_dot<false>(P.srp[i] + G.sl, P.srp[i + 1], G.L, P.sci, P.sav,
+            s = lane_dot<false>(P.rp[i] + G.sl, P.rp[i] + P.srn[i], G.L, P.sci, P.sav,
                                 [&](int p) { return P.yy[p]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
@@ -533,7 +584,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.n, P.cn2, P.g, P.cp, bs);
+            phase_compact_count(P, P.n, P.cn2, P.g, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on A_U with c = z_k: beta1 = ||z_k||, alpha1 = ||A_U^T z_k|| / beta1
@@ -542,14 +593,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
                 O.alpha1 = sqrt(S.red_d[D_EXTRA]) * O.inv_beta1;
             }
-            // U_k, and A_U's columns copied contiguously (the v-space side of LSQR)
-            const LineCopy ucopy{P.cp, P.ri, P.cv, P.scp, P.sri, P.scv};
-            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, &ucopy, S.tab, S.tab2, bs);
+            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_COL_SEL);
-            const Lines Arows{P.rp, P.ci, P.av, P.m, P.ipr};
-            phase_extract_count(P, Arows, P.colpos, bs);
-            RGD_SYNC(0, 0, 0);
             rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
             const double inv_beta1 = O.inv_beta1;
             for (long long p = gthread(); p < nU; p += nthreads()) {
@@ -558,13 +604,16 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 P.yy[p] = 0.0;
                 if (rec_u) P.tr_lists[tr_off + p] = j;
             }
-            nnzU = phase_extract_write(P, Arows, P.colpos, P.srp, P.sci, P.sav, S.tab, bs);
-            RGD_SYNC(0, 0, 0);
+            // A_U: the entries of every row of A that lie in U's columns
+            const Lines Arows{P.rp, P.ci, P.av, P.m, P.ipr};
+            phase_extract(P, Arows, P.colpos, P.srn, P.sci, P.sav, bs);
+            RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_COL_EXT);
+            nnzU = S.red_i[I_NNZ];
             Lsub_u = pick_lanes_fp64(nnzU, P.m);
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
-                const SideC rows{P.srp, P.sci, P.sav, P.m, Lsub_u};
-                const SideC cols{P.scp, P.sri, P.scv, nU, P.tpc};   // columns of A
+                const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
+                const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
                 stepsU = run_lsqr(P, rows, cols, P.z, P.yy, nullptr, true, O.alpha1, O.beta1,
                                   O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
@@ -598,7 +647,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.m, P.rn2, P.r, P.rp, bs);
+            phase_compact_count(P, P.m, P.rn2, P.r, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on A^J with c = r_J: beta1 = ||r_J||
@@ -606,26 +655,25 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 O.beta1 = sqrt(S.red_d[D_EXTRA]);
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
             }
-            // J_k, and A^J's rows copied contiguously (the u-space side of LSQR)
-            const LineCopy jcopy{P.rp, P.ci, P.av, P.srp, P.sci, P.sav};
-            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, &jcopy, S.tab, S.tab2, bs);
+            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
-            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.ipc};
-            phase_extract_count(P, Acols, P.rowpos, bs);
-            RGD_SYNC(0, 0, 0);
             rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
             for (long long p = gthread(); p < nJ; p += nthreads()) {
                 const int i = P.jlist[p];
                 P.uu[p] = P.r[i];  // u~_1 = r_J
                 if (rec_j) P.tr_lists[tr_off + nU + p] = i;
             }
-            nnzJ = phase_extract_write(P, Acols, P.rowpos, P.scp, P.sri, P.scv, S.tab, bs);
-            RGD_SYNC(0, 0, 0);
+            // A^J: the entries of every column of A that lie in J's rows
+            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.ipc};
+            phase_extract(P, Acols, P.rowpos, P.scn, P.sri, P.scv, bs);
+            RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_ROW_EXT);
+            nnzJ = S.red_i[I_NNZ];
             if (O.beta1 > 0.0) {
-                const SideC rows{P.srp, P.sci, P.sav, nJ, P.tpr};
-                const SideC cols{P.scp, P.sri, P.scv, P.n, pick_lanes_fp64(nnzJ, P.n)};
+                const SideC rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
+                const SideC cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
+                                 pick_lanes_fp64(nnzJ, P.n)};
                 stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, P.xt, false, 0.0, O.beta1, O.fro2,
                                   dsmem, P.dsmem_bytes, S);
                 if (stepsJ < 0) return;
@@ -740,9 +788,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
             phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
             RGD_SYNC(0, 0, 0);
         }
-        phase_compact_count(P, len, eps, eps, nullptr, bs);
+        phase_compact_count(P, len, eps, eps, bs);
         RGD_SYNC(0, 0, 0);
-        count = phase_compact_write(P, len, P.rowpos, idx, nullptr, S.tab, S.tab2, bs);
+        count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctrl->sample_count = bad ? -1 : count;

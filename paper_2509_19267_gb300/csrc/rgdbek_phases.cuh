@@ -45,11 +45,11 @@ struct Params {
     unsigned char *flag;    // drawn / selected marks
     int *colpos, *rowpos;   // position of a column in U / of a row in J, or -1
     int *ulist, *jlist;     // U_k and J_k, ascending
-    long long *srp;         // A_U as CSR over all m rows, columns renumbered 0..|U|-1
-    int *sci;
+    int *srn;               // A_U as CSR over all m rows: row i holds srn[i] entries
+    int *sci;               // at sci/sav[rp[i] ..], columns renumbered 0..|U|-1
     double *sav;
-    long long *scp;         // A^J as CSC over all n columns, rows renumbered 0..|J|-1
-    int *sri;
+    int *scn;               // A^J as CSC over all n columns: column j holds scn[j]
+    int *sri;               // entries at sri/scv[cp[j] ..], rows renumbered 0..|J|-1
     double *scv;
     double *dots, *dots2;   // per-line dot products of the inner solve when a CTA's
                             // chunk does not fit in shared memory (max(m, n) each)
@@ -361,14 +361,12 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 }
 
 // Count of marked indices in the chunk, and over them the sums of norm2 (the
-// block's squared Frobenius norm), of vec^2 (for the LSQR start) and, when
-// lptr is given, of the line lengths lptr[j+1] - lptr[j] (for the compact
-// copy of the selected lines).
+// block's squared Frobenius norm) and of vec^2 (for the LSQR start).
 __device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
                                                     const double *norm2, const double *vec,
-                                                    const long long *lptr, BlockScratch &bs) {
+                                                    BlockScratch &bs) {
     const Chunk C(len, blockIdx.x, gridDim.x);
-    long long cnt = 0, lsum = 0;
+    long long cnt = 0;
     double fro = 0.0, ext = 0.0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
@@ -378,30 +376,17 @@ __device__ __forceinline__ void phase_compact_count(const Params &P, long long l
             fro += __ldg(norm2 + j);
             const double v = vec[j];
             ext = fma(v, v, ext);
-            if (lptr) lsum += __ldg(lptr + j + 1) - __ldg(lptr + j);
         }
     }
     cnt = block_sum(cnt, bs);
     fro = block_sum(fro, bs);
     ext = block_sum(ext, bs);
-    if (lptr) lsum = block_sum(lsum, bs);
     if (threadIdx.x == 0) {
         P.pi[I_CNT * gridDim.x + blockIdx.x] = cnt;
-        P.pi[I_LEN * gridDim.x + blockIdx.x] = lsum;
         P.pd[D_FRO * gridDim.x + blockIdx.x] = fro;
         P.pd[D_EXTRA * gridDim.x + blockIdx.x] = ext;
     }
 }
-
-// Source lines and destination of a compact copy of the selected lines.
-struct LineCopy {
-    const long long *sptr;
-    const int *sidx;
-    const double *sval;
-    long long *dptr;
-    int *didx;
-    double *dval;
-};
 
 // Exclusive rank of a predicate over the CTA in thread order (ballot/popc per
 // warp, then the warp counts scanned); *total gets the CTA count.
@@ -427,20 +412,15 @@ __device__ __forceinline__ long long block_rank_pred(bool f, BlockScratch &bs, l
 }
 
 // Marked indices -> ascending list; pos[j] = position in the list or -1.
-// With cp given, the selected lines are also copied, in list order, into a
-// compact CSR-like array (dptr over list positions).  tab and tab2 are
-// kMaxGrid-long smem tables.  Returns the list length.
+// Returns the list length.
 __device__ __forceinline__ long long phase_compact_write(const Params &P, long long len, int *pos,
-                                                         int *list, const LineCopy *cp,
-                                                         long long *tab, long long *tab2,
+                                                         int *list, long long *tab,
                                                          BlockScratch &bs) {
     const int nct = gridDim.x;
     partials_prefix(P.pi + I_CNT * nct, nct, tab, bs);
-    if (cp) partials_prefix(P.pi + I_LEN * nct, nct, tab2, bs);
     const long long total = tab[nct - 1];
     const Chunk C(len, blockIdx.x, nct);
     long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
-    long long erun = (cp && blockIdx.x > 0) ? tab2[blockIdx.x - 1] : 0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
         const bool f = j < C.hi && P.flag[j];
@@ -454,51 +434,19 @@ __device__ __forceinline__ long long phase_compact_write(const Params &P, long l
                 pos[j] = -1;
             }
         }
-        if (cp) {
-            long long s0 = 0, s1 = 0;
-            if (f) {
-                s0 = __ldg(cp->sptr + j);
-                s1 = __ldg(cp->sptr + j + 1);
-            }
-            long long etot;
-            const long long eex = block_excl_scan<long long>(s1 - s0, bs, &etot);
-            if (f) {
-                const long long o = erun + eex;
-                cp->dptr[run + ex] = o;
-                long long e = s0;
-                for (; e + 3 < s1; e += 4) {
-                    const int i0 = __ldg(cp->sidx + e), i1 = __ldg(cp->sidx + e + 1);
-                    const int i2 = __ldg(cp->sidx + e + 2), i3 = __ldg(cp->sidx + e + 3);
-                    const double a0 = __ldg(cp->sval + e), a1 = __ldg(cp->sval + e + 1);
-                    const double a2 = __ldg(cp->sval + e + 2), a3 = __ldg(cp->sval + e + 3);
-                    const long long d = o + (e - s0);
-                    cp->didx[d] = i0;
-                    cp->didx[d + 1] = i1;
-                    cp->didx[d + 2] = i2;
-                    cp->didx[d + 3] = i3;
-                    cp->dval[d] = a0;
-                    cp->dval[d + 1] = a1;
-                    cp->dval[d + 2] = a2;
-                    cp->dval[d + 3] = a3;
-                }
-                for (; e < s1; ++e) {
-                    cp->didx[o + (e - s0)] = __ldg(cp->sidx + e);
-                    cp->dval[o + (e - s0)] = __ldg(cp->sval + e);
-                }
-            }
-            erun += etot;
-        }
         run += tot;
     }
-    if (cp && blockIdx.x == 0 && threadIdx.x == 0) cp->dptr[total] = tab2[nct - 1];
     return total;
 }
 
 // ---------------------------------------------------------------------------
-// Block extraction: the nonzeros of `nlines` CSR rows (or CSC columns) whose
-// other index is selected (map[idx] >= 0), renumbered through map.  Output is
-// a CSR (CSC) over all nlines lines, so A_U keeps all m rows and A^J all n
-// columns, and both block products are gathers (no atomics).
+// Block extraction in one pass: for each line (CSR row or CSC column) of A,
+// the entries whose other index is selected (map[idx] >= 0) are written,
+// renumbered through map, at the start of the line's own slot in A's arrays
+// (oidx/oval[ptr[l] .. ptr[l] + ocnt[l])).  No scan over the grid is needed;
+// the block products read each line as (ptr[l], ocnt[l]).  A_U keeps all m
+// rows and A^J all n columns, so both block products are gathers.
+// Partial: the number of extracted entries.
 // ---------------------------------------------------------------------------
 struct Lines {
     const long long *ptr;
@@ -508,61 +456,49 @@ struct Lines {
     int L;
 };
 
-__device__ __forceinline__ void phase_extract_count(const Params &P, const Lines &A, const int *map,
-                                                    BlockScratch &bs) {
+__device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, const int *map,
+                                              int *ocnt, int *oidx, double *oval,
+                                              BlockScratch &bs) {
     const Grp G(A.L);
-    const Chunk C(A.n, blockIdx.x, gridDim.x);
-    const long long per_tile = (long long)(blockDim.x >> 5) * G.rpw;
-    long long cnt = 0;
-    for (long long tb = C.lo; tb < C.hi; tb += per_tile) {
-        const long long i = tb + (long long)(threadIdx.x >> 5) * G.rpw + G.sub;
-        if (i < C.hi) cnt += lane_count(__ldg(A.ptr + i) + G.sl, __ldg(A.ptr + i + 1), G.L, A.idx, map);
-    }
-    cnt = block_sum(cnt, bs);
-    if (threadIdx.x == 0) P.pi[I_NNZ * gridDim.x + blockIdx.x] = cnt;
-}
-
-__device__ __forceinline__ long long phase_extract_write(const Params &P, const Lines &A,
-                                                         const int *map, long long *optr,
-                                                         int *oidx, double *oval, long long *tab,
-                                                         BlockScratch &bs) {
-    const int nct = gridDim.x;
-    partials_prefix(P.pi + I_NNZ * nct, nct, tab, bs);
-    const long long total = tab[nct - 1];
-    const Grp G(A.L);
-    const Chunk C(A.n, blockIdx.x, nct);
-    const long long per_tile = (long long)(blockDim.x >> 5) * G.rpw;
-    long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
-    for (long long tb = C.lo; tb < C.hi; tb += per_tile) {
-        const long long i = tb + (long long)(threadIdx.x >> 5) * G.rpw + G.sub;
-        const bool valid = i < C.hi;
+    const long long L = G.L;
+    long long total = 0;
+    for (long long base = gwarp() * G.rpw; base < A.n; base += nwarps() * G.rpw) {
+        const long long i = base + G.sub;
+        const bool valid = i < A.n;
         const long long e0 = valid ? __ldg(A.ptr + i) : 0;
         const long long e1 = valid ? __ldg(A.ptr + i + 1) : 0;
-        int c = lane_count(e0 + G.sl, e1, G.L, A.idx, map);
-        c = group_sum(c, G.L);
-        long long tot;
-        const long long ex = block_excl_scan<long long>((valid && G.sl == 0) ? c : 0, bs, &tot);
-        const long long start = run + __shfl_sync(kFull, ex, G.lead);
-        if (valid && G.sl == 0) optr[i] = start;
-        int nit = valid ? (int)((e1 - e0 + G.L - 1) / G.L) : 0;
-        nit = __reduce_max_sync(kFull, (unsigned)nit);
-        long long pos = start;
+        int nit = valid ? (int)((e1 - e0 + 4 * L - 1) / (4 * L)) : 0;
+        nit = (int)__reduce_max_sync(kFull, (unsigned)nit);
+        long long pos = e0;
         for (int it = 0; it < nit; ++it) {
-            const long long e = e0 + (long long)it * G.L + G.sl;
-            int p = -1;
-            if (valid && e < e1) p = map[__ldg(A.idx + e)];
-            const unsigned gm = G.mine(__ballot_sync(kFull, p >= 0));
-            if (p >= 0) {
-                const long long o = pos + __popc(gm & ((1u << G.sl) - 1u));
-                oidx[o] = p;
-                oval[o] = __ldg(A.val + e);
+            // four entries per lane per trip: index loads, then map gathers
+            const long long e = e0 + (long long)it * 4 * L + G.sl;
+            int p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long f = e + q * L;
+                p[q] = (valid && f < e1) ? __ldg(A.idx + f) : -1;
             }
-            pos += __popc(gm);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p[q] = p[q] >= 0 ? map[p[q]] : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned gm = G.mine(__ballot_sync(kFull, p[q] >= 0));
+                if (p[q] >= 0) {
+                    const long long o = pos + __popc(gm & ((1u << G.sl) - 1u));
+                    oidx[o] = p[q];
+                    oval[o] = __ldg(A.val + e + q * L);
+                }
+                pos += __popc(gm);
+            }
         }
-        run += tot;
+        if (valid && G.sl == 0) {
+            ocnt[i] = (int)(pos - e0);
+            total += pos - e0;
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) optr[A.n] = total;
-    return total;
+    total = block_sum(total, bs);
+    if (threadIdx.x == 0) P.pi[I_NNZ * gridDim.x + blockIdx.x] = total;
 }
 
 __device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {
