@@ -64,8 +64,15 @@ def dist_env():
 
 
 def make_system(rank: int):
+    """The benchmark system of this rank (independent systems per rank)."""
     w = WORKLOAD
     return workloads.sparse_ls(w["m"], w["n"], w["k"], sigma=w["sigma"], seed=w["seed"] + rank)
+
+
+def make_system_small(rank: int):
+    """The same recipe at 2000 x 500 (for host-side tests)."""
+    w = WORKLOAD
+    return workloads.sparse_ls(2000, 500, w["k"], sigma=w["sigma"], seed=w["seed"] + rank)
 
 
 # ---------------------------------------------------------------------------
@@ -264,14 +271,7 @@ def run_ours(args):
     ms = [a.elapsed_time(bb) for a, bb in ev]
     total_s = sum(ms) / 1e3
     iters = sum(s.iters for s in stats)
-    if dist is not None:
-        t = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_max, iters_all = float(tmax[0]), float(t[1])
-    else:
-        total_max, iters_all = total_s, float(iters)
+    total_max, iters_all = aggregate(total_s, iters, dist, dev)
     value = iters_all / total_max
 
     # roofline of the dominant kernel (the persistent solve kernel): algorithmic
@@ -341,6 +341,19 @@ def run_ours(args):
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def aggregate(total_s: float, iters: int, dist=None, device=None):
+    """Whole-job numbers over the ranks: the slowest rank's timed seconds and
+    the outer iterations of all ranks (each rank solved its own system)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_s), float(iters)
+    import torch
+    t = torch.tensor([total_s, float(iters)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
 
 
 def source_hash() -> str:

@@ -190,7 +190,11 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
     out.val = nullptr;
     const SmemArena save = A;
     long long *ps = A.take<long long>(out.nl + 1);
-    if (!ps) return out;
+    long long *gs = ps ? A.take<long long>(out.nl) : nullptr;  // global start of each line
+    if (!gs) {
+        A = save;
+        return out;
+    }
     // line lengths -> local offsets (exclusive scan in line order)
     long long run = 0;
     for (int base = 0; base < out.nl; base += blockDim.x) {
@@ -200,6 +204,7 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
             long long b, e;
             line_span(S, C.lo + li, b, e);
             len = e - b;
+            gs[li] = b;
         }
         long long tot;
         const long long ex = block_excl_scan<long long>(len, bs, &tot);
@@ -215,15 +220,19 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
         return out;
     }
     __syncthreads();
-    // warp per line, lanes over entries
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int li = warp; li < out.nl; li += blockDim.x >> 5) {
-        long long b, e;
-        line_span(S, C.lo + li, b, e);
-        const long long o = ps[li];
-        for (long long k = lane; k < e - b; k += 32) {
-            is[o + k] = S.idx[b + k];
-            vs[o + k] = S.val[b + k];
+    // a group of L lanes per line (one thread per line for short lines)
+    {
+        const Grp G(S.L);
+        const int per = (blockDim.x >> 5) * G.rpw;
+        for (int base = 0; base < out.nl; base += per) {
+            const int li = base + (threadIdx.x >> 5) * G.rpw + G.sub;
+            if (li < out.nl) {
+                const long long b = gs[li], o = ps[li], len = ps[li + 1] - o;
+                for (long long k = G.sl; k < len; k += G.L) {
+                    is[o + k] = S.idx[b + k];
+                    vs[o + k] = S.val[b + k];
+                }
+            }
         }
     }
     __syncthreads();

@@ -45,3 +45,17 @@ def test_host_only_calls():
     assert rg._lib.rgdbek_create(ctypes.byref(h), 0, 5, 0, None, None, None, 0, None, None) \
         == rg.ERR_INVALID_ARG
     assert rg._lib.rgdbek_solve(None, None, None, 1e-8, 10, 0, None) == rg.ERR_INVALID_ARG
+
+
+def test_size_limits_rejected_before_any_device_call():
+    gpu_util.build_library()
+    import numpy as np
+    import paper_2509_19267_gb300 as rg
+    h = ctypes.c_void_p()
+    rp = np.zeros(2, dtype=np.int64)
+    for m, n in ((2**31, 5), (5, 2**31), (-1, 5)):
+        assert rg._lib.rgdbek_create(ctypes.byref(h), m, n, 0, rp.ctypes.data, None, None, 0,
+                                     None, None) == rg.ERR_INVALID_ARG
+    bad = rg.default_options(eta_col=1.5)
+    assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 0, rp.ctypes.data, None, None, 0,
+                                 ctypes.byref(bad), None) == rg.ERR_INVALID_ARG
