@@ -101,6 +101,21 @@ def algorithmic_bytes(st, m: int, n: int, nnz: int) -> float:
     return float(full_passes + selection + extraction + caching + zstep + lsqr_u + lsqr_j)
 
 
+# FP64 flops of one solve: 2 per stored nonzero per sparse product (the
+# vector updates are O(m + n) and left out).  Per outer iteration: A^T z and
+# A^T t in the column pass, A xt in the residual pass; per inner solve: the
+# first A_U^T z (or A^J-side product), two products per LSQR step, and the
+# z update A_U y.
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no FP64 tensor path)
+
+
+def algorithmic_flops(st, nnz: int) -> float:
+    it = st.iters
+    full = 2 * nnz * (3 * it + 2)
+    inner = 2 * (2 * st.lsqr_nnz_u + 2 * st.sum_nnz_u) + 2 * (2 * st.lsqr_nnz_j + st.sum_nnz_j)
+    return float(full + inner)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -279,6 +294,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     bytes_per = [algorithmic_bytes(s, S.m, S.n, S.nnz) for s in stats]
     achieved = sum(bytes_per) / total_s / 1e9
+    flops_per = [algorithmic_flops(s, S.nnz) for s in stats]
+    fp64_tflops = sum(flops_per) / total_s / 1e12
     traffic = None
     tp = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
     if os.path.exists(tp):
@@ -330,7 +347,11 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "solve_kernel (persistent, one launch per solve)",
                          "peak_source": peak_kind,
-                         "algorithmic_bytes_per_launch": statistics.mean(bytes_per)},
+                         "algorithmic_bytes_per_launch": statistics.mean(bytes_per),
+                         "fp64": {"flops_per_launch": statistics.mean(flops_per),
+                                  "achieved_tflops": fp64_tflops,
+                                  "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal",
+                                  "frac": fp64_tflops / FP64_PEAK_TFLOPS}},
             "spmv": spmv,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -384,6 +405,8 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
             fn()
         ts = []
         for i in range(10):
+            # the flush (a 256 MiB write) evicts A from L2 and keeps the GPU
+            # busy while the host queues the timed launch
             flush.fill_(float(i))
             a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
