@@ -24,6 +24,10 @@ Parity status of each routine (what pins it, in ``tests/test_oracle_*.py``):
                 Pythagoras identity (Eq. 5) per iteration, the linear-rate
                 bound of Theorem 2.3, and the mean iteration counts of
                 Tables 1 and 2.
+  backward      (implicit adjoint, in this module) central finite
+                differences of numpy lstsq / pinv solutions, along
+                rank-preserving directions for rank-deficient A, and the
+                scaling identities <dL/db, b> = g^T x, <dL/dA, A> = -g^T x
 """
 from __future__ import annotations
 
@@ -344,3 +348,94 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
             res.zs = keep["zs"][:res.iters + 1].copy()
             res.xs = keep["xs"][:res.iters + 1, :n].copy()
     return res
+
+
+# ---------------------------------------------------------------------------
+# Implicit adjoint of the solve
+#
+# The method converges to x = A^+ b, the minimum-norm least-squares solution
+# (the convergence theorem of Section 2).  For a loss L(x) with gradient
+# g = dL/dx, the derivative of the pseudo-inverse (Golub and Pereyra, "The
+# differentiation of pseudo-inverses and nonlinear least squares problems",
+# SIAM J. Numer. Anal. 10, 1973, Theorem 4.3), taken along perturbations that
+# keep rank(A), gives
+#   dL/db = w,                          w = A^+T g
+#   dL/dA = r v^T - w x^T + u p^T,      r = b - A x,  v = A^+ w,
+#                                       u = A^+T x,   p = (I - A^+ A) g
+# The last term vanishes when A has full column rank (p = 0).  Only the
+# entries on A's sparsity pattern are returned.
+# ---------------------------------------------------------------------------
+def transpose(A, n: int):
+    """CSR of A^T (n rows), column indices ascending within each row."""
+    rp, ci, av = _csr(A)
+    m = len(rp) - 1
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp))
+    order = np.lexsort((rows, ci))          # by column of A, then by row
+    counts = np.bincount(ci, minlength=n)
+    tp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=tp[1:])
+    return tp, rows[order].astype(np.int32), av[order].copy()
+
+
+@dataclass
+class Adjoint:
+    grad_b: np.ndarray
+    grad_vals: np.ndarray
+    w: np.ndarray
+    v: np.ndarray
+    u: np.ndarray | None
+    p: np.ndarray | None
+    solves: list          # Result of each inner solve: w, v[, u, q]
+
+
+def backward(A, b, x, g, opts: Options | None = None, n: int | None = None,
+             rank_term: bool = False) -> Adjoint:
+    """Gradients of L(x), x = A^+ b, from inner Algorithm 1 solves.
+
+    w solves A^T w = g (minimum norm: w = A^+T g), v solves A v = w, and with
+    rank_term u solves A^T u = x and q solves A q = A g (p = g - q).  Solve i
+    (0, 1, 2, 3 in that order) uses seed opts.seed + i."""
+    import dataclasses
+    opts = opts or Options()
+    rp, ci, av = _csr(A)
+    m = len(rp) - 1
+    if n is None:
+        n = int(ci.max()) + 1 if len(ci) else 0
+    At = transpose(A, n)
+    b = np.asarray(b, np.float64)
+    x = np.asarray(x, np.float64)
+    g = np.asarray(g, np.float64)
+    o = [dataclasses.replace(opts, seed=opts.seed + i) for i in range(4)]
+    sw = solve(At, g, o[0], n=m)
+    sv = solve((rp, ci, av), sw.x, o[1], n=n)
+    w, v = sw.x, sv.x
+    r = b - spmv((rp, ci, av), x)
+    rows = np.repeat(np.arange(m), np.diff(rp))
+    gv = r[rows] * v[ci] - w[rows] * x[ci]
+    solves = [sw, sv]
+    u = p = None
+    if rank_term:
+        su = solve(At, x, o[2], n=m)
+        sq = solve((rp, ci, av), spmv((rp, ci, av), g), o[3], n=n)
+        u, p = su.x, g - sq.x
+        gv = gv + u[rows] * p[ci]
+        solves += [su, sq]
+    return Adjoint(grad_b=w.copy(), grad_vals=gv, w=w, v=v, u=u, p=p, solves=solves)
+
+
+def backward_dense(D, b, g, rank_term: bool = True, rcond: float = 1e-12):
+    """The same gradients from the dense pseudo-inverse (small cases): the
+    definition written out, for pinning the iterative version.  Returns
+    (grad_b, dense dL/dA)."""
+    D = np.asarray(D, np.float64)
+    Ap = np.linalg.pinv(D, rcond=rcond)
+    x = Ap @ b
+    w = Ap.T @ g
+    v = Ap @ w
+    r = b - D @ x
+    G = np.outer(r, v) - np.outer(w, x)
+    if rank_term:
+        u = Ap.T @ x
+        p = g - Ap @ (D @ g)
+        G = G + np.outer(u, p)
+    return w, G

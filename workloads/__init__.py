@@ -16,6 +16,13 @@ Workloads (the recipe of each is restated in the design notes):
   sprandn_like        every entry nonzero independently with probability
                       `density`, N(0,1) values, b = A x*  (the random matrices
                       of Tables 1 and 2: 99% sparse)
+  blur_image          the s^2 x s^2 separable Gaussian blur T (x) T (9 taps,
+                      sigma 1.5, taps summing to 1, zero boundary; up to 81
+                      nonzeros per row), a blocky test image (uniform [0,1]
+                      background under 8-32 random rectangles of U[0,1]
+                      values) and b = A x + 1% Gaussian noise
+  deblur_regularised  [A; lam I] and [b; 0] for that blur (lam = 0.05): the
+                      full-column-rank system of the adjoint workload
 """
 from __future__ import annotations
 
@@ -128,3 +135,64 @@ def from_dense(D: np.ndarray, b: np.ndarray, name: str = "dense", x_true=None,
     m, n = D.shape
     return System(name, m, n, rp, ci, av, np.asarray(b, np.float64),
                   np.zeros(n) if x_true is None else x_true, consistent)
+
+
+def gaussian_taps(sigma: float = 1.5, taps: int = 9) -> np.ndarray:
+    h = taps // 2
+    w = np.exp(-0.5 * (np.arange(-h, h + 1) / sigma) ** 2)
+    return w / w.sum()
+
+
+def blur_csr(side: int, sigma: float = 1.5, taps: int = 9):
+    """CSR of T (x) T, T the side x side banded 1-D blur with zero boundary.
+
+    Row p*side + q holds T[p, p'] T[q, q'] at column p'*side + q' (sorted)."""
+    w = gaussian_taps(sigma, taps)
+    h = taps // 2
+    s = side
+    off = np.arange(-h, h + 1)
+    col1 = np.arange(s)[:, None] + off[None, :]                  # (s, taps)
+    ok1 = (col1 >= 0) & (col1 < s)
+    val1 = np.where(ok1, w[None, :], 0.0)
+    # rows (p, q), entries (a, c): column col1[p, a] * s + col1[q, c]
+    cols = col1[:, None, :, None] * s + col1[None, :, None, :]   # (s, s, taps, taps)
+    vals = val1[:, None, :, None] * val1[None, :, None, :]
+    ok = ok1[:, None, :, None] & ok1[None, :, None, :]
+    cols = cols.reshape(s * s, taps * taps)
+    vals = vals.reshape(s * s, taps * taps)
+    ok = ok.reshape(s * s, taps * taps)
+    counts = ok.sum(axis=1)
+    row_ptr = np.zeros(s * s + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, cols[ok].astype(np.int32), vals[ok].astype(np.float64)
+
+
+def blocky_image(rng, side: int) -> np.ndarray:
+    img = rng.random((side, side))
+    for _ in range(int(rng.integers(8, 33))):
+        r0, r1 = np.sort(rng.integers(0, side + 1, size=2))
+        c0, c1 = np.sort(rng.integers(0, side + 1, size=2))
+        img[r0:max(r1, r0 + 1), c0:max(c1, c0 + 1)] = rng.random()
+    return img.reshape(-1)
+
+
+def blur_image(side: int = 256, seed: int = 4) -> System:
+    rng = np.random.default_rng(seed)
+    rp, ci, av = blur_csr(side)
+    x = blocky_image(rng, side)
+    clean = _csr_matvec(rp, ci, av, x)
+    rms = float(np.sqrt(np.mean(clean ** 2)))
+    b = clean + 0.01 * rms * rng.standard_normal(side * side)
+    return System(f"blur_{side}x{side}", side * side, side * side, rp, ci, av, b, x, False)
+
+
+def deblur_regularised(side: int = 256, lam: float = 0.05, seed: int = 4) -> System:
+    """[A; lam I] x ~ [b; 0] for the blur of `blur_image` (Tikhonov form)."""
+    B = blur_image(side, seed)
+    N = side * side
+    row_ptr = np.concatenate([B.row_ptr, B.row_ptr[-1] + 1 + np.arange(N, dtype=np.int64)])
+    col_idx = np.concatenate([B.col_idx, np.arange(N, dtype=np.int32)])
+    vals = np.concatenate([B.vals, np.full(N, lam)])
+    b = np.concatenate([B.b, np.zeros(N)])
+    return System(f"deblur_{side}x{side}_lam{lam}", 2 * N, N, row_ptr, col_idx, vals, b,
+                  B.x_true, False)
