@@ -168,6 +168,39 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
                          const double *tol, int64_t max_iter, uint64_t seed,
                          rgdbek_stats *st);
 
+/* Implicit adjoint of the solve (reverse-mode gradient).  The method
+ * converges to x = A^+ b, the minimum-norm least-squares solution (the
+ * convergence theorem of Section 2).  Given the gradient g = dL/dx of a loss
+ * at that x, the derivative of the pseudo-inverse (Golub and Pereyra 1973,
+ * along perturbations that keep rank(A)) gives
+ *   dL/db    = w                         with w = A^+T g
+ *   dL/dA_ij = r_i v_j - w_i x_j         with r = b - A x, v = A^+ w
+ *              [+ u_i p_j]               with u = A^+T x, p = (I - A^+ A) g
+ * The bracketed term is zero when A has full column rank; it is added only
+ * with flags = RGDBEK_ADJ_RANK_TERM.  Each of w, v, u and A^+(A g) is an
+ * Algorithm 1 solve on the device from a zero start (w and u on A^T, using
+ * the handle's CSC arrays as the CSR form of A^T), with the handle's options,
+ * tolerance tol and cap max_iter; solve i (w, v, u, q in that order) uses
+ * seed + i.  The paper itself has no adjoint; this call builds on its solver.
+ *   b          device double[m]   right-hand side of the forward solve
+ *   x          device double[n]   the forward solution
+ *   grad_x     device double[n]   g
+ *   grad_b     device double[m]   output dL/db, or NULL
+ *   grad_vals  device double[nnz] output dL/dA at the stored entries, in the
+ *                                 CSR order given to rgdbek_create; or NULL
+ *                                 (then only w is solved for)
+ *   st         host rgdbek_stats[4] (w, v, u, q solves; unused ones zeroed),
+ *              or NULL
+ * The handle owns a scratch area of 4m + 2n doubles, allocated on the first
+ * call and freed by rgdbek_destroy.  Returns OK, NOT_CONVERGED (some solve hit
+ * max_iter; the gradients are still written), or the first error of a solve
+ * (its outputs are then not written), INVALID_ARG (a NULL input, tol < 0,
+ * max_iter < 0, unknown flag bits), OOM, CUDA. */
+#define RGDBEK_ADJ_RANK_TERM 1
+int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *grad_x,
+                    double *grad_b, double *grad_vals, double tol, int64_t max_iter,
+                    uint64_t seed, int flags, rgdbek_stats *st);
+
 /* Records the blocks of each iteration of the next solves into device
  * buffers: counts int64[count_cap][4] = (|U_k|, |J_k|, LSQR steps of the
  * column step, of the row step); lists int32[list_cap] = U_0, J_0, U_1, J_1,

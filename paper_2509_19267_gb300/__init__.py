@@ -85,6 +85,8 @@ SIGNATURES = [
                                  ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_solve_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
                                     ctypes.POINTER(rgdbek_stats)]),
+    ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
+                               ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
     ("rgdbek_spmv", _int, [_ptr, _ptr, _ptr]),
     ("rgdbek_spmv_t", _int, [_ptr, _ptr, _ptr]),
@@ -234,6 +236,22 @@ def rgdbek_solve_batched(hs, bs, xs, tols, max_iter: int, seed: int = 0):
     return status, list(S)
 
 
+ADJ_RANK_TERM = 1
+
+
+def rgdbek_backward(h: int, b, x, grad_x, grad_b=None, grad_vals=None, tol: float = 1e-10,
+                    max_iter: int = 100000, seed: int = 0, flags: int = 0,
+                    raise_on_error: bool = True):
+    """Implicit adjoint of x = A^+ b: writes dL/db into grad_b and dL/dA (at the
+    stored entries, CSR order) into grad_vals.  Returns (status, [4 stats])."""
+    S = (rgdbek_stats * 4)()
+    status = _lib.rgdbek_backward(h, _dptr(b), _dptr(x), _dptr(grad_x), _dptr(grad_b),
+                                  _dptr(grad_vals), tol, max_iter, seed, flags, S)
+    if raise_on_error:
+        _check(status, "rgdbek_backward", allow=(OK, NOT_CONVERGED))
+    return status, list(S)
+
+
 def rgdbek_set_trace(h: int, counts=None, lists=None) -> None:
     """counts: int64 CUDA tensor of shape (cap, 4); lists: int32 CUDA tensor."""
     if counts is not None and (counts.dim() != 2 or counts.shape[1] != 4):
@@ -314,6 +332,21 @@ class Solver:
             x = torch.empty(self.n, dtype=torch.float64, device=b.device)
         st = rgdbek_solve(self.handle, b, x, tol, max_iter, seed, raise_on_error)
         return SolveResult(x, st)
+
+    def backward(self, b, x, grad_x, tol: float = 1e-10, max_iter: int = 100000, seed: int = 0,
+                 rank_term: bool = False, want_vals: bool = True, nnz: int | None = None):
+        """(grad_b, grad_vals or None, status, stats) for a loss with gradient grad_x."""
+        import torch
+        grad_b = torch.empty(self.m, dtype=torch.float64, device=b.device)
+        grad_vals = None
+        if want_vals:
+            nnz = self.info().nnz if nnz is None else nnz
+            grad_vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=b.device)
+        status, st = rgdbek_backward(self.handle, b, x, grad_x, grad_b, grad_vals, tol, max_iter,
+                                     seed, ADJ_RANK_TERM if rank_term else 0)
+        if grad_vals is not None:
+            grad_vals = grad_vals[:nnz]
+        return grad_b, grad_vals, status, st
 
     def close(self):
         if getattr(self, "handle", None):

@@ -35,6 +35,11 @@ struct rgdbek_s {
     long long *pi;
     Ctrl *ctrl;
     double *b_stage, *x_stage;
+    // implicit adjoint scratch, allocated by the first rgdbek_backward call:
+    // A x, w, v, u (length m or n, whichever the transposed solves need) and
+    // A g, q
+    double *adj = nullptr;
+    double *adj_ax, *adj_w, *adj_v, *adj_u, *adj_ag, *adj_q;
     // launch shape
     int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
     // trace
@@ -69,28 +74,30 @@ void carve(rgdbek_s *h, Layout &L) {
     h->cv = L.take<double>(nnz);
     h->rn2 = L.take<double>(m);
     h->cn2 = L.take<double>(n);
-    h->z = L.take<double>(m);
-    h->t = L.take<double>(m);
-    h->r = L.take<double>(m);
-    h->epsr = L.take<double>(m);
-    h->uu = L.take<double>(m);
-    h->g = L.take<double>(n);
-    h->epsc = L.take<double>(n);
-    h->vv = L.take<double>(n);
-    h->ww = L.take<double>(n);
-    h->yy = L.take<double>(n);
-    h->dx = L.take<double>(n);
-    h->xt = L.take<double>(n);
+    // Work vectors indexed by rows or by columns are all max(m, n) long, so
+    // that the same workspace serves the solves on A^T of rgdbek_backward.
+    h->z = L.take<double>(mx);
+    h->t = L.take<double>(mx);
+    h->r = L.take<double>(mx);
+    h->epsr = L.take<double>(mx);
+    h->uu = L.take<double>(mx);
+    h->g = L.take<double>(mx);
+    h->epsc = L.take<double>(mx);
+    h->vv = L.take<double>(mx);
+    h->ww = L.take<double>(mx);
+    h->yy = L.take<double>(mx);
+    h->dx = L.take<double>(mx);
+    h->xt = L.take<double>(mx);
     h->Q = L.take<unsigned long long>(mx);
     h->flag = L.take<unsigned char>(mx);
-    h->colpos = L.take<int>(n);
+    h->colpos = L.take<int>(mx);
     h->rowpos = L.take<int>(mx);
-    h->ulist = L.take<int>(n);
-    h->jlist = L.take<int>(m);
-    h->srn = L.take<int>(m);
+    h->ulist = L.take<int>(mx);
+    h->jlist = L.take<int>(mx);
+    h->srn = L.take<int>(mx);
     h->sci = L.take<int>(nnz);
     h->sav = L.take<double>(nnz);
-    h->scn = L.take<int>(n);
+    h->scn = L.take<int>(mx);
     h->sri = L.take<int>(nnz);
     h->scv = L.take<double>(nnz);
     h->dots = L.take<double>(mx);
@@ -136,7 +143,10 @@ int configure_launch(rgdbek_s *h) {
     return RGDBEK_OK;
 }
 
-Params make_params(const rgdbek_s *h) {
+// Kernel parameters for A (transposed = false) or for A^T (transposed =
+// true): the CSC arrays of A are the CSR arrays of A^T and vice versa, and
+// row and column norms trade places.  The trace is recorded for A only.
+Params make_params(const rgdbek_s *h, bool transposed = false) {
     Params P{};
     P.m = h->m;
     P.n = h->n;
@@ -195,6 +205,26 @@ Params make_params(const rgdbek_s *h) {
     P.ipr = h->ipr;
     P.ipc = h->ipc;
     P.dsmem_bytes = kSolveDsmemBytes;
+    if (transposed) {
+        P.m = h->n;
+        P.n = h->m;
+        P.rp = h->cp;
+        P.ci = h->ri;
+        P.av = h->cv;
+        P.cp = h->rp;
+        P.ri = h->ci;
+        P.cv = h->av;
+        P.rn2 = h->cn2;
+        P.cn2 = h->rn2;
+        P.tpr = h->tpc;
+        P.tpc = h->tpr;
+        P.ipr = h->ipc;
+        P.ipc = h->ipr;
+        P.tr_counts = nullptr;
+        P.tr_count_cap = 0;
+        P.tr_lists = nullptr;
+        P.tr_list_cap = 0;
+    }
     return P;
 }
 
@@ -220,8 +250,49 @@ int read_ctrl(rgdbek_s *h) {
     return cuda_status(e);
 }
 
+// One persistent-kernel solve of A x = b (or of A^T x = b when transposed),
+// x0 = 0; reads the control block back into *st.
+int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double tol,
+              long long max_iter, uint64_t seed, rgdbek_stats *st) {
+    Params P = make_params(h, transposed);
+    P.b = b;
+    P.x = x;
+    P.tol = tol;
+    P.max_iter = max_iter;
+    P.seed = seed;
+    P.s_col = num_draws(h->opt.eta_col, P.n);
+    P.s_row = num_draws(h->opt.eta_row, P.m);
+    cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
+    if (e == cudaSuccess) e = launch_solve(P, h->grid, h->block, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rs = read_ctrl(h);
+    if (rs != RGDBEK_OK) return rs;
+    const Ctrl &c = *h->ctrl_host;
+    int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
+    if (st) {
+        st->iters = c.iters;
+        st->inner_u = c.inner_u;
+        st->inner_j = c.inner_j;
+        st->sum_nu = c.sum_nu;
+        st->sum_nj = c.sum_nj;
+        st->sum_nnz_u = c.sum_nnzu;
+        st->sum_nnz_j = c.sum_nnzj;
+        st->lsqr_nnz_u = c.lsqr_nnzu;
+        st->lsqr_nnz_j = c.lsqr_nnzj;
+        st->lsqr_n_u = c.lsqr_nu;
+        st->lsqr_n_j = c.lsqr_nj;
+        st->rel_res = c.rel_res;
+        st->normal_res = c.normal_res;
+        st->rse = c.rse;
+        st->status = status;
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
+    }
+    return status;
+}
+
 void release(rgdbek_s *h) {
     if (!h) return;
+    if (h->adj) cudaFree(h->adj);
     if (h->arena) cudaFree(h->arena);
     if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
     delete h;
@@ -409,40 +480,7 @@ int rgdbek_set_trace(rgdbek_t h, int64_t *counts, int64_t count_cap, int32_t *li
 int rgdbek_solve(rgdbek_t h, const double *b, double *x, double tol, int64_t max_iter,
                  uint64_t seed, rgdbek_stats *st) {
     if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return RGDBEK_ERR_INVALID_ARG;
-    Params P = make_params(h);
-    P.b = b;
-    P.x = x;
-    P.tol = tol;
-    P.max_iter = max_iter;
-    P.seed = seed;
-    P.s_col = num_draws(h->opt.eta_col, h->n);
-    P.s_row = num_draws(h->opt.eta_row, h->m);
-    cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
-    if (e == cudaSuccess) e = launch_solve(P, h->grid, h->block, h->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    int rs = read_ctrl(h);
-    if (rs != RGDBEK_OK) return rs;
-    const Ctrl &c = *h->ctrl_host;
-    int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
-    if (st) {
-        st->iters = c.iters;
-        st->inner_u = c.inner_u;
-        st->inner_j = c.inner_j;
-        st->sum_nu = c.sum_nu;
-        st->sum_nj = c.sum_nj;
-        st->sum_nnz_u = c.sum_nnzu;
-        st->sum_nnz_j = c.sum_nnzj;
-        st->lsqr_nnz_u = c.lsqr_nnzu;
-        st->lsqr_nnz_j = c.lsqr_nnzj;
-        st->lsqr_n_u = c.lsqr_nu;
-        st->lsqr_n_j = c.lsqr_nj;
-        st->rel_res = c.rel_res;
-        st->normal_res = c.normal_res;
-        st->rse = c.rse;
-        st->status = status;
-        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
-    }
-    return status;
+    return run_solve(h, false, b, x, tol, max_iter, seed, st);
 }
 
 int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double tol,
@@ -473,6 +511,79 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
         else if (s == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = s;
     }
     return worst;
+}
+
+int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *grad_x,
+                    double *grad_b, double *grad_vals, double tol, int64_t max_iter,
+                    uint64_t seed, int flags, rgdbek_stats *st) {
+    if (!h || !b || !x || !grad_x || !(tol >= 0.0) || max_iter < 0 ||
+        (flags & ~RGDBEK_ADJ_RANK_TERM) != 0)
+        return RGDBEK_ERR_INVALID_ARG;
+    const bool rank_term = (flags & RGDBEK_ADJ_RANK_TERM) != 0;
+    const long long m = h->m, n = h->n;
+    cudaError_t e = cudaSuccess;
+    if (!h->adj) {
+        Layout L;
+        for (int pass = 0; pass < 2; ++pass) {
+            h->adj_ax = L.take<double>(m);
+            h->adj_w = L.take<double>(m);
+            h->adj_v = L.take<double>(n);
+            h->adj_u = L.take<double>(m);
+            h->adj_ag = L.take<double>(m);
+            h->adj_q = L.take<double>(n);
+            if (pass == 0) {
+                void *p = nullptr;
+                if ((e = cudaMalloc(&p, L.off)) != cudaSuccess) return cuda_status(e);
+                h->adj = static_cast<double *>(p);
+                L = Layout();
+                L.base = static_cast<char *>(p);
+            }
+        }
+    }
+    rgdbek_stats local[4];
+    rgdbek_stats *S = st ? st : local;
+    std::memset(S, 0, 4 * sizeof(rgdbek_stats));
+    int worst = RGDBEK_OK;
+    auto fold = [&](int s) {
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        else if (s == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = s;
+    };
+    // w = A^+T g: the minimum-norm solution of A^T w = g
+    int s0 = run_solve(h, true, grad_x, h->adj_w, tol, max_iter, seed, S + 0);
+    fold(s0);
+    if (s0 < 0) return s0;
+    if (grad_b) {
+        e = cudaMemcpyAsync(grad_b, h->adj_w, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice,
+                            h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (!grad_vals) {
+        e = cudaStreamSynchronize(h->stream);
+        return e == cudaSuccess ? worst : cuda_status(e);
+    }
+    // v = A^+ w
+    int s1 = run_solve(h, false, h->adj_w, h->adj_v, tol, max_iter, seed + 1, S + 1);
+    fold(s1);
+    if (s1 < 0) return s1;
+    const Params P = make_params(h);
+    if (rank_term) {
+        // u = A^+T x and q = A^+ (A g), so that p = g - q = (I - A^+ A) g
+        int s2 = run_solve(h, true, x, h->adj_u, tol, max_iter, seed + 2, S + 2);
+        fold(s2);
+        if (s2 < 0) return s2;
+        if ((e = launch_spmv(P, h->grid, h->block, grad_x, h->adj_ag, h->stream)) != cudaSuccess)
+            return cuda_status(e);
+        int s3 = run_solve(h, false, h->adj_ag, h->adj_q, tol, max_iter, seed + 3, S + 3);
+        fold(s3);
+        if (s3 < 0) return s3;
+    }
+    e = launch_spmv(P, h->grid, h->block, x, h->adj_ax, h->stream);
+    if (e == cudaSuccess)
+        e = launch_adjoint_vals(P, h->grid, h->block, b, h->adj_ax, h->adj_w, h->adj_v, x,
+                                rank_term ? h->adj_u : nullptr, grad_x,
+                                rank_term ? h->adj_q : nullptr, grad_vals, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? worst : cuda_status(e);
 }
 
 int rgdbek_spmv(rgdbek_t h, const double *x, double *y) {

@@ -26,6 +26,12 @@ cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, d
                         cudaStream_t s);
 cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
                           cudaStream_t s);
+// gv[e] = (b_i - ax_i) v_j - w_i x_j [+ u_i (g_j - q_j) when u != nullptr]
+// over the stored entries e = (i, j) of P's CSR form
+cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const double *b,
+                                const double *ax, const double *w, const double *v,
+                                const double *x, const double *u, const double *g,
+                                const double *q, double *gv, cudaStream_t s);
 cudaError_t launch_weights(const double *v, const double *norm2, long long len, double *eps,
                            Ctrl *ctrl, int grid, int block, cudaStream_t s);
 // CTAs of `block` threads of the persistent kernels that fit on one SM

@@ -740,6 +740,32 @@ __global__ void __launch_bounds__(kSolveMaxThreads) spmv_t_kernel(const Params P
     cols_matvec(P, z, g);
 }
 
+// Gradient of a loss with respect to the stored entries of A (the implicit
+// adjoint of x = A^+ b; Golub-Pereyra derivative of the pseudo-inverse):
+//   gv[e] = (b_i - (Ax)_i) v_j - w_i x_j  [+ u_i (g_j - q_j)]  for entry e = (i, j).
+// Each product and difference is rounded on its own (no contraction), in
+// that order.  L lanes per row stream the row's column indices once.
+__global__ void __launch_bounds__(kSolveMaxThreads)
+    adjoint_vals_kernel(const Params P, const double *b, const double *ax, const double *w,
+                        const double *v, const double *x, const double *u, const double *g,
+                        const double *q, double *gv) {
+    const Grp G(P.ipr);
+    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+        const long long i = base + G.sub;
+        if (i >= P.m) continue;
+        const double ri = __dsub_rn(b[i], ax[i]);
+        const double wi = w[i];
+        const double ui = u ? u[i] : 0.0;
+        const long long e1 = __ldg(P.rp + i + 1);
+        for (long long e = __ldg(P.rp + i) + G.sl; e < e1; e += G.L) {
+            const int j = __ldg(P.ci + e);
+            double d = __dsub_rn(__dmul_rn(ri, v[j]), __dmul_rn(wi, x[j]));
+            if (u) d = __dadd_rn(d, __dmul_rn(ui, __dsub_rn(g[j], q[j])));
+            gv[e] = d;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kSolveMaxThreads) weights_kernel(const double *v,
                                                                    const double *norm2,
                                                                    long long len, double *eps,
@@ -860,6 +886,14 @@ cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, d
 cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
                           cudaStream_t s) {
     spmv_t_kernel<<<grid, block, 0, s>>>(P, z, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const double *b,
+                                const double *ax, const double *w, const double *v,
+                                const double *x, const double *u, const double *g,
+                                const double *q, double *gv, cudaStream_t s) {
+    adjoint_vals_kernel<<<grid, block, 0, s>>>(P, b, ax, w, v, x, u, g, q, gv);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,8 @@ def test_host_only_calls():
     assert rg._lib.rgdbek_create(ctypes.byref(h), 0, 5, 0, None, None, None, 0, None, None) \
         == rg.ERR_INVALID_ARG
     assert rg._lib.rgdbek_solve(None, None, None, 1e-8, 10, 0, None) == rg.ERR_INVALID_ARG
+    assert rg._lib.rgdbek_backward(None, None, None, None, None, None, 1e-8, 10, 0, 0,
+                                   None) == rg.ERR_INVALID_ARG
 
 
 def test_size_limits_rejected_before_any_device_call():
