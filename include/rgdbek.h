@@ -50,6 +50,19 @@ extern "C" {
 #define RGDBEK_STOP_NORMAL 2   /* ||A^T (b - A x)|| / ||A^T b|| <= tol            */
 #define RGDBEK_STOP_RSE 3      /* ||A x - b||^2 / ||b||^2 <= tol (Section 3.1)    */
 
+/* ---- arithmetic of the inner solves --------------------------------------- */
+#define RGDBEK_PRECISION_FP64 0  /* everything in FP64                          */
+/* The inner LSQR products B v and B^T u run in FP32: the block's values are
+ * held as float, the gathered vectors as float copies, and each dot product
+ * accumulates with Kahan compensation.  The outer iteration stays FP64 (the
+ * products A^T z and b - A x, the norms, weights, LSQR scalars and vectors,
+ * and the stopping test), so it refines the FP32 block solves: the limit and
+ * the stopping rule are those of the FP64 solve.  The inner tolerance is
+ * raised to at least RGDBEK_FP32_INNER_TOL, below which FP32 products carry
+ * no information. */
+#define RGDBEK_PRECISION_FP32_INNER 1
+#define RGDBEK_FP32_INNER_TOL 1e-6
+
 typedef struct rgdbek_s *rgdbek_t;
 
 typedef struct {
@@ -64,6 +77,7 @@ typedef struct {
     uint64_t system_id;    /* second word of the Philox key                         */
     int blocks_per_sm;     /* persistent grid: CTAs per SM, 0 = largest that fits   */
     int threads_per_block; /* 0 = 1024; a multiple of 32 in [64, 1024]              */
+    int precision;         /* RGDBEK_PRECISION_*                                    */
 } rgdbek_options;
 
 typedef struct {
@@ -107,7 +121,7 @@ typedef struct {
 /* Fills *opt with the defaults: eta_col = eta_row = 0.5 (the paper's
  * sequential experiments, Section 3.1), random selection, inner_tol = 1e-10,
  * inner_max = 200, stop_rule = AUTO, no time budget, system_id = 0,
- * automatic launch shape. */
+ * automatic launch shape, precision = FP64. */
 void rgdbek_default_options(rgdbek_options *opt);
 
 /* Creates a solver for the m x n matrix A given in CSR form (Eq. 1).

@@ -33,6 +33,9 @@ STOP_NORMAL = 2
 STOP_RSE = 3
 PHASE_NAMES = ("setup", "col_pass", "col_select", "col_extract", "col_lsqr", "z_update",
                "row_select", "row_extract", "row_lsqr", "residual_pass")
+PRECISION_FP64 = 0
+PRECISION_FP32_INNER = 1
+FP32_INNER_TOL = 1e-6
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -45,7 +48,7 @@ class rgdbek_options(ctypes.Structure):
     _fields_ = [
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", _int), ("inner_tol", _dbl),
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
-        ("blocks_per_sm", _int), ("threads_per_block", _int),
+        ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
     ]
 
 
@@ -358,3 +361,61 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Autograd: the solve as a differentiable function of A's values and b
+# ---------------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class RGDBEKLstsq(torch.autograd.Function):
+        """x = A^+ b by rgdbek_solve; backward by rgdbek_backward (the implicit
+        adjoint: no iterate is stored or unrolled)."""
+
+        @staticmethod
+        def forward(ctx, vals, b, row_ptr, col_idx, m, n, tol, max_iter, seed, adj_tol,
+                    rank_term, options):
+            solver = Solver(m, n, row_ptr, col_idx, vals.detach().contiguous(), **options)
+            res = solver.solve(b.detach().contiguous(), tol=tol, max_iter=max_iter, seed=seed)
+            ctx.solver = solver
+            ctx.nnz = vals.shape[0]
+            ctx.adj = (adj_tol, max_iter, seed + 1, rank_term)
+            ctx.save_for_backward(b, res.x)
+            ctx.stats = res.stats
+            return res.x
+
+        @staticmethod
+        def backward(ctx, grad_x):
+            b, x = ctx.saved_tensors
+            adj_tol, max_iter, seed, rank_term = ctx.adj
+            gb, gv, _, _ = ctx.solver.backward(b.detach().contiguous(), x,
+                                               grad_x.contiguous(), tol=adj_tol,
+                                               max_iter=max_iter, seed=seed,
+                                               rank_term=rank_term,
+                                               want_vals=ctx.needs_input_grad[0], nnz=ctx.nnz)
+            ctx.solver.close()
+            return (gv if ctx.needs_input_grad[0] else None,
+                    gb if ctx.needs_input_grad[1] else None,
+                    None, None, None, None, None, None, None, None, None, None)
+
+    return RGDBEKLstsq
+
+
+_LSTSQ = None
+
+
+def rgdbek_lstsq(row_ptr, col_idx, vals, b, m: int, n: int, tol: float = 1e-10,
+                 max_iter: int = 100000, seed: int = 0, adj_tol: float | None = None,
+                 rank_term: bool = False, **options):
+    """Differentiable minimum-norm least-squares solve x = A^+ b.
+
+    row_ptr (int64, m+1), col_idx (int32, nnz), vals (float64, nnz) and b
+    (float64, m) are CUDA tensors; gradients flow to vals (on A's pattern) and
+    to b.  Each call creates a handle for the given values; the backward pass
+    reuses it and closes it."""
+    global _LSTSQ
+    if _LSTSQ is None:
+        _LSTSQ = _autograd_function()
+    return _LSTSQ.apply(vals, b, row_ptr, col_idx, m, n, tol, max_iter, seed,
+                        tol if adj_tol is None else adj_tol, rank_term, options)

@@ -31,6 +31,7 @@ struct rgdbek_s {
     int *sci, *sri;
     double *sav, *scv;
     double *dots, *dots2;
+    float *vv32, *uu32;
     double *pd;
     long long *pi;
     Ctrl *ctrl;
@@ -102,6 +103,8 @@ void carve(rgdbek_s *h, Layout &L) {
     h->scv = L.take<double>(nnz);
     h->dots = L.take<double>(mx);
     h->dots2 = L.take<double>(mx);
+    h->vv32 = L.take<float>(mx);
+    h->uu32 = L.take<float>(mx);
     h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
     h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
     h->ctrl = L.take<Ctrl>(1);
@@ -118,6 +121,8 @@ int check_options(const rgdbek_options &o) {
     if (o.stop_rule < 0 || o.stop_rule > 3) return RGDBEK_ERR_INVALID_ARG;
     if (!(o.time_budget_s >= 0.0)) return RGDBEK_ERR_INVALID_ARG;
     if (o.blocks_per_sm < 0 || o.threads_per_block < 0) return RGDBEK_ERR_INVALID_ARG;
+    if (o.precision != RGDBEK_PRECISION_FP64 && o.precision != RGDBEK_PRECISION_FP32_INNER)
+        return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -194,7 +199,12 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.tr_list_cap = h->tr_list_cap;
     P.eta_col = h->opt.eta_col;
     P.eta_row = h->opt.eta_row;
-    P.inner_tol = h->opt.inner_tol;
+    P.fp32_inner = h->opt.precision == RGDBEK_PRECISION_FP32_INNER;
+    P.inner_tol = P.fp32_inner && h->opt.inner_tol < RGDBEK_FP32_INNER_TOL
+                      ? RGDBEK_FP32_INNER_TOL
+                      : h->opt.inner_tol;
+    P.vv32 = h->vv32;
+    P.uu32 = h->uu32;
     P.inner_max = h->opt.inner_max;
     P.stop_rule = h->opt.stop_rule;
     P.selection = h->opt.selection;
@@ -314,6 +324,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->system_id = 0;
     opt->blocks_per_sm = 0;
     opt->threads_per_block = 0;
+    opt->precision = RGDBEK_PRECISION_FP64;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,

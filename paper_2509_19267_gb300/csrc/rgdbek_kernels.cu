@@ -152,10 +152,12 @@ __device__ __forceinline__ void line_span(const SideC &S, long long l, long long
 struct CtaSide {
     const long long *ptr;
     const int *idx;
-    const double *val;
+    const double *val;   // cached values (FP64 inner products)
+    const float *valf;   // cached values (FP32 inner products)
     int nl;
     long long lo;
-    int L;
+    int L;               // lanes per line, FP64 products
+    int Lf;              // lanes per line, FP32 products
     bool cached;
     SideC g;
 };
@@ -176,18 +178,22 @@ struct SmemArena {
 };
 
 // Copies this CTA's chunk of a side into shared memory (compacting the
-// lines), if it fits.  All threads of the CTA call it.
+// lines), if it fits; with fp32 the values are stored as float.  All threads
+// of the CTA call it.
+template <bool fp32>
 __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, BlockScratch &bs) {
     const Chunk C(S.n, blockIdx.x, gridDim.x);
     CtaSide out;
     out.nl = (int)(C.hi - C.lo);
     out.lo = C.lo;
     out.L = S.L;
+    out.Lf = S.L;
     out.g = S;
     out.cached = false;
     out.ptr = nullptr;
     out.idx = nullptr;
     out.val = nullptr;
+    out.valf = nullptr;
     const SmemArena save = A;
     long long *ps = A.take<long long>(out.nl + 1);
     long long *gs = ps ? A.take<long long>(out.nl) : nullptr;  // global start of each line
@@ -212,9 +218,20 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
         run += tot;
     }
     if (threadIdx.x == 0) ps[out.nl] = run;
+    // FP32 products are cheap to reduce across lanes, so they spread each line
+    // over enough lanes for about four entries per lane (one round of
+    // gathers), as far as warps 1.. cover all lines in one pass
+    int Lf = 1;
+    {
+        const long long per_line = out.nl > 0 ? (run + out.nl - 1) / out.nl : 0;
+        const long long lanes = (long long)((blockDim.x >> 5) - 1) * 32;
+        while (Lf < 32 && 4ll * Lf < per_line) Lf *= 2;
+        while (Lf > 1 && (long long)out.nl * Lf > lanes) Lf >>= 1;
+    }
     int *is = A.take<int>(run);
-    double *vs = is ? A.take<double>(run) : nullptr;
-    if (!vs) {
+    double *vs = (is && !fp32) ? A.take<double>(run) : nullptr;
+    float *vf = (is && fp32) ? A.take<float>(run) : nullptr;
+    if (!vs && !vf) {
         A = save;
         __syncthreads();
         return out;
@@ -230,25 +247,80 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
                 const long long b = gs[li], o = ps[li], len = ps[li + 1] - o;
                 for (long long k = G.sl; k < len; k += G.L) {
                     is[o + k] = S.idx[b + k];
-                    vs[o + k] = S.val[b + k];
+                    if (fp32) vf[o + k] = (float)S.val[b + k];
+                    else vs[o + k] = S.val[b + k];
                 }
             }
         }
     }
     __syncthreads();
     out.cached = true;
+    out.Lf = Lf;
     out.ptr = ps;
     out.idx = is;
     out.val = vs;
+    out.valf = vf;
     return out;
+}
+
+// This lane's share of an FP32 dot product over entries e, e + L, ... < e1,
+// Kahan-compensated (Kahan 1965): c carries the rounding error of the running
+// sum into the next term; the lane returns s - c.  Four entries per trip,
+// their gathers issued together.
+__device__ __forceinline__ float lane_dot_kahan(int e, int e1, int L, const int *idx,
+                                                const float *val, const float *vec) {
+    float s = 0.f, c = 0.f;
+    for (; e < e1; e += 4 * L) {
+        int ix[4];
+        float a[4], x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool ok = e + q * L < e1;
+            ix[q] = ok ? idx[e + q * L] : -1;
+            a[q] = ok ? val[e + q * L] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = ix[q] >= 0 ? vec[ix[q]] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (ix[q] >= 0) {
+                const float y = fmaf(a[q], x[q], -c);
+                const float t = s + y;
+                c = (t - s) - y;
+                s = t;
+            }
+        }
+    }
+    return s - c;
 }
 
 // Dot products of this CTA's lines with a gathered vector, into dots[li].
 // Warp 0 is left out: it reduces the partials of the previous barrier and
 // computes the LSQR scalars meanwhile.
-__device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, double *dots) {
+// FP32 form of cta_dots for a cached side.
+__device__ __forceinline__ void cta_dots_f32(const long long *ptr, const int *idx, const float *valf,
+                                          int nl, int Lf, const float *vec32, double *dots) {
+    const int warp = threadIdx.x >> 5;
+    const Grp G(Lf);
+    const int per = ((blockDim.x >> 5) - 1) * G.rpw;
+    for (int base = 0; base < nl; base += per) {
+        const int li = base + (warp - 1) * G.rpw + G.sub;
+        float s = 0.f;
+        if (li < nl) s = lane_dot_kahan((int)ptr[li] + G.sl, (int)ptr[li + 1], G.L, idx, valf, vec32);
+        s = group_sum(s, G.L);
+        if (li < nl && G.sl == 0) dots[li] = (double)s;
+    }
+}
+
+template <bool F32>
+__device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, const float *vec32,
+                                         double *dots) {
     const int warp = threadIdx.x >> 5;
     if (warp == 0) return;
+    if (F32 && C.cached) {
+        cta_dots_f32(C.ptr, C.idx, C.valf, C.nl, C.Lf, vec32, dots);
+        return;
+    }
     const Grp G(C.L);
     const int per = ((blockDim.x >> 5) - 1) * G.rpw;
     const auto gat = [&](int j) { return vec[j]; };
@@ -290,8 +362,10 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot) {
 // Per phase: grid barrier | warp 0 reduces the partials and updates the
 // scalars while warps 1.. compute the dot products of the CTA's lines |
 // __syncthreads | all threads combine element-wise and form the partial.
+template <bool f32>
 __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
-                                        const double *c0, double *y_g, double *xt, bool v_given,
+                                        const double *c0, const float *c0_32, double *y_g,
+                                        double *xt, bool v_given,
                                         double alpha1, double beta1, double fro2,
                                         unsigned char *dsmem, long long dsmem_bytes,
                                         SolveSmem &S) {
@@ -323,8 +397,8 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             yown[i] = 0.0;
         }
     }
-    const CtaSide R = cache_side(Rs, A, S.bs);
-    const CtaSide C = cache_side(Cs, A, S.bs);
+    const CtaSide R = cache_side<f32>(Rs, A, S.bs);
+    const CtaSide C = cache_side<f32>(Cs, A, S.bs);
     if (threadIdx.x == 0) {
         L.inv_b = 1.0 / beta1;
         L.done = 0;
@@ -333,13 +407,14 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
 
     if (!v_given) {
         // v~_1 = B^T c0 / beta1 (warp 0 has no scalars to update in this phase)
-        cta_dots(C, c0, dc);
+        cta_dots<f32>(C, c0, c0_32, dc);
         __syncthreads();
         double acc = 0.0;
         for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
             const double v = dc[li] * L.inv_b;
             vown[li] = v;
             P.vv[CC.lo + li] = v;
+            if (f32) P.vv32[CC.lo + li] = (float)v;
             acc = fma(v, v, acc);
         }
         acc = block_sum(acc, S.bs);
@@ -368,7 +443,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
     for (int it = 1;; ++it) {
         const bool first = it == 1;
         // ---- rows phase: u~_new = B v~ / alpha - (alpha/beta) u~, w update
-        cta_dots(R, P.vv, dr);
+        cta_dots<f32>(R, P.vv, P.vv32, dr);
         if (threadIdx.x < 32 && !first) {
             // scalars from ||v~||^2 of the previous cols phase
             const double vv = warp0_collect(P.pd, D_VV);
@@ -404,6 +479,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             for (int li = threadIdx.x; li < nrl; li += blockDim.x) {
                 const double u = dr[li] * inv_a - ab * uo[li];
                 P.uu[RC.lo + li] = u;
+                if (f32) P.uu32[RC.lo + li] = (float)u;
                 if (st_smem) uold[li] = u;
                 acc = fma(u, u, acc);
             }
@@ -413,7 +489,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         if (!grid_barrier(P.ctrl, S.epoch)) return -1;
 
         // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
-        cta_dots(C, P.uu, dc);
+        cta_dots<f32>(C, P.uu, P.uu32, dc);
         if (threadIdx.x < 32) {
             const double uu = warp0_collect(P.pd, D_UU);
             if (threadIdx.x == 0) {
@@ -444,6 +520,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                     const double v = dc[li] * inv_b - ba * vown[li];
                     vown[li] = v;
                     P.vv[CC.lo + li] = v;
+                    if (f32) P.vv32[CC.lo + li] = (float)v;
                     acc = fma(v, v, acc);
                 }
                 const double y = fma(phi_rho, wown[li], yown[li]);
@@ -500,6 +577,9 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
         if (!sync_collect(P, S, (dm), (dx), (im))) return;   \
     } while (0)
 
+// F32: inner LSQR products in FP32 (RGDBEK_PRECISION_FP32_INNER); a separate
+// instantiation, so the FP64 kernel's registers are unaffected.
+template <bool F32>
 __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
     __shared__ SolveSmem S;
     extern __shared__ __align__(16) unsigned char dsmem[];
@@ -609,7 +689,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             const double inv_beta1 = O.inv_beta1;
             for (long long p = gthread(); p < nU; p += nthreads()) {
                 const int j = P.ulist[p];
-                P.vv[p] = P.g[j] * inv_beta1;  // v~_1 = A_U^T z_k / beta1
+                const double v1 = P.g[j] * inv_beta1;  // v~_1 = A_U^T z_k / beta1
+                P.vv[p] = v1;
+                if (F32) P.vv32[p] = (float)v1;
                 P.yy[p] = 0.0;
                 if (rec_u) P.tr_lists[tr_off + p] = j;
             }
@@ -623,7 +705,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
                 const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr(P, rows, cols, P.z, P.yy, nullptr, true, O.alpha1, O.beta1,
+                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, true, O.alpha1, O.beta1,
                                   O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
@@ -671,6 +753,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             for (long long p = gthread(); p < nJ; p += nthreads()) {
                 const int i = P.jlist[p];
                 P.uu[p] = P.r[i];  // u~_1 = r_J
+                if (F32) P.uu32[p] = (float)P.r[i];
                 if (rec_j) P.tr_lists[tr_off + nU + p] = i;
             }
             // A^J: the entries of every column of A that lie in J's rows
@@ -683,7 +766,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
                 const SideC rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
                 const SideC cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
                                  pick_lanes_fp64(nnzJ, P.n)};
-                stepsJ = run_lsqr(P, rows, cols, P.uu, P.dx, P.xt, false, 0.0, O.beta1, O.fro2,
+                stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, false, 0.0, O.beta1, O.fro2,
                                   dsmem, P.dsmem_bytes, S);
                 if (stepsJ < 0) return;
                 mark(S, PH_ROW_LSQR);
@@ -863,8 +946,9 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
 cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s) {
     Params p = P;
     void *args[] = {&p};
-    return cudaLaunchCooperativeKernel((const void *)solve_kernel, dim3(grid), dim3(block), args,
-                                       (size_t)P.dsmem_bytes, s);
+    const void *fn = P.fp32_inner ? (const void *)solve_kernel<true>
+                                  : (const void *)solve_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, (size_t)P.dsmem_bytes, s);
 }
 
 cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
@@ -904,14 +988,18 @@ cudaError_t launch_weights(const double *v, const double *norm2, long long len, 
 }
 
 int solve_blocks_per_sm(int block) {
-    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSolveDsmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSolveDsmemBytes) != cudaSuccess)
         return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel, block, kSolveDsmemBytes) !=
-        cudaSuccess)
+    int nb = 0, nb32 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, block,
+                                                      kSolveDsmemBytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb32, solve_kernel<true>, block,
+                                                      kSolveDsmemBytes) != cudaSuccess)
         return 0;
-    return nb;
+    return nb < nb32 ? nb : nb32;
 }
 
 int sample_blocks_per_sm(int block) {

@@ -66,6 +66,8 @@ struct Params {
     long long max_iter, s_col, s_row;
     unsigned long long seed, sysid;
     int inner_max, stop_rule, selection;
+    int fp32_inner;         // inner LSQR products in FP32 (Kahan dots)
+    float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
     int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel

@@ -168,3 +168,45 @@ def test_backward_full_size_deblur_properties(rg):
     e = rng.choice(S.nnz, size=20000, replace=False)
     expect = r[rows[e]] * v[S.col_idx[e]] - gb[rows[e]] * x[S.col_idx[e]]
     assert _rel(gv[e], expect) <= 1e-6
+
+
+def test_autograd_function_gradients_wrt_b_lambda_and_values(rg):
+    """rgdbek_lstsq under torch.autograd on [A; lam I] x = [b; 0] (16 x 16
+    deblur): dL/dlam (through lam's entries of the stacked values) against
+    central differences of dense lstsq solutions with h = 1e-6, dL/db and
+    dL/dA against the dense pseudo-inverse gradient."""
+    import torch
+    side, lam0 = 16, 0.05
+    S = workloads.deblur_regularised(side, lam=lam0)
+    nb = S.m - S.n                                  # blur rows
+    nnz_a = int(S.row_ptr[nb])
+    dev = "cuda"
+    rp = torch.tensor(S.row_ptr, device=dev)
+    ci = torch.tensor(S.col_idx, device=dev)
+    va = torch.tensor(S.vals[:nnz_a], device=dev, requires_grad=True)
+    lam = torch.tensor(lam0, dtype=torch.float64, device=dev, requires_grad=True)
+    bb = torch.tensor(S.b[:nb], device=dev, requires_grad=True)
+    xt = torch.tensor(S.x_true, device=dev)
+    vals = torch.cat([va, lam * torch.ones(S.n, dtype=torch.float64, device=dev)])
+    b = torch.cat([bb, torch.zeros(S.n, dtype=torch.float64, device=dev)])
+    x = rg.rgdbek_lstsq(rp, ci, vals, b, S.m, S.n, tol=1e-12, eta_col=ETA, eta_row=ETA,
+                        stop_rule=rg.STOP_NORMAL)
+    loss = ((x - xt) ** 2).sum()
+    loss.backward()
+
+    D = S.dense()
+
+    def L(lmb):
+        Dl = D.copy()
+        Dl[nb:, :] = lmb * np.eye(S.n)
+        xs = np.linalg.lstsq(Dl, S.b, rcond=None)[0]
+        return float(((xs - S.x_true) ** 2).sum())
+
+    h = 1e-6
+    fd = (L(lam0 + h) - L(lam0 - h)) / (2 * h)
+    assert abs(float(lam.grad) - fd) <= 1e-6 * abs(fd)
+    xs = np.linalg.lstsq(D, S.b, rcond=None)[0]
+    gb_d, Gd = oracle.backward_dense(D, S.b, 2 * (xs - S.x_true), rank_term=False)
+    rows = np.repeat(np.arange(S.m), np.diff(S.row_ptr))
+    assert _rel(G.host(bb.grad), gb_d[:nb]) <= 1e-8
+    assert _rel(G.host(va.grad), Gd[rows[:nnz_a], S.col_idx[:nnz_a]]) <= 1e-8

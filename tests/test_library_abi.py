@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import gpu_util
 
 HEADER = os.path.join(gpu_util.ROOT, "include", "rgdbek.h")
@@ -47,6 +49,15 @@ def test_host_only_calls():
     assert rg._lib.rgdbek_solve(None, None, None, 1e-8, 10, 0, None) == rg.ERR_INVALID_ARG
     assert rg._lib.rgdbek_backward(None, None, None, None, None, None, 1e-8, 10, 0, 0,
                                    None) == rg.ERR_INVALID_ARG
+    # an unknown precision is rejected by the option check, before the device
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    av = np.array([1.0])
+    bad = rg.default_options(precision=2)
+    assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 1, rp.ctypes.data, ci.ctypes.data,
+                                 av.ctypes.data, 0, ctypes.byref(bad), None) \
+        == rg.ERR_INVALID_ARG
+    assert rg.default_options().precision == rg.PRECISION_FP64
 
 
 def test_size_limits_rejected_before_any_device_call():

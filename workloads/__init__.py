@@ -196,3 +196,68 @@ def deblur_regularised(side: int = 256, lam: float = 0.05, seed: int = 4) -> Sys
     b = np.concatenate([B.b, np.zeros(N)])
     return System(f"deblur_{side}x{side}_lam{lam}", 2 * N, N, row_ptr, col_idx, vals, b,
                   B.x_true, False)
+
+
+def poisson_p1_matrix(nx: int, keep_zeros: bool = False):
+    """Stiffness matrix of -Laplace(u) = f on [0,1]^2 with u = 0 on the boundary:
+    linear (P1) elements on the nx x nx uniform grid, each cell split into two
+    right triangles by its (lower-left, upper-right) diagonal.  Element
+    matrices are assembled from the gradients of the barycentric basis;
+    Dirichlet rows become identity rows and their columns are eliminated from
+    the other rows.  Entries that assemble to exactly zero (the couplings
+    across the cell diagonals) are dropped unless keep_zeros.
+
+    Returns (row_ptr, col_idx, vals, coords) with coords (N, 2), N = nx^2,
+    node (i, j) -> index j * nx + i at (i h, j h), h = 1 / (nx - 1)."""
+    h = 1.0 / (nx - 1)
+    ii, jj = np.meshgrid(np.arange(nx - 1), np.arange(nx - 1), indexing="xy")
+    ii, jj = ii.reshape(-1), jj.reshape(-1)
+    n00 = jj * nx + ii
+    n10 = n00 + 1
+    n01 = n00 + nx
+    n11 = n01 + 1
+    tris = np.concatenate([np.stack([n00, n10, n11], 1), np.stack([n00, n11, n01], 1)])
+    coords = np.stack([np.tile(np.arange(nx) * h, nx), np.repeat(np.arange(nx) * h, nx)], 1)
+    P = coords[tris]                                      # (T, 3, 2)
+    # gradients of the barycentric functions: grad phi_a = rot(P_b - P_c) / (2 area)
+    e = np.stack([P[:, 2] - P[:, 1], P[:, 0] - P[:, 2], P[:, 1] - P[:, 0]], 1)  # opposite edges
+    area2 = e[:, 1, 0] * e[:, 2, 1] - e[:, 1, 1] * e[:, 2, 0]
+    # K_ab = (e_a . e_b) / (2 area2)  (area2 = twice the area)
+    K = np.einsum("tad,tbd->tab", e, e) / (2.0 * area2[:, None, None])
+    rows = np.repeat(tris, 3, axis=1).reshape(-1)
+    cols = np.tile(tris, (1, 3)).reshape(-1)
+    N = nx * nx
+    key = rows.astype(np.int64) * N + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    val = np.zeros(len(uk))
+    np.add.at(val, inv, K.reshape(-1))
+    r, c = uk // N, uk % N
+    bnd = np.zeros(N, bool)
+    on = (coords[:, 0] == 0) | (coords[:, 1] == 0) | (np.arange(N) % nx == nx - 1) | \
+         (np.arange(N) // nx == nx - 1)
+    bnd[on] = True
+    keep = ~bnd[r] & ~bnd[c]
+    if not keep_zeros:
+        keep &= val != 0.0
+    r, c, val = r[keep], c[keep], val[keep]
+    b_idx = np.nonzero(bnd)[0]
+    r = np.concatenate([r, b_idx])
+    c = np.concatenate([c, b_idx])
+    val = np.concatenate([val, np.ones(len(b_idx))])
+    order = np.lexsort((c, r))
+    r, c, val = r[order], c[order], val[order]
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=N), out=row_ptr[1:])
+    return row_ptr, c.astype(np.int32), val, coords
+
+
+def poisson_p1(nx: int = 1024, sigma: float = 1e-3, seed: int = 2,
+               keep_zeros: bool = False) -> System:
+    """K x* = b with x* = sin(pi x) sin(pi y) at the nodes plus N(0, sigma^2)
+    noise (consistent, square)."""
+    rng = np.random.default_rng(seed)
+    rp, ci, av, xy = poisson_p1_matrix(nx, keep_zeros)
+    x = np.sin(np.pi * xy[:, 0]) * np.sin(np.pi * xy[:, 1]) + sigma * rng.standard_normal(nx * nx)
+    b = _csr_matvec(rp, ci, av, x)
+    N = nx * nx
+    return System(f"poisson_p1_{nx}x{nx}", N, N, rp, ci, av, b, x, True)
