@@ -78,6 +78,9 @@ typedef struct {
     int blocks_per_sm;     /* persistent grid: CTAs per SM, 0 = largest that fits   */
     int threads_per_block; /* 0 = 1024; a multiple of 32 in [64, 1024]              */
     int precision;         /* RGDBEK_PRECISION_*                                    */
+    int batch_team;        /* CTAs per system in rgdbek_solve_batched (read from the
+                              first handle): 0 = the size rgdbek_tune_batched found,
+                              else about one system per team                        */
 } rgdbek_options;
 
 typedef struct {
@@ -174,13 +177,37 @@ int rgdbek_solve(rgdbek_t h, const double *b, double *x, double tol, int64_t max
 int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double tol,
                       int64_t max_iter, uint64_t seed, rgdbek_stats *st);
 
-/* Solves nsys independent systems, system i on handle hs[i] with device
- * buffers b[i] and x[i], tolerance tol[i] and system_id i (seed shared).
- * st: host array of nsys records, may be NULL.  Returns the worst status
- * (the most negative error, else NOT_CONVERGED if any system hit the cap). */
+/* Solves nsys independent systems in ONE persistent cooperative launch:
+ * system i on handle hs[i] (its matrix, options and workspace; the handles
+ * must be distinct, on one device, with the same block size and precision)
+ * with device buffers b[i], x[i], tolerance tol[i] and system_id i (seed
+ * shared).  The grid is cut into teams of `team` CTAs (options.batch_team of
+ * hs[0], or the tuned size, see rgdbek_tune_batched); each team solves its
+ * share of the systems one after another with barriers among its own CTAs,
+ * each system to its own stopping rule or cap (a per-system convergence
+ * mask: a finished system frees its team for the next one).  Systems are
+ * assigned largest first to the least loaded team (work ~ nnz + m + n).
+ * The launch runs on hs[0]'s stream after the other handles' streams are
+ * synchronised.  st: host array of nsys records, may be NULL.  Returns the
+ * worst status (the most negative error, else NOT_CONVERGED if any system
+ * hit the cap).  Device scratch of about 600 B per system is allocated and
+ * freed inside the call. */
 int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                          const double *tol, int64_t max_iter, uint64_t seed,
                          rgdbek_stats *st);
+
+/* Autotuner of the batched solve: runs the batch for probe_iters outer
+ * iterations with each candidate team size (1, 2, 4, 8, 19, 38, 76, 152 CTAs
+ * per system, those not above the grid), times each launch with CUDA
+ * events, and keeps the fastest in hs[0] for later rgdbek_solve_batched
+ * calls with batch_team = 0.  *team_out receives it; ms_out (host
+ * double[RGDBEK_BATCH_TEAM_CANDIDATES], may be NULL) the time of each
+ * candidate (-1 where skipped).  The x buffers are overwritten by the probe
+ * solves.  Returns OK or the first error. */
+#define RGDBEK_BATCH_TEAM_CANDIDATES 8
+int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
+                        const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
+                        double *ms_out);
 
 /* Implicit adjoint of the solve (reverse-mode gradient).  The method
  * converges to x = A^+ b, the minimum-norm least-squares solution (the

@@ -49,6 +49,7 @@ class rgdbek_options(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", _int), ("inner_tol", _dbl),
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
         ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
+        ("batch_team", _int),
     ]
 
 
@@ -88,6 +89,8 @@ SIGNATURES = [
                                  ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_solve_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
                                     ctypes.POINTER(rgdbek_stats)]),
+    ("rgdbek_tune_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
+                                    ctypes.POINTER(_int), ctypes.POINTER(_dbl)]),
     ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
                                ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
@@ -229,6 +232,7 @@ def rgdbek_solve_host(h: int, b, x, tol: float, max_iter: int, seed: int = 0,
 
 
 def rgdbek_solve_batched(hs, bs, xs, tols, max_iter: int, seed: int = 0):
+    """All systems in one persistent launch; returns (status, [stats])."""
     n = len(hs)
     H = (_ptr * n)(*hs)
     B = (_ptr * n)(*[_dptr(b) for b in bs])
@@ -237,6 +241,23 @@ def rgdbek_solve_batched(hs, bs, xs, tols, max_iter: int, seed: int = 0):
     S = (rgdbek_stats * n)()
     status = _lib.rgdbek_solve_batched(n, H, B, X, T, max_iter, seed, S)
     return status, list(S)
+
+
+BATCH_TEAM_CANDIDATES = (1, 2, 4, 8, 19, 38, 76, 152)
+
+
+def rgdbek_tune_batched(hs, bs, xs, tols, probe_iters: int = 3, seed: int = 0):
+    """Times the batch with each team size; returns (best_team, {team: ms})."""
+    n = len(hs)
+    H = (_ptr * n)(*hs)
+    B = (_ptr * n)(*[_dptr(b) for b in bs])
+    X = (_ptr * n)(*[_dptr(x) for x in xs])
+    T = (_dbl * n)(*tols)
+    team = _int(0)
+    ms = (_dbl * len(BATCH_TEAM_CANDIDATES))()
+    _check(_lib.rgdbek_tune_batched(n, H, B, X, T, probe_iters, seed, ctypes.byref(team), ms),
+           "rgdbek_tune_batched")
+    return team.value, {c: ms[i] for i, c in enumerate(BATCH_TEAM_CANDIDATES) if ms[i] >= 0}
 
 
 ADJ_RANK_TERM = 1

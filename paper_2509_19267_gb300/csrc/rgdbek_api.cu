@@ -1,10 +1,12 @@
 // Host side of the C ABI declared in include/rgdbek.h: handle life cycle,
 // option checks, device memory layout, and the launches of the persistent
 // solve kernel and of the component kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "rgdbek_internal.h"
 
@@ -43,6 +45,7 @@ struct rgdbek_s {
     double *adj_ax, *adj_w, *adj_v, *adj_u, *adj_ag, *adj_q;
     // launch shape
     int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
+    int tuned_team = 0;  // team size found by rgdbek_tune_batched (0 = none yet)
     // trace
     long long *tr_counts = nullptr;
     long long tr_count_cap = 0;
@@ -123,6 +126,7 @@ int check_options(const rgdbek_options &o) {
     if (o.blocks_per_sm < 0 || o.threads_per_block < 0) return RGDBEK_ERR_INVALID_ARG;
     if (o.precision != RGDBEK_PRECISION_FP64 && o.precision != RGDBEK_PRECISION_FP32_INNER)
         return RGDBEK_ERR_INVALID_ARG;
+    if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -215,6 +219,7 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.ipr = h->ipr;
     P.ipc = h->ipc;
     P.dsmem_bytes = kSolveDsmemBytes;
+    P.team = h->grid;
     if (transposed) {
         P.m = h->n;
         P.n = h->m;
@@ -260,6 +265,8 @@ int read_ctrl(rgdbek_s *h) {
     return cuda_status(e);
 }
 
+void fill_stats(const Ctrl &c, int status, rgdbek_stats *st);
+
 // One persistent-kernel solve of A x = b (or of A^T x = b when transposed),
 // x0 = 0; reads the control block back into *st.
 int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double tol,
@@ -278,7 +285,12 @@ int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double t
     int rs = read_ctrl(h);
     if (rs != RGDBEK_OK) return rs;
     const Ctrl &c = *h->ctrl_host;
-    int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
+    const int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
+    fill_stats(c, status, st);
+    return status;
+}
+
+void fill_stats(const Ctrl &c, int status, rgdbek_stats *st) {
     if (st) {
         st->iters = c.iters;
         st->inner_u = c.inner_u;
@@ -297,7 +309,134 @@ int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double t
         st->status = status;
         for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
     }
-    return status;
+}
+
+// Team sizes the batched solve and its tuner consider (CTAs per system).
+constexpr int kNumTeamCandidates = RGDBEK_BATCH_TEAM_CANDIDATES;
+constexpr int kTeamCandidates[kNumTeamCandidates] = {1, 2, 4, 8, 19, 38, 76, 152};
+
+// Without a tuned or requested size: about one system per team, i.e. the
+// candidate nearest grid / nsys (at least 1).
+int default_team(const rgdbek_s *h, int nsys) {
+    if (!h) return 1;
+    const double want = (double)h->grid / (double)nsys;
+    int best = 1;
+    for (int c = 0; c < kNumTeamCandidates; ++c)
+        if (kTeamCandidates[c] <= h->grid && kTeamCandidates[c] <= want) best = kTeamCandidates[c];
+    return best;
+}
+
+// Largest-first list scheduling (LPT) of the systems onto nteams teams, by a
+// work estimate of nnz + m + n per outer iteration.  plan[t * stride + q] is
+// the q-th system of team t, -1 after the last.
+void plan_batch(int nsys, rgdbek_t *hs, int nteams, std::vector<int> &plan, int &stride) {
+    std::vector<int> order(nsys);
+    for (int i = 0; i < nsys; ++i) order[i] = i;
+    auto cost = [&](int i) { return (double)(hs[i]->nnz + hs[i]->m + hs[i]->n); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+    std::vector<double> load(nteams, 0.0);
+    std::vector<std::vector<int>> lists(nteams);
+    for (int i : order) {
+        int t = 0;
+        for (int u = 1; u < nteams; ++u)
+            if (load[u] < load[t]) t = u;
+        load[t] += cost(i);
+        lists[t].push_back(i);
+    }
+    stride = 1;
+    for (const auto &l : lists) stride = std::max(stride, (int)l.size() + 1);
+    plan.assign((size_t)nteams * stride, -1);
+    for (int t = 0; t < nteams; ++t)
+        for (size_t q = 0; q < lists[t].size(); ++q) plan[(size_t)t * stride + q] = lists[t][q];
+}
+
+// One cooperative launch solving all systems with `team` CTAs each.
+// Optionally times the launch (ms).  Statuses: the most negative error, else
+// NOT_CONVERGED if any system hit its cap.
+int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
+                const double *tol, long long max_iter, uint64_t seed, rgdbek_stats *st, int team,
+                float *ms) {
+    rgdbek_s *h0 = hs[0];
+    if (!h0 || team < 1 || team > h0->grid) return RGDBEK_ERR_INVALID_ARG;
+    for (int i = 0; i < nsys; ++i) {
+        if (!hs[i] || !b[i] || !x[i] || !(tol[i] >= 0.0) || max_iter < 0) return RGDBEK_ERR_INVALID_ARG;
+        if (hs[i]->device != h0->device || hs[i]->block != h0->block ||
+            hs[i]->opt.precision != h0->opt.precision)
+            return RGDBEK_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return RGDBEK_ERR_INVALID_ARG;  // one workspace per system
+    }
+    const int nteams = h0->grid / team;
+    std::vector<Params> sys(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        Params P = make_params(hs[i]);
+        P.b = b[i];
+        P.x = x[i];
+        P.tol = tol[i];
+        P.max_iter = max_iter;
+        P.seed = seed;
+        P.sysid = (unsigned long long)i;
+        P.s_col = num_draws(hs[i]->opt.eta_col, P.n);
+        P.s_row = num_draws(hs[i]->opt.eta_row, P.m);
+        P.team = team;
+        P.tr_counts = nullptr;
+        P.tr_count_cap = 0;
+        P.tr_lists = nullptr;
+        P.tr_list_cap = 0;
+        sys[i] = P;
+    }
+    std::vector<int> plan;
+    int stride = 1;
+    plan_batch(nsys, hs, nteams, plan, stride);
+    const size_t sys_bytes = (sizeof(Params) * nsys + 255) & ~(size_t)255;
+    const size_t plan_bytes = (sizeof(int) * plan.size() + 255) & ~(size_t)255;
+    const size_t ctrl_bytes = sizeof(Ctrl) * nsys;
+    char *dev = nullptr;
+    Ctrl *host = nullptr;
+    cudaStream_t s = h0->stream;
+    cudaError_t e = cudaMalloc(&dev, sys_bytes + plan_bytes + ctrl_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&host, ctrl_bytes);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (e == cudaSuccess && ms) {
+        e = cudaEventCreate(&ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    }
+    Params *sys_dev = reinterpret_cast<Params *>(dev);
+    int *plan_dev = reinterpret_cast<int *>(dev + sys_bytes);
+    Ctrl *ctrl_dev = reinterpret_cast<Ctrl *>(dev + sys_bytes + plan_bytes);
+    // the handles' own streams must have finished their earlier work
+    for (int i = 0; e == cudaSuccess && i < nsys; ++i)
+        if (hs[i]->stream != s) e = cudaStreamSynchronize(hs[i]->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sys_dev, sys.data(), sizeof(Params) * nsys, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(plan_dev, plan.data(), sizeof(int) * plan.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_reset_ctrls(sys_dev, nsys, s);
+    if (e == cudaSuccess && ms) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess)
+        e = launch_solve_batched(sys_dev, plan_dev, stride, team, nteams,
+                                 h0->opt.precision == RGDBEK_PRECISION_FP32_INNER, h0->block, s);
+    if (e == cudaSuccess && ms) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess) e = launch_gather_ctrls(sys_dev, nsys, ctrl_dev, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, ctrl_dev, ctrl_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && ms) e = cudaEventElapsedTime(ms, ev0, ev1);
+    int worst = RGDBEK_OK;
+    if (e == cudaSuccess) {
+        for (int i = 0; i < nsys; ++i) {
+            const Ctrl &c = host[i];
+            const int status = c.status == kStatusRunning ? RGDBEK_ERR_CUDA : c.status;
+            fill_stats(c, status, st ? st + i : nullptr);
+            if (status < 0 && (worst >= 0 || status < worst)) worst = status;
+            else if (status == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = status;
+        }
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (host) cudaFreeHost(host);
+    if (dev) cudaFree(dev);
+    return e == cudaSuccess ? worst : cuda_status(e);
 }
 
 void release(rgdbek_s *h) {
@@ -325,6 +464,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->blocks_per_sm = 0;
     opt->threads_per_block = 0;
     opt->precision = RGDBEK_PRECISION_FP64;
+    opt->batch_team = 0;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
@@ -511,17 +651,38 @@ int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double t
 int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                          const double *tol, int64_t max_iter, uint64_t seed, rgdbek_stats *st) {
     if (nsys < 0 || (nsys > 0 && (!hs || !b || !x || !tol))) return RGDBEK_ERR_INVALID_ARG;
-    int worst = RGDBEK_OK;
-    for (int i = 0; i < nsys; ++i) {
-        if (!hs[i]) return RGDBEK_ERR_INVALID_ARG;
-        const uint64_t saved = hs[i]->opt.system_id;
-        hs[i]->opt.system_id = (uint64_t)i;
-        const int s = rgdbek_solve(hs[i], b[i], x[i], tol[i], max_iter, seed, st ? st + i : nullptr);
-        hs[i]->opt.system_id = saved;
-        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
-        else if (s == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = s;
+    if (nsys == 0) return RGDBEK_OK;
+    int team = hs[0] ? hs[0]->opt.batch_team : 0;
+    if (team == 0 && hs[0]) team = hs[0]->tuned_team;
+    if (team == 0) team = default_team(hs[0], nsys);
+    return run_batched(nsys, hs, b, x, tol, max_iter, seed, st, team, nullptr);
+}
+
+int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
+                        const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
+                        double *ms_out) {
+    if (nsys < 1 || !hs || !b || !x || !tol || probe_iters < 1 || !team_out || !hs[0])
+        return RGDBEK_ERR_INVALID_ARG;
+    const int grid = hs[0]->grid;
+    int best = 0;
+    float best_ms = 0.f;
+    for (int c = 0; c < kNumTeamCandidates; ++c) {
+        const int T = kTeamCandidates[c];
+        if (ms_out) ms_out[c] = -1.0;
+        if (T > grid) continue;
+        float ms = 0.f;
+        const int s0 = run_batched(nsys, hs, b, x, tol, probe_iters, seed, nullptr, T, &ms);
+        if (s0 < 0) return s0;
+        if (ms_out) ms_out[c] = ms;
+        if (best == 0 || ms < best_ms) {
+            best = T;
+            best_ms = ms;
+        }
     }
-    return worst;
+    if (best == 0) return RGDBEK_ERR_INVALID_ARG;
+    hs[0]->tuned_team = best;
+    *team_out = best;
+    return RGDBEK_OK;
 }
 
 int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *grad_x,

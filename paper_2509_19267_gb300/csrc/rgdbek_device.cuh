@@ -93,21 +93,22 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Grid-wide barrier for cooperative launches (all CTAs resident).  `epoch`
-// (read and advanced by thread 0 only) counts the barriers this CTA has
-// passed, the same number in every CTA: barrier
-// number e completes when the arrival counter reaches gridDim.x * (e + 1).
+// Barrier of the nct CTAs of a team in a cooperative launch (all CTAs
+// resident; the team is the whole grid for a single solve), on the team's own
+// counter.  `epoch` (read and advanced by thread 0 only) counts the barriers
+// this CTA has passed, the same number in every CTA of the team: barrier
+// number e completes when the arrival counter reaches nct * (e + 1).
 // Arrival is a release add by thread 0 after the CTA's __syncthreads (so the
 // CTA's writes are published); the wait is an acquire load followed by a
 // __syncthreads (so every thread sees the other CTAs' writes).  Returns false
 // if the wait was abandoned: another CTA raised the abort flag, or the
 // time/spin limit ran out (then this CTA records TIMEOUT and raises abort).
-__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch) {
+__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch, int nct) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned long long target = (unsigned long long)gridDim.x * (epoch + 1);
+        const unsigned long long target = (unsigned long long)nct * (epoch + 1);
         atom_add_release_u64(&c->bar_count, 1ull);
         unsigned long long spins = 0;
         const unsigned long long t0 = globaltimer_ns();

@@ -17,6 +17,14 @@ constexpr int kSolveDsmemBytes = 96 * 1024;
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
 // persistent solve (cooperative launch); returns the launch error
 cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s);
+// batched solve: nteams * team CTAs (cooperative launch); sys_dev holds one
+// Params per system (team already set), plan_dev[t * stride + q] the q-th
+// system of team t (-1 ends a team's list)
+cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int stride, int team,
+                                 int nteams, bool fp32, int block, cudaStream_t s);
+// control blocks of a batch: reset before the launch, gathered after it
+cudaError_t launch_reset_ctrls(const Params *sys_dev, int nsys, cudaStream_t s);
+cudaError_t launch_gather_ctrls(const Params *sys_dev, int nsys, Ctrl *out, cudaStream_t s);
 // standalone sampler on given weights (cooperative launch)
 cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
                           long long s, unsigned long long seed, unsigned long long sysid,

@@ -55,6 +55,7 @@ struct SolveSmem {
     LsqrState lsqr;                                  // LSQR scalars (written by thread 0)
     OuterState o;                                    // outer-loop scalars (thread 0)
     unsigned long long epoch;                        // grid barriers passed (thread 0 copy)
+    int leader;                                      // this CTA has rank 0 in its team
     unsigned long long tlast;                        // phase timers (CTA 0, thread 0)
     unsigned long long tphase[RGDBEK_NUM_PHASES];
 };
@@ -62,9 +63,9 @@ struct SolveSmem {
 enum PhaseId { PH_SETUP = 0, PH_COL, PH_COL_SEL, PH_COL_EXT, PH_COL_LSQR, PH_ZUPD, PH_ROW_SEL,
                PH_ROW_EXT, PH_ROW_LSQR, PH_RESID };
 
-// charges the time since the previous mark to phase `id` (CTA 0 only)
+// charges the time since the previous mark to phase `id` (team rank 0 only)
 __device__ __forceinline__ void mark(SolveSmem &S, int id) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (S.leader && threadIdx.x == 0) {
         const unsigned long long now = globaltimer_ns();
         S.tphase[id] += now - S.tlast;
         S.tlast = now;
@@ -77,15 +78,15 @@ __device__ __forceinline__ void mark(SolveSmem &S, int id) {
 // Returns false if the barrier was abandoned.
 __device__ __forceinline__ bool sync_collect(const Params &P, SolveSmem &S, unsigned dmask,
                                              unsigned dmax, unsigned imask) {
-    if (!grid_barrier(P.ctrl, S.epoch)) return false;
+    if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return false;
     if (dmask | imask)
-        collect_partials(P.pd, P.pi, gridDim.x, dmask, dmax, imask, S.red_d, S.red_i);
+        collect_partials(P.pd, P.pi, tsize(P), dmask, dmax, imask, S.red_d, S.red_i);
     return true;
 }
 
 __device__ __forceinline__ void finish(const Params &P, int status, long long k, double rel,
                                        double nrm, const SolveSmem &S) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (trank(P) == 0 && threadIdx.x == 0) {
         const Acc &a = S.acc;
         Ctrl *C = P.ctrl;
         for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) C->phase_ns[i] = S.tphase[i];
@@ -181,8 +182,9 @@ struct SmemArena {
 // lines), if it fits; with fp32 the values are stored as float.  All threads
 // of the CTA call it.
 template <bool fp32>
-__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, BlockScratch &bs) {
-    const Chunk C(S.n, blockIdx.x, gridDim.x);
+__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, BlockScratch &bs,
+                                              int rank, int nct) {
+    const Chunk C(S.n, rank, nct);
     CtaSide out;
     out.nl = (int)(C.hi - C.lo);
     out.lo = C.lo;
@@ -342,8 +344,7 @@ __device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, co
 }
 
 // Warp 0: sum of the per-CTA partials of one slot (fixed order), for lane 0.
-__device__ __forceinline__ double warp0_collect(const double *pd, int slot) {
-    const int nb = gridDim.x;
+__device__ __forceinline__ double warp0_collect(const double *pd, int slot, int nb) {
     const double *p = pd + slot * nb;
     double s = 0.0;
 #pragma unroll 8
@@ -371,7 +372,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                                         SolveSmem &S) {
     LsqrState &L = S.lsqr;
     SmemArena A{dsmem, dsmem_bytes, 0};
-    const Chunk RC(Rs.n, blockIdx.x, gridDim.x), CC(Cs.n, blockIdx.x, gridDim.x);
+    const Chunk RC(Rs.n, trank(P), tsize(P)), CC(Cs.n, trank(P), tsize(P));
     const int nrl = (int)(RC.hi - RC.lo), ncl = (int)(CC.hi - CC.lo);
     // per-CTA vector slices and dot buffers
     double *uold = A.take<double>(nrl);
@@ -397,8 +398,8 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             yown[i] = 0.0;
         }
     }
-    const CtaSide R = cache_side<f32>(Rs, A, S.bs);
-    const CtaSide C = cache_side<f32>(Cs, A, S.bs);
+    const CtaSide R = cache_side<f32>(Rs, A, S.bs, trank(P), tsize(P));
+    const CtaSide C = cache_side<f32>(Cs, A, S.bs, trank(P), tsize(P));
     if (threadIdx.x == 0) {
         L.inv_b = 1.0 / beta1;
         L.done = 0;
@@ -418,10 +419,10 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             acc = fma(v, v, acc);
         }
         acc = block_sum(acc, S.bs);
-        if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
-        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
+        if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
+        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
         if (threadIdx.x < 32) {
-            const double vv = warp0_collect(P.pd, D_VV);
+            const double vv = warp0_collect(P.pd, D_VV, tsize(P));
             if (threadIdx.x == 0) L.alpha = sqrt(vv);
         }
         __syncthreads();
@@ -446,7 +447,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         cta_dots<f32>(R, P.vv, P.vv32, dr);
         if (threadIdx.x < 32 && !first) {
             // scalars from ||v~||^2 of the previous cols phase
-            const double vv = warp0_collect(P.pd, D_VV);
+            const double vv = warp0_collect(P.pd, D_VV, tsize(P));
             if (threadIdx.x == 0) {
                 // alpha_{i+1} = ||v~||; the divisions of the recurrence are
                 // multiplications by reciprocals formed with rsqrt, which keeps
@@ -484,14 +485,14 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 acc = fma(u, u, acc);
             }
             acc = block_sum(acc, S.bs);
-            if (threadIdx.x == 0) P.pd[D_UU * gridDim.x + blockIdx.x] = acc;
+            if (threadIdx.x == 0) P.pd[D_UU * tsize(P) + trank(P)] = acc;
         }
-        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
+        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
 
         // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
         cta_dots<f32>(C, P.uu, P.uu32, dc);
         if (threadIdx.x < 32) {
-            const double uu = warp0_collect(P.pd, D_UU);
+            const double uu = warp0_collect(P.pd, D_UU, tsize(P));
             if (threadIdx.x == 0) {
                 // beta_{i+1} = ||u~||, rho = sqrt(rhobar^2 + beta^2); 1/rho from
                 // rsqrt of rho^2 directly, in parallel with sqrt(||u~||^2)
@@ -529,9 +530,9 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 if (xt) xt[CC.lo + li] = P.x[CC.lo + li] + y;
             }
             acc = block_sum(acc, S.bs);
-            if (threadIdx.x == 0) P.pd[D_VV * gridDim.x + blockIdx.x] = acc;
+            if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
         }
-        if (!grid_barrier(P.ctrl, S.epoch)) return -1;
+        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
     }
 }
 
@@ -542,7 +543,7 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
     const Grp G(hasU ? Lsub : 1);
     double emax = 0.0, zz = 0.0;
     long long bad = 0;
-    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
         if (hasU && i < P.m)
@@ -566,9 +567,9 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
     zz = block_sum(zz, bs);
     bad = block_sum(bad, bs);
     if (threadIdx.x == 0) {
-        P.pd[D_EMAX_R * gridDim.x + blockIdx.x] = emax;
-        P.pd[D_ZZ * gridDim.x + blockIdx.x] = zz;
-        P.pi[I_BAD_R * gridDim.x + blockIdx.x] = bad;
+        P.pd[D_EMAX_R * tsize(P) + trank(P)] = emax;
+        P.pd[D_ZZ * tsize(P) + trank(P)] = zz;
+        P.pi[I_BAD_R * tsize(P) + trank(P)] = bad;
     }
 }
 
@@ -577,19 +578,19 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
         if (!sync_collect(P, S, (dm), (dx), (im))) return;   \
     } while (0)
 
+// One whole solve of Algorithm 1 by the CTAs of a team (after enter_team).
 // F32: inner LSQR products in FP32 (RGDBEK_PRECISION_FP32_INNER); a separate
-// instantiation, so the FP64 kernel's registers are unaffected.
+// instantiation, so the FP64 code's registers are unaffected.
 template <bool F32>
-__global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
-    __shared__ SolveSmem S;
-    extern __shared__ __align__(16) unsigned char dsmem[];
+__device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsigned char *dsmem) {
     BlockScratch &bs = S.bs;
     OuterState &O = S.o;
-    const int nct = gridDim.x;
+    const int nct = tsize(P);
     const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
     const unsigned long long t_start = globaltimer_ns();
     if (threadIdx.x == 0) {
         S.epoch = 0;
+        S.leader = trank(P) == 0;
         S.acc = Acc{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         S.tlast = t_start;
         for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) S.tphase[i] = 0;
@@ -599,22 +600,22 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
     {
         double bb = 0.0;
         long long bad = 0;
-        for (long long i = gthread(); i < P.m; i += nthreads()) {
+        for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
             const double bi = __ldg(P.b + i);
             P.z[i] = bi;
             P.t[i] = bi;
             bb = fma(bi, bi, bb);
             if (!isfinite(bi)) bad = 1;
         }
-        for (long long j = gthread(); j < P.n; j += nthreads()) {
+        for (long long j = tthread(P); j < P.n; j += tthreads(P)) {
             P.x[j] = 0.0;
             P.xt[j] = 0.0;
         }
         bb = block_sum(bb, bs);
         bad = block_sum(bad, bs);
         if (threadIdx.x == 0) {
-            P.pd[D_BB * nct + blockIdx.x] = bb;
-            P.pi[I_BAD_R * nct + blockIdx.x] = bad;
+            P.pd[D_BB * nct + trank(P)] = bb;
+            P.pi[I_BAD_R * nct + trank(P)] = bad;
         }
     }
     RGD_SYNC(DS(D_BB), 0, DS(I_BAD_R));
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
 
     for (long long k = 0;; ++k) {
         // ---- column pass and stopping test on x_k
-        if (blockIdx.x == 0 && threadIdx.x == 0 && P.time_budget_ns > 0.0 &&
+        if (trank(P) == 0 && threadIdx.x == 0 && P.time_budget_ns > 0.0 &&
             (double)(globaltimer_ns() - t_start) > P.time_budget_ns)
             P.ctrl->stop_req = 1;
         phase_col(P, bs);
@@ -687,7 +688,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             mark(S, PH_COL_SEL);
             rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
             const double inv_beta1 = O.inv_beta1;
-            for (long long p = gthread(); p < nU; p += nthreads()) {
+            for (long long p = tthread(P); p < nU; p += tthreads(P)) {
                 const int j = P.ulist[p];
                 const double v1 = P.g[j] * inv_beta1;  // v~_1 = A_U^T z_k / beta1
                 P.vv[p] = v1;
@@ -750,7 +751,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
             rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
-            for (long long p = gthread(); p < nJ; p += nthreads()) {
+            for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
                 const int i = P.jlist[p];
                 P.uu[p] = P.r[i];  // u~_1 = r_J
                 if (F32) P.uu32[p] = (float)P.r[i];
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
             acc.lsqr_nu += (long long)stepsU * nU;
             acc.lsqr_nj += (long long)stepsJ * nJ;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0 && P.tr_counts && k < P.tr_count_cap) {
+        if (trank(P) == 0 && threadIdx.x == 0 && P.tr_counts && k < P.tr_count_cap) {
             P.tr_counts[4 * k + 0] = nU;
             P.tr_counts[4 * k + 1] = nJ;
             P.tr_counts[4 * k + 2] = stepsU;
@@ -811,15 +812,75 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
     }
 }
 
+// A single solve: the whole grid is one team.
+template <bool F32>
+__global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
+    __shared__ SolveSmem S;
+    extern __shared__ __align__(16) unsigned char dsmem[];
+    enter_team(P);
+    solve_body<F32>(P, S, dsmem);
+}
+
+// Many independent systems in one cooperative launch: the grid is cut into
+// teams of `team` consecutive CTAs; team t solves the systems
+// plan[t * stride], plan[t * stride + 1], ... (ending at -1) one after
+// another, each to its own stopping rule (its Params and control block in
+// sys[]), with barriers among the team's CTAs only.
+template <bool F32>
+__global__ void __launch_bounds__(kSolveMaxThreads, 1)
+    batched_solve_kernel(const Params *sys, const int *plan, int stride, int team) {
+    __shared__ SolveSmem S;
+    __shared__ Params SP;
+    extern __shared__ __align__(16) unsigned char dsmem[];
+    const int t = (int)(blockIdx.x / (unsigned)team);
+    for (int q = 0; q < stride; ++q) {
+        const int i = plan[(long long)t * stride + q];
+        if (i < 0) break;
+        {
+            const int *src = reinterpret_cast<const int *>(sys + i);
+            int *dst = reinterpret_cast<int *>(&SP);
+            for (int w = threadIdx.x; w < (int)(sizeof(Params) / sizeof(int)); w += blockDim.x)
+                dst[w] = src[w];
+        }
+        __syncthreads();
+        enter_team(SP);
+        solve_body<F32>(SP, S, dsmem);
+        __syncthreads();
+    }
+}
+
+// Resets the control blocks of a batch (one thread each).
+__global__ void reset_ctrls_kernel(const Params *sys, int nsys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsys) return;
+    Ctrl *c = sys[i].ctrl;
+    c->bar_count = 0;
+    c->abort = 0;
+    c->status = kStatusRunning;
+    c->stop_req = 0;
+}
+
+// Copies the control blocks of a batch into one array (for one host copy).
+__global__ void gather_ctrls_kernel(const Params *sys, int nsys, Ctrl *out) {
+    const int i = blockIdx.x;
+    if (i >= nsys) return;
+    const int *src = reinterpret_cast<const int *>(sys[i].ctrl);
+    int *dst = reinterpret_cast<int *>(out + i);
+    for (int w = threadIdx.x; w < (int)(sizeof(Ctrl) / sizeof(int)); w += blockDim.x)
+        dst[w] = src[w];
+}
+
 // ---------------------------------------------------------------------------
 // Component kernels
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSolveMaxThreads) spmv_kernel(const Params P, const double *x,
                                                                 double *y) {
+    enter_team(P);
     rows_matvec(P, x, y);
 }
 __global__ void __launch_bounds__(kSolveMaxThreads) spmv_t_kernel(const Params P, const double *z,
                                                                   double *g) {
+    enter_team(P);
     cols_matvec(P, z, g);
 }
 
@@ -832,8 +893,9 @@ __global__ void __launch_bounds__(kSolveMaxThreads)
     adjoint_vals_kernel(const Params P, const double *b, const double *ax, const double *w,
                         const double *v, const double *x, const double *u, const double *g,
                         const double *q, double *gv) {
+    enter_team(P);
     const Grp G(P.ipr);
-    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         if (i >= P.m) continue;
         const double ri = __dsub_rn(b[i], ax[i]);
@@ -878,13 +940,14 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
     sample_kernel(const Params P, const double *eps, long long len, long long s,
                   unsigned long long seed, unsigned long long sysid, unsigned long long k,
                   unsigned long long phase, int *idx, bool greedy, double eta) {
+    enter_team(P);
     __shared__ SolveSmem S;
     BlockScratch &bs = S.bs;
-    const int nct = gridDim.x;
+    const int nct = tsize(P);
     if (threadIdx.x == 0) S.epoch = 0;
     double emax = 0.0;
     long long bad = 0;
-    for (long long j = gthread(); j < len; j += nthreads()) {
+    for (long long j = tthread(P); j < len; j += tthreads(P)) {
         const double e = eps[j];
         if (!isfinite(e) || e < 0.0) bad = 1;
         else emax = max_nonneg(emax, e);
@@ -892,8 +955,8 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
     emax = block_max(emax, bs);
     bad = block_sum(bad, bs);
     if (threadIdx.x == 0) {
-        P.pd[D_EMAX_C * nct + blockIdx.x] = emax;
-        P.pi[I_BAD_C * nct + blockIdx.x] = bad;
+        P.pd[D_EMAX_C * nct + trank(P)] = emax;
+        P.pi[I_BAD_C * nct + trank(P)] = bad;
     }
     RGD_SYNC(DS(D_EMAX_C), DS(D_EMAX_C), DS(I_BAD_C));
     emax = S.red_d[D_EMAX_C];
@@ -910,7 +973,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
         RGD_SYNC(0, 0, 0);
         count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (trank(P) == 0 && threadIdx.x == 0) {
         P.ctrl->sample_count = bad ? -1 : count;
         __threadfence();
         atomicCAS(&P.ctrl->status, kStatusRunning, RGDBEK_OK);
@@ -945,6 +1008,7 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
 
 cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s) {
     Params p = P;
+    p.team = grid;
     void *args[] = {&p};
     const void *fn = P.fp32_inner ? (const void *)solve_kernel<true>
                                   : (const void *)solve_kernel<false>;
@@ -956,6 +1020,7 @@ cudaError_t launch_sample(const Params &P, int grid, int block, const double *ep
                           unsigned long long k, unsigned long long phase, int *idx, bool greedy,
                           double eta, cudaStream_t st) {
     Params p = P;
+    p.team = grid;
     void *args[] = {&p, &eps, &len, &s, &seed, &sysid, &k, &phase, &idx, &greedy, &eta};
     return cudaLaunchCooperativeKernel((const void *)sample_kernel, dim3(grid), dim3(block), args, 0,
                                        st);
@@ -963,13 +1028,17 @@ cudaError_t launch_sample(const Params &P, int grid, int block, const double *ep
 
 cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, double *y,
                         cudaStream_t s) {
-    spmv_kernel<<<grid, block, 0, s>>>(P, x, y);
+    Params p = P;
+    p.team = grid;
+    spmv_kernel<<<grid, block, 0, s>>>(p, x, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
                           cudaStream_t s) {
-    spmv_t_kernel<<<grid, block, 0, s>>>(P, z, g);
+    Params p = P;
+    p.team = grid;
+    spmv_t_kernel<<<grid, block, 0, s>>>(p, z, g);
     return cudaGetLastError();
 }
 
@@ -977,7 +1046,9 @@ cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const doub
                                 const double *ax, const double *w, const double *v,
                                 const double *x, const double *u, const double *g,
                                 const double *q, double *gv, cudaStream_t s) {
-    adjoint_vals_kernel<<<grid, block, 0, s>>>(P, b, ax, w, v, x, u, g, q, gv);
+    Params p = P;
+    p.team = grid;
+    adjoint_vals_kernel<<<grid, block, 0, s>>>(p, b, ax, w, v, x, u, g, q, gv);
     return cudaGetLastError();
 }
 
@@ -987,19 +1058,42 @@ cudaError_t launch_weights(const double *v, const double *norm2, long long len, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int stride, int team,
+                                 int nteams, bool fp32, int block, cudaStream_t s) {
+    void *args[] = {&sys_dev, &plan_dev, &stride, &team};
+    const void *fn = fp32 ? (const void *)batched_solve_kernel<true>
+                          : (const void *)batched_solve_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(nteams * team), dim3(block), args,
+                                       (size_t)kSolveDsmemBytes, s);
+}
+
+cudaError_t launch_reset_ctrls(const Params *sys_dev, int nsys, cudaStream_t s) {
+    if (nsys <= 0) return cudaSuccess;
+    reset_ctrls_kernel<<<(nsys + 255) / 256, 256, 0, s>>>(sys_dev, nsys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_ctrls(const Params *sys_dev, int nsys, Ctrl *out, cudaStream_t s) {
+    if (nsys <= 0) return cudaSuccess;
+    gather_ctrls_kernel<<<nsys, 128, 0, s>>>(sys_dev, nsys, out);
+    return cudaGetLastError();
+}
+
 int solve_blocks_per_sm(int block) {
-    if (cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSolveDsmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSolveDsmemBytes) != cudaSuccess)
-        return 0;
-    int nb = 0, nb32 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, block,
-                                                      kSolveDsmemBytes) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb32, solve_kernel<true>, block,
-                                                      kSolveDsmemBytes) != cudaSuccess)
-        return 0;
-    return nb < nb32 ? nb : nb32;
+    const void *fns[4] = {(const void *)solve_kernel<false>, (const void *)solve_kernel<true>,
+                          (const void *)batched_solve_kernel<false>,
+                          (const void *)batched_solve_kernel<true>};
+    int best = 1 << 30;
+    for (const void *f : fns) {
+        int nb = 0;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSolveDsmemBytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, kSolveDsmemBytes) !=
+                cudaSuccess)
+            return 0;
+        if (nb < best) best = nb;
+    }
+    return best;
 }
 
 int sample_blocks_per_sm(int block) {

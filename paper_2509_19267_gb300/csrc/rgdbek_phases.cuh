@@ -67,6 +67,7 @@ struct Params {
     unsigned long long seed, sysid;
     int inner_max, stop_rule, selection;
     int fp32_inner;         // inner LSQR products in FP32 (Kahan dots)
+    int team;               // CTAs that work on this system (rank = blockIdx.x % team)
     float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
     int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
@@ -103,6 +104,35 @@ __device__ __forceinline__ long long gthread() {
 }
 __device__ __forceinline__ long long nthreads() {
     return (long long)gridDim.x * blockDim.x;
+}
+
+// The CTAs that solve one system form a team: the whole grid for a single
+// solve, `team` consecutive CTAs of a batched launch.  Phase code indexes by
+// the CTA's rank in its team and by the team's size.
+// The rank is computed once per kernel by enter_team (every kernel that runs
+// phase code calls it first) and kept in shared memory.
+__shared__ int s_team_rank;
+__device__ __forceinline__ void enter_team(const Params &P) {
+    if (threadIdx.x == 0) s_team_rank = (int)(blockIdx.x % (unsigned)P.team);
+    __syncthreads();
+}
+__device__ __forceinline__ int trank(const Params &P) {
+    (void)P;
+    // re-read at each use (like a special register) rather than held live
+    return *reinterpret_cast<volatile int *>(&s_team_rank);
+}
+__device__ __forceinline__ int tsize(const Params &P) { return P.team; }
+__device__ __forceinline__ long long twarp(const Params &P) {
+    return (long long)trank(P) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+}
+__device__ __forceinline__ long long twarps(const Params &P) {
+    return (long long)P.team * (blockDim.x >> 5);
+}
+__device__ __forceinline__ long long tthread(const Params &P) {
+    return (long long)trank(P) * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ long long tthreads(const Params &P) {
+    return (long long)P.team * blockDim.x;
 }
 
 // Loads through the read-only path (RO) for arrays that never change during
@@ -194,7 +224,7 @@ __device__ __forceinline__ int lane_count(long long e, long long e1, long long L
 // y = A x (rows of the CSR form, L lanes per row).  Component entry point.
 __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, double *y) {
     const Grp G(P.tpr);
-    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
         if (i < P.m)
@@ -208,7 +238,7 @@ __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, 
 // g = A^T z (columns of the CSC form, L lanes per column).  Component entry point.
 __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, double *gout) {
     const Grp G(P.tpc);
-    for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
         double s = 0.0;
         if (j < P.n)
@@ -228,7 +258,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
     const Grp G(P.tpc);
     double emax = 0.0, hh = 0.0;
     long long bad = 0;
-    for (long long base = gwarp() * G.rpw; base < P.n; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
         double sg = 0.0, sh = 0.0;
         if (j < P.n)
@@ -251,9 +281,9 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
     hh = block_sum(hh, bs);
     bad = block_sum(bad, bs);
     if (threadIdx.x == 0) {
-        P.pd[D_EMAX_C * gridDim.x + blockIdx.x] = emax;
-        P.pd[D_HH * gridDim.x + blockIdx.x] = hh;
-        P.pi[I_BAD_C * gridDim.x + blockIdx.x] = bad;
+        P.pd[D_EMAX_C * tsize(P) + trank(P)] = emax;
+        P.pd[D_HH * tsize(P) + trank(P)] = hh;
+        P.pi[I_BAD_C * tsize(P) + trank(P)] = bad;
     }
 }
 
@@ -261,7 +291,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
 __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs) {
     const Grp G(P.tpr);
     double tt = 0.0;
-    for (long long base = gwarp() * G.rpw; base < P.m; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
         if (i < P.m)
@@ -275,7 +305,7 @@ __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs
         }
     }
     tt = block_sum(tt, bs);
-    if (threadIdx.x == 0) P.pd[D_TT * gridDim.x + blockIdx.x] = tt;
+    if (threadIdx.x == 0) P.pd[D_TT * tsize(P) + trank(P)] = tt;
 }
 
 // ---------------------------------------------------------------------------
@@ -296,7 +326,7 @@ struct Chunk {
 __device__ __forceinline__ void phase_quantize(const Params &P, const double *eps, long long len,
                                                double emax, bool greedy, double eta,
                                                BlockScratch &bs) {
-    const Chunk C(len, blockIdx.x, gridDim.x);
+    const Chunk C(len, trank(P), tsize(P));
     if (greedy) {
         const double thr = __dmul_rn(eta, emax);
         for (long long j = C.lo + threadIdx.x; j < C.hi; j += blockDim.x) {
@@ -320,7 +350,7 @@ __device__ __forceinline__ void phase_quantize(const Params &P, const double *ep
         if (j < C.hi) P.Q[j] = run + ex + q;
         run += tot;
     }
-    if (threadIdx.x == 0) P.pi[I_TOT * gridDim.x + blockIdx.x] = (long long)run;
+    if (threadIdx.x == 0) P.pi[I_TOT * tsize(P) + trank(P)] = (long long)run;
 }
 
 // s independent draws: R = word (t mod 4) of Philox4x64-10 with key
@@ -331,13 +361,13 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
                                            unsigned long long seed, unsigned long long sysid,
                                            unsigned long long k, unsigned long long phase,
                                            long long *tab, BlockScratch &bs) {
-    const int nct = gridDim.x;
+    const int nct = tsize(P);
     partials_prefix(P.pi + I_TOT * nct, nct, tab, bs);
     const unsigned long long qtot = (unsigned long long)tab[nct - 1];
     if (qtot == 0) return;
     const long long csize = (len + nct - 1) / nct;
     const long long nblk = (s + 3) >> 2;
-    for (long long t4 = gthread(); t4 < nblk; t4 += nthreads()) {
+    for (long long t4 = tthread(P); t4 < nblk; t4 += tthreads(P)) {
         const U64x4 R = philox4x64_10(seed, sysid, k, phase, (unsigned long long)t4, 0ull);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -367,7 +397,7 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 __device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
                                                     const double *norm2, const double *vec,
                                                     BlockScratch &bs) {
-    const Chunk C(len, blockIdx.x, gridDim.x);
+    const Chunk C(len, trank(P), tsize(P));
     long long cnt = 0;
     double fro = 0.0, ext = 0.0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
@@ -384,9 +414,9 @@ __device__ __forceinline__ void phase_compact_count(const Params &P, long long l
     fro = block_sum(fro, bs);
     ext = block_sum(ext, bs);
     if (threadIdx.x == 0) {
-        P.pi[I_CNT * gridDim.x + blockIdx.x] = cnt;
-        P.pd[D_FRO * gridDim.x + blockIdx.x] = fro;
-        P.pd[D_EXTRA * gridDim.x + blockIdx.x] = ext;
+        P.pi[I_CNT * tsize(P) + trank(P)] = cnt;
+        P.pd[D_FRO * tsize(P) + trank(P)] = fro;
+        P.pd[D_EXTRA * tsize(P) + trank(P)] = ext;
     }
 }
 
@@ -418,11 +448,11 @@ __device__ __forceinline__ long long block_rank_pred(bool f, BlockScratch &bs, l
 __device__ __forceinline__ long long phase_compact_write(const Params &P, long long len, int *pos,
                                                          int *list, long long *tab,
                                                          BlockScratch &bs) {
-    const int nct = gridDim.x;
+    const int nct = tsize(P);
     partials_prefix(P.pi + I_CNT * nct, nct, tab, bs);
     const long long total = tab[nct - 1];
-    const Chunk C(len, blockIdx.x, nct);
-    long long run = blockIdx.x > 0 ? tab[blockIdx.x - 1] : 0;
+    const Chunk C(len, trank(P), nct);
+    long long run = trank(P) > 0 ? tab[trank(P) - 1] : 0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
         const bool f = j < C.hi && P.flag[j];
@@ -464,7 +494,7 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
     const Grp G(A.L);
     const long long L = G.L;
     long long total = 0;
-    for (long long base = gwarp() * G.rpw; base < A.n; base += nwarps() * G.rpw) {
+    for (long long base = twarp(P) * G.rpw; base < A.n; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         const bool valid = i < A.n;
         const long long e0 = valid ? __ldg(A.ptr + i) : 0;
@@ -500,7 +530,7 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
         }
     }
     total = block_sum(total, bs);
-    if (threadIdx.x == 0) P.pi[I_NNZ * gridDim.x + blockIdx.x] = total;
+    if (threadIdx.x == 0) P.pi[I_NNZ * tsize(P) + trank(P)] = total;
 }
 
 __device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {

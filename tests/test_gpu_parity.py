@@ -303,6 +303,9 @@ def test_batched_matches_single(rg):
                for S in systems]
     bs = [G.dev(S.b) for S in systems]
     xs = [torch.empty(S.n, dtype=torch.float64, device="cuda") for S in systems]
+    # with the whole grid as the team, each system is solved exactly as
+    # rgdbek_solve would (system_id = its index)
+    solvers[0].set_options(batch_team=solvers[0].info().grid)
     status, stats = rg.rgdbek_solve_batched([s.handle for s in solvers], bs, xs,
                                             [1e-10] * 3, 3000, seed=6)
     assert status == rg.OK

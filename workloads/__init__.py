@@ -23,6 +23,12 @@ Workloads (the recipe of each is restated in the design notes):
                       values) and b = A x + 1% Gaussian noise
   deblur_regularised  [A; lam I] and [b; 0] for that blur (lam = 0.05): the
                       full-column-rank system of the adjoint workload
+  poisson_p1          -Laplace(u) = f on the unit square, P1 elements on a
+                      uniform right-triangle grid, Dirichlet rows as identity
+                      rows; K x* = b with x* = sin(pi x) sin(pi y) + noise
+                      (the mixed-precision workload)
+  blur_batch          many blur_image systems of uneven sizes (the batched
+                      workload)
 """
 from __future__ import annotations
 
@@ -261,3 +267,12 @@ def poisson_p1(nx: int = 1024, sigma: float = 1e-3, seed: int = 2,
     b = _csr_matvec(rp, ci, av, x)
     N = nx * nx
     return System(f"poisson_p1_{nx}x{nx}", N, N, rp, ci, av, b, x, True)
+
+
+def blur_batch(count: int = 256, side_lo: int = 64, side_hi: int = 512, seed: int = 3) -> list:
+    """`count` independent deblurring systems of uneven sizes: side lengths
+    uniform in [side_lo, side_hi], each the blur_image recipe with its own
+    seed (seed * 100003 + i)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, size=count)
+    return [blur_image(int(s), seed=seed * 100003 + i) for i, s in enumerate(sides)]
