@@ -9,6 +9,18 @@ is outer iterations per second over the K timed solves, with the matrix and
 b resident in HBM; L2 is flushed (a 256 MiB write) before every timed solve.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload sparse_ls|batched_deblur|poisson_mixed|deblur_adjoint]
+
+The default workload is the headline above.  The others measure the other
+forms of the solver, one JSON line each, on one GPU:
+  batched_deblur  256 blur systems of sides 64..512 (2.07e9 nonzeros in all),
+                  a fixed budget of outer iterations each, in ONE batched
+                  launch (team size from the tuner); against solving them one
+                  after another with the whole GPU each
+  poisson_mixed   the P1 Poisson system on 1024 x 1024 nodes (1.05e6
+                  unknowns), a fixed budget, FP32 inner products against FP64
+  deblur_adjoint  the implicit adjoint on the regularised 256 x 256 deblur
+                  ([A; 0.05 I], 131072 x 65536), FP64 and FP32 inner products
 
 --impl reference times the FP64 CPU oracle (the plain implementation of the
 paper's Algorithm 1 used by the tests) on the same workload, each step a
@@ -53,6 +65,11 @@ def parse():
                     help="cap on outer iterations per solve (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="sparse_ls",
+                    choices=["sparse_ls", "batched_deblur", "poisson_mixed", "deblur_adjoint"])
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--budget", type=int, default=None,
+                    help="outer iterations per system (batched_deblur, poisson_mixed)")
     return ap.parse_args()
 
 
@@ -455,10 +472,184 @@ def end_to_end(rg, S, opts, w, max_iter, args):
             "what": "rgdbek_create from pinned host CSR + rgdbek_solve_host + destroy per step"}
 
 
+def _setup_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_rgdbek_build", os.path.join(ROOT, "paper_2509_19267_gb300", "build.py"))
+    bmod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bmod)
+    bmod.build()
+    import paper_2509_19267_gb300 as rg
+    return torch, rg
+
+
+def _timed(torch, fn, steps):
+    stream = torch.cuda.current_stream()
+    ms, outs = [], []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        outs.append(fn())
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms, outs
+
+
+def run_batched_deblur(args):
+    """Many uneven systems in one persistent launch, against one solve after
+    another; a fixed budget of outer iterations per system."""
+    torch, rg = _setup_gpu()
+    budget = args.budget or 10
+    t0 = time.perf_counter()
+    S = workloads.blur_batch(args.batch_count, 64, 512, seed=3)
+    gen_s = time.perf_counter() - t0
+    opts = dict(eta_col=0.1, eta_row=0.1, stop_rule=rg.STOP_REL_RES)
+    hs = [rg.Solver(s.m, s.n, s.row_ptr, s.col_idx, s.vals, **opts) for s in S]
+    H = [h.handle for h in hs]
+    bs = [torch.from_numpy(s.b).cuda() for s in S]
+    xs = [torch.empty(s.n, dtype=torch.float64, device="cuda") for s in S]
+    tols = [1e-8] * len(S)
+    team, tune_ms = rg.rgdbek_tune_batched(H, bs, xs, tols, probe_iters=2)
+    for _ in range(args.warmup):
+        rg.rgdbek_solve_batched(H, bs, xs, tols, budget, seed=0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, outs = _timed(torch, lambda: rg.rgdbek_solve_batched(H, bs, xs, tols, budget, seed=0),
+                      args.steps)
+    clk = clocks.stop()
+    iters = sum(st.iters for st in outs[0][1])
+    value = iters * args.steps / (sum(ms) / 1e3)
+
+    def sequential():
+        its = 0
+        for h, b, x in zip(hs, bs, xs):
+            its += rg.rgdbek_solve(h.handle, b, x, 1e-8, budget, 0).iters
+        return its
+
+    sequential()
+    ms_seq, outs_seq = _timed(torch, sequential, 1)
+    seq_value = outs_seq[0] / (ms_seq[0] / 1e3)
+    rel = [st.rel_res for st in outs[0][1]]
+    line = {"metric": f"batched RGDBEK system-iterations/s ({len(S)} deblur systems, "
+                      f"{budget}-iteration budget each)",
+            "value": value, "unit": "system-iters/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"blur_batch_{len(S)}_sides64-512", "systems": len(S),
+                       "unknowns": int(sum(s.n for s in S)), "nnz": int(sum(s.nnz for s in S)),
+                       "eta": 0.1, "budget": budget, "team": team,
+                       "teams": hs[0].info().grid // team,
+                       "l2": "inputs larger than L2 (25 GB of CSR)"},
+            "tuner_ms": {str(k): v for k, v in tune_ms.items()},
+            "sequential": {"value": seq_value, "unit": "system-iters/s",
+                           "ms": ms_seq[0], "what": "rgdbek_solve per system, whole GPU each"},
+            "speedup_vs_sequential": value / seq_value,
+            "rel_res_after_budget": {"min": min(rel), "median": statistics.median(rel),
+                                     "max": max(rel)},
+            "generate_s": gen_s, "gpu_launches": args.steps * 4, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for h in hs:
+        h.close()
+
+
+def run_poisson_mixed(args):
+    """FP32 inner products against FP64 on the P1 Poisson system, fixed budget."""
+    torch, rg = _setup_gpu()
+    budget = args.budget or 500
+    S = workloads.poisson_p1(1024, seed=2)
+    b = torch.from_numpy(S.b).cuda()
+    res = {}
+    xs = {}
+    for name, prec in (("fp64", rg.PRECISION_FP64), ("fp32_inner", rg.PRECISION_FP32_INNER)):
+        h = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=0.1, eta_row=0.1,
+                      stop_rule=rg.STOP_REL_RES, precision=prec, inner_tol=1e-6)
+        x = torch.empty(S.n, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            rg.rgdbek_solve(h.handle, b, x, 1e-8, min(budget, 20), 0)
+        ms, outs = _timed(torch, lambda: rg.rgdbek_solve(h.handle, b, x, 1e-8, budget, 0),
+                          args.steps)
+        st = outs[-1]
+        res[name] = {"iters_per_s": st.iters * args.steps / (sum(ms) / 1e3),
+                     "ms_per_solve": statistics.mean(ms), "iters": st.iters,
+                     "rel_res": st.rel_res,
+                     "lsqr_steps_per_iter": (st.inner_u + st.inner_j) / max(st.iters, 1)}
+        xs[name] = x.clone()
+        h.close()
+    diff = float(torch.linalg.norm(xs["fp32_inner"] - xs["fp64"]) / torch.linalg.norm(xs["fp64"]))
+    xstar = torch.from_numpy(S.x_true).cuda()
+    line = {"metric": f"P1 Poisson 1024x1024 outer iterations/s, FP32 inner products "
+                      f"({budget}-iteration budget)",
+            "value": res["fp32_inner"]["iters_per_s"], "unit": "iters/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fp32_inner"]["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer",
+            "data": "synthetic",
+            "config": {"workload": "poisson_p1_1024x1024", "unknowns": S.n, "nnz": S.nnz,
+                       "eta": 0.1, "budget": budget, "inner_tol": 1e-6,
+                       "l2": "inputs larger than L2 after the solver's workspace"},
+            "fp64": res["fp64"], "fp32_inner": res["fp32_inner"],
+            "speedup_vs_fp64": res["fp32_inner"]["iters_per_s"] / res["fp64"]["iters_per_s"],
+            "rel_diff_x_fp32_vs_fp64": diff,
+            "rel_err_vs_x_star": {k: float(torch.linalg.norm(v - xstar) / torch.linalg.norm(xstar))
+                                  for k, v in xs.items()},
+            "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_deblur_adjoint(args):
+    """Forward solve and implicit adjoint on the regularised 256 x 256 deblur."""
+    torch, rg = _setup_gpu()
+    S = workloads.deblur_regularised(256)
+    b = torch.from_numpy(S.b).cuda()
+    xt = torch.from_numpy(S.x_true).cuda()
+    out = {}
+    for name, prec in (("fp64", rg.PRECISION_FP64), ("fp32_inner", rg.PRECISION_FP32_INNER)):
+        h = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=0.1, eta_row=0.1,
+                      stop_rule=rg.STOP_NORMAL, precision=prec)
+        fwd = h.solve(b, tol=1e-10, max_iter=200000, seed=0)
+        x = fwd.x
+        g = 2.0 * (x - xt)
+        steps = max(1, min(args.steps, 2))
+        ms, outs = _timed(torch, lambda: h.backward(b, x, g, tol=1e-10, max_iter=200000,
+                                                    seed=1, nnz=S.nnz), steps)
+        gb, gv, status, st = outs[-1]
+        gx = float(torch.dot(g, x))
+        out[name] = {"backward_s": statistics.mean(ms) / 1e3, "status": status,
+                     "solve_iters": [st[0].iters, st[1].iters],
+                     "forward_iters": fwd.stats.iters,
+                     "identity_db": abs(float(torch.dot(gb, b)) - gx) / abs(gx),
+                     "identity_dA": abs(float(torch.dot(gv, torch.from_numpy(S.vals).cuda())) + gx)
+                     / abs(gx)}
+        h.close()
+    line = {"metric": "implicit adjoint of the regularised 256x256 deblur: backward passes/s",
+            "value": 1.0 / out["fp64"]["backward_s"], "unit": "backward/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * out["fp64"]["backward_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "deblur_regularised_256x256_lam0.05", "m": S.m, "n": S.n,
+                       "nnz": S.nnz, "eta": 0.1, "tol": 1e-10,
+                       "loss": "||x - x_true||^2"},
+            "fp64": out["fp64"], "fp32_inner": out["fp32_inner"],
+            "gpu_launches": 6 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_deblur":
+        run_batched_deblur(args)
+    elif args.workload == "poisson_mixed":
+        run_poisson_mixed(args)
+    elif args.workload == "deblur_adjoint":
+        run_deblur_adjoint(args)
     else:
         run_ours(args)
 
