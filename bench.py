@@ -421,11 +421,13 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
         for _ in range(3):
             fn()
         ts = []
-        for i in range(10):
-            # the flush (a 256 MiB write) evicts A from L2 and keeps the GPU
-            # busy while the host queues the timed launch
-            flush.fill_(float(i))
+        for i in range(20):
             a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            # the flush (a 256 MiB write) evicts A from L2; the GPU-side delay
+            # after it keeps the GPU busy while the host queues the start event
+            # and the timed launch, so that no host launch latency is timed
+            flush.fill_(float(i))
+            torch.cuda._sleep(400000)
             a.record(stream)
             fn()
             bb.record(stream)
