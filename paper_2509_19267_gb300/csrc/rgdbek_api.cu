@@ -129,14 +129,14 @@ int check_options(const rgdbek_options &o) {
     if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
-         o.threads_per_block > kSolveMaxThreads))
+         o.threads_per_block > kSolveThreads))
         return RGDBEK_ERR_INVALID_ARG;
     return RGDBEK_OK;
 }
 
 // launch shape of the persistent kernels for the handle's options
 int configure_launch(rgdbek_s *h) {
-    const int block = h->opt.threads_per_block ? h->opt.threads_per_block : kSolveMaxThreads;
+    const int block = h->opt.threads_per_block ? h->opt.threads_per_block : kSolveThreads;
     int fit = solve_blocks_per_sm(block);
     int fit_s = sample_blocks_per_sm(block);
     if (fit < 1 || fit_s < 1) return RGDBEK_ERR_CUDA;
@@ -743,15 +743,15 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
         int s2 = run_solve(h, true, x, h->adj_u, tol, max_iter, seed + 2, S + 2);
         fold(s2);
         if (s2 < 0) return s2;
-        if ((e = launch_spmv(P, h->grid, h->block, grad_x, h->adj_ag, h->stream)) != cudaSuccess)
+        if ((e = launch_spmv(P, h->num_sms, kSolveMaxThreads, grad_x, h->adj_ag, h->stream)) != cudaSuccess)
             return cuda_status(e);
         int s3 = run_solve(h, false, h->adj_ag, h->adj_q, tol, max_iter, seed + 3, S + 3);
         fold(s3);
         if (s3 < 0) return s3;
     }
-    e = launch_spmv(P, h->grid, h->block, x, h->adj_ax, h->stream);
+    e = launch_spmv(P, h->num_sms, kSolveMaxThreads, x, h->adj_ax, h->stream);
     if (e == cudaSuccess)
-        e = launch_adjoint_vals(P, h->grid, h->block, b, h->adj_ax, h->adj_w, h->adj_v, x,
+        e = launch_adjoint_vals(P, h->num_sms, kSolveMaxThreads, b, h->adj_ax, h->adj_w, h->adj_v, x,
                                 rank_term ? h->adj_u : nullptr, grad_x,
                                 rank_term ? h->adj_q : nullptr, grad_vals, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -760,12 +760,12 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
 
 int rgdbek_spmv(rgdbek_t h, const double *x, double *y) {
     if (!h || !x || !y) return RGDBEK_ERR_INVALID_ARG;
-    return cuda_status(launch_spmv(make_params(h), h->grid, h->block, x, y, h->stream));
+    return cuda_status(launch_spmv(make_params(h), h->num_sms, kSolveMaxThreads, x, y, h->stream));
 }
 
 int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g) {
     if (!h || !z || !g) return RGDBEK_ERR_INVALID_ARG;
-    return cuda_status(launch_spmv_t(make_params(h), h->grid, h->block, z, g, h->stream));
+    return cuda_status(launch_spmv_t(make_params(h), h->num_sms, kSolveMaxThreads, z, g, h->stream));
 }
 
 int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *eps_max) {
@@ -773,7 +773,7 @@ int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *
     const long long len = which == 0 ? h->n : h->m;
     cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
     if (e == cudaSuccess)
-        e = launch_weights(v, which == 0 ? h->cn2 : h->rn2, len, eps, h->ctrl, h->grid, h->block,
+        e = launch_weights(v, which == 0 ? h->cn2 : h->rn2, len, eps, h->ctrl, h->num_sms, kSolveMaxThreads,
                            h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     const int rs = read_ctrl(h);

@@ -9,7 +9,11 @@
 
 namespace rgd {
 
-constexpr int kSolveMaxThreads = 1024;  // launch bound of the persistent kernels
+constexpr int kSolveMaxThreads = 1024;  // launch bound of the component kernels and the sampler
+// launch bound and default block of the solve kernels: 512 threads leave 128
+// registers a thread (no spills); measured faster than 1024 threads with 64
+// registers and than 256 threads
+constexpr int kSolveThreads = 512;
 // dynamic shared memory of a solve CTA: its chunk of the inner-solve block
 constexpr int kSolveDsmemBytes = 96 * 1024;
 

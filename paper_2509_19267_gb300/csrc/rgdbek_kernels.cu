@@ -814,7 +814,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
 
 // A single solve: the whole grid is one team.
 template <bool F32>
-__global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params P) {
+__global__ void __launch_bounds__(kSolveThreads, 1) solve_kernel(const Params P) {
     __shared__ SolveSmem S;
     extern __shared__ __align__(16) unsigned char dsmem[];
     enter_team(P);
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1) solve_kernel(const Params
 // another, each to its own stopping rule (its Params and control block in
 // sys[]), with barriers among the team's CTAs only.
 template <bool F32>
-__global__ void __launch_bounds__(kSolveMaxThreads, 1)
+__global__ void __launch_bounds__(kSolveThreads, 1)
     batched_solve_kernel(const Params *sys, const int *plan, int stride, int team) {
     __shared__ SolveSmem S;
     __shared__ Params SP;
