@@ -32,7 +32,9 @@
  *     phase 0 for columns and 1 for rows; draw t uses word t mod 4.
  *   - the inner LSQR starts from 0 (so it returns the minimum-norm solution)
  *     and stops when ||B^T r|| <= tol ||B||_F ||r|| or ||r|| <= tol ||c||, or
- *     after inner_max steps.
+ *     after inner_max steps.  In the column step it runs on A_U with its
+ *     columns scaled to unit norm (the projection A_U A_U^+ z does not depend
+ *     on which least-squares solution is used).
  *   - a block whose weights are all zero is empty and its update is skipped;
  *     when both blocks are empty x can no longer change and the solve ends.
  */
@@ -410,6 +412,8 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
     int64_t *srp = malloc((size_t)(m + 1) * sizeof(int64_t));
     int32_t *sci = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
     double *sav = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    double *bsc = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    double *dcol = malloc((size_t)n * sizeof(double));
 
     orc_row_norms2(m, rp, av, rn2);
     orc_col_norms2(m, n, rp, ci, av, cn2);
@@ -435,7 +439,7 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
         if (tr) { tr->list_len = 0; tr->n_iters = 0; }
         free(rn2); free(cn2); free(z); free(t); free(r); free(Ax); free(g); free(h);
         free(epsz); free(epsx); free(y); free(d); free(rJ); free(U); free(J);
-        free(srp); free(sci); free(sav);
+        free(srp); free(sci); free(sav); free(bsc); free(dcol);
         return -2;
     }
     for (k = 0;; ++k) {
@@ -478,11 +482,18 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
         }
         int steps_u = 0;
         if (nu > 0) {
+            /* The least-squares problem min ||A_U y - z_k|| is solved by LSQR
+               on B = A_U D with D = diag(1 / ||A_j||) (unit columns), then
+               y = D y^.  Every least-squares solution gives the same A_U y,
+               the projection of z_k onto range(A_U), so the scaling changes
+               only the path of the inner solver, not z_{k+1}.  A selected
+               column has a positive weight, hence a positive norm. */
             extract_columns(m, n, rp, ci, av, nu, U, srp, sci, sav);
-            double fro2 = 0.0;
-            for (int64_t p = 0; p < nu; ++p) fro2 += cn2[U[p]];
-            steps_u = orc_lsqr(m, nu, srp, sci, sav, z, o->inner_tol, sqrt(fro2),
+            for (int64_t p = 0; p < nu; ++p) dcol[p] = 1.0 / sqrt(cn2[U[p]]);
+            for (int64_t e = 0; e < srp[m]; ++e) bsc[e] = sav[e] * dcol[sci[e]];
+            steps_u = orc_lsqr(m, nu, srp, sci, bsc, z, o->inner_tol, sqrt((double)nu),
                                o->inner_max, y);
+            for (int64_t p = 0; p < nu; ++p) y[p] *= dcol[p];
             orc_spmv(m, srp, sci, sav, y, Ax); /* A_U y */
             for (int64_t i = 0; i < m; ++i) z[i] -= Ax[i];
         }
@@ -554,6 +565,6 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
 
     free(rn2); free(cn2); free(z); free(t); free(r); free(Ax); free(g); free(h);
     free(epsz); free(epsx); free(y); free(d); free(rJ); free(U); free(J);
-    free(srp); free(sci); free(sav);
+    free(srp); free(sci); free(sav); free(bsc); free(dcol);
     return status;
 }

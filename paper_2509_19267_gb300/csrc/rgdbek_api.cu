@@ -34,6 +34,7 @@ struct rgdbek_s {
     double *sav, *scv;
     double *dots, *dots2;
     float *vv32, *uu32;
+    double *vvs, *dsc, *yh;
     double *pd;
     long long *pi;
     Ctrl *ctrl;
@@ -108,6 +109,9 @@ void carve(rgdbek_s *h, Layout &L) {
     h->dots2 = L.take<double>(mx);
     h->vv32 = L.take<float>(mx);
     h->uu32 = L.take<float>(mx);
+    h->vvs = L.take<double>(mx);
+    h->dsc = L.take<double>(mx);
+    h->yh = L.take<double>(mx);
     h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
     h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
     h->ctrl = L.take<Ctrl>(1);
@@ -209,6 +213,9 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
                       : h->opt.inner_tol;
     P.vv32 = h->vv32;
     P.uu32 = h->uu32;
+    P.vvs = h->vvs;
+    P.dsc = h->dsc;
+    P.yh = h->yh;
     P.inner_max = h->opt.inner_max;
     P.stop_rule = h->opt.stop_rule;
     P.selection = h->opt.selection;

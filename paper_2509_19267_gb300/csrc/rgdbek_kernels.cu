@@ -357,8 +357,12 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot, int 
 // P.vv and alpha1 is passed; otherwise it is computed first (one more
 // phase).  fro2 = ||B||_F^2.  y_g (v-space) receives the solution; with xt
 // given (the row step, v-space = x-space) also xt = x + y, so the residual
-// pass gathers x_{k+1} without an addition per nonzero.  Returns the number
-// of steps (0 if alpha1 == 0), or -1 if a grid barrier was abandoned.
+// pass gathers x_{k+1} without an addition per nonzero.  With csc (the column
+// step; requires v_given) the solve runs on B D, D = diag(csc) over the
+// v-space (unit columns): the rows phase gathers D v~, the cols phase scales
+// B^T u~ by D, and y_g receives y = D y^, so B y_g is the projection of c0
+// whatever the scaling.  Returns the number of steps (0 if alpha1 == 0), or
+// -1 if a grid barrier was abandoned.
 //
 // Per phase: grid barrier | warp 0 reduces the partials and updates the
 // scalars while warps 1.. compute the dot products of the CTA's lines |
@@ -366,7 +370,7 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot, int 
 template <bool f32>
 __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
                                         const double *c0, const float *c0_32, double *y_g,
-                                        double *xt, bool v_given,
+                                        double *xt, const double *csc, bool v_given,
                                         double alpha1, double beta1, double fro2,
                                         unsigned char *dsmem, long long dsmem_bytes,
                                         SolveSmem &S) {
@@ -381,14 +385,16 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
     double *wown = vown ? A.take<double>(ncl) : nullptr;
     double *yown = wown ? A.take<double>(ncl) : nullptr;
     double *dc = yown ? A.take<double>(ncl) : nullptr;
-    const bool st_smem = dc != nullptr;
+    // column scaling D of the v-space (column step): its slice
+    double *sown = (dc && csc) ? A.take<double>(ncl) : nullptr;
+    const bool st_smem = dc != nullptr && (sown != nullptr || csc == nullptr);
     if (!st_smem) {
         A = SmemArena{dsmem, dsmem_bytes, 0};
         uold = nullptr;
         dr = P.dots + RC.lo;
         vown = P.vv + CC.lo;
         wown = P.ww + CC.lo;
-        yown = y_g + CC.lo;
+        yown = (csc ? P.yh : y_g) + CC.lo;  // scaled: y^ apart from y = D y^
         dc = P.dots2 + CC.lo;
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = 0.0;
     } else {
@@ -396,8 +402,12 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
             vown[i] = v_given ? P.vv[CC.lo + i] : 0.0;
             yown[i] = 0.0;
+            if (sown) sown[i] = csc[CC.lo + i];
         }
     }
+    const double *dloc = csc ? (sown ? sown : csc + CC.lo) : nullptr;
+    // the rows phase gathers D v~ when the v-space is scaled
+    const double *vsrc = csc ? P.vvs : P.vv;
     const CtaSide R = cache_side<f32>(Rs, A, S.bs, trank(P), tsize(P));
     const CtaSide C = cache_side<f32>(Cs, A, S.bs, trank(P), tsize(P));
     if (threadIdx.x == 0) {
@@ -444,7 +454,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
     for (int it = 1;; ++it) {
         const bool first = it == 1;
         // ---- rows phase: u~_new = B v~ / alpha - (alpha/beta) u~, w update
-        cta_dots<f32>(R, P.vv, P.vv32, dr);
+        cta_dots<f32>(R, vsrc, P.vv32, dr);
         if (threadIdx.x < 32 && !first) {
             // scalars from ||v~||^2 of the previous cols phase
             const double vv = warp0_collect(P.pd, D_VV, tsize(P));
@@ -517,16 +527,18 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             const bool mv = L.mv != 0;
             double acc = 0.0;
             for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
+                const double dl = dloc ? dloc[li] : 1.0;
                 if (mv) {
-                    const double v = dc[li] * inv_b - ba * vown[li];
+                    const double v = (dloc ? dc[li] * dl : dc[li]) * inv_b - ba * vown[li];
                     vown[li] = v;
                     P.vv[CC.lo + li] = v;
-                    if (f32) P.vv32[CC.lo + li] = (float)v;
+                    if (dloc) P.vvs[CC.lo + li] = v * dl;
+                    if (f32) P.vv32[CC.lo + li] = (float)(dloc ? v * dl : v);
                     acc = fma(v, v, acc);
                 }
                 const double y = fma(phi_rho, wown[li], yown[li]);
                 yown[li] = y;
-                y_g[CC.lo + li] = y;
+                y_g[CC.lo + li] = dloc ? y * dl : y;   // y = D y^ when scaled
                 if (xt) xt[CC.lo + li] = P.x[CC.lo + li] + y;
             }
             acc = block_sum(acc, S.bs);
@@ -674,10 +686,13 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.n, P.cn2, P.g, bs);
+            phase_compact_count(P, P.n, P.cn2, P.g, P.epsc, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
-                // LSQR start on A_U with c = z_k: beta1 = ||z_k||, alpha1 = ||A_U^T z_k|| / beta1
+                // LSQR start on B = A_U D (columns scaled to unit norm, D =
+                // diag(1/||A_j||)) with c = z_k: beta1 = ||z_k||, alpha1 =
+                // ||B^T z_k|| / beta1 = sqrt(sum of the selected eps^z) / beta1,
+                // ||B||_F^2 = |U|
                 O.fro2 = S.red_d[D_FRO];
                 O.beta1 = sqrt(O.zz);
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
@@ -690,9 +705,12 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             const double inv_beta1 = O.inv_beta1;
             for (long long p = tthread(P); p < nU; p += tthreads(P)) {
                 const int j = P.ulist[p];
-                const double v1 = P.g[j] * inv_beta1;  // v~_1 = A_U^T z_k / beta1
+                const double d = rsqrt(P.cn2[j]);       // selected: ||A_j|| > 0
+                const double v1 = P.g[j] * d * inv_beta1;  // v~_1 = B^T z_k / beta1
+                P.dsc[p] = d;
                 P.vv[p] = v1;
-                if (F32) P.vv32[p] = (float)v1;
+                P.vvs[p] = v1 * d;
+                if (F32) P.vv32[p] = (float)(v1 * d);
                 P.yy[p] = 0.0;
                 if (rec_u) P.tr_lists[tr_off + p] = j;
             }
@@ -706,7 +724,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
                 const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, true, O.alpha1, O.beta1,
+                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, P.dsc, true, O.alpha1, O.beta1,
                                   O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
@@ -739,7 +757,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.m, P.rn2, P.r, bs);
+            phase_compact_count(P, P.m, P.rn2, P.r, nullptr, bs);
             RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on A^J with c = r_J: beta1 = ||r_J||
@@ -767,7 +785,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 const SideC rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
                 const SideC cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
                                  pick_lanes_fp64(nnzJ, P.n)};
-                stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, false, 0.0, O.beta1, O.fro2,
+                stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, nullptr, false, 0.0, O.beta1, O.fro2,
                                   dsmem, P.dsmem_bytes, S);
                 if (stepsJ < 0) return;
                 mark(S, PH_ROW_LSQR);
@@ -969,7 +987,7 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
             phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
             RGD_SYNC(0, 0, 0);
         }
-        phase_compact_count(P, len, eps, eps, bs);
+        phase_compact_count(P, len, eps, eps, nullptr, bs);
         RGD_SYNC(0, 0, 0);
         count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
     }

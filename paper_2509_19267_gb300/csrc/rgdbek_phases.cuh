@@ -69,6 +69,8 @@ struct Params {
     int fp32_inner;         // inner LSQR products in FP32 (Kahan dots)
     int team;               // CTAs that work on this system (rank = blockIdx.x % team)
     float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
+    double *vvs, *dsc;      // column step: D v~ and D = 1/||A_j|| per column of U
+    double *yh;             // column step: y^ of the scaled block (global fallback)
     int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
@@ -394,9 +396,12 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 
 // Count of marked indices in the chunk, and over them the sums of norm2 (the
 // block's squared Frobenius norm) and of vec^2 (for the LSQR start).
+// With unit (the column step, whose inner solve runs on A_U with unit
+// columns): fro counts the selected lines and ext sums their weights eps,
+// i.e. the squared Frobenius norm and ||B^T c||^2 of the column-scaled block.
 __device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
                                                     const double *norm2, const double *vec,
-                                                    BlockScratch &bs) {
+                                                    const double *unit, BlockScratch &bs) {
     const Chunk C(len, trank(P), tsize(P));
     long long cnt = 0;
     double fro = 0.0, ext = 0.0;
@@ -405,9 +410,14 @@ __device__ __forceinline__ void phase_compact_count(const Params &P, long long l
         const bool f = j < C.hi && P.flag[j];
         cnt += __popc(__ballot_sync(kFull, f)) * ((threadIdx.x & 31) == 0);
         if (f) {
-            fro += __ldg(norm2 + j);
-            const double v = vec[j];
-            ext = fma(v, v, ext);
+            if (unit) {
+                fro += 1.0;
+                ext += unit[j];
+            } else {
+                fro += __ldg(norm2 + j);
+                const double v = vec[j];
+                ext = fma(v, v, ext);
+            }
         }
     }
     cnt = block_sum(cnt, bs);
