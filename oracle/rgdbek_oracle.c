@@ -34,7 +34,10 @@
  *     and stops when ||B^T r|| <= tol ||B||_F ||r|| or ||r|| <= tol ||c||, or
  *     after inner_max steps.  In the column step it runs on A_U with its
  *     columns scaled to unit norm (the projection A_U A_U^+ z does not depend
- *     on which least-squares solution is used).
+ *     on which least-squares solution is used); in the row step, when |J| <= n,
+ *     first on A^J with its rows scaled to unit norm, which has the same
+ *     minimum-norm solution whenever the block system is consistent, and
+ *     again unscaled when LSQR finds it inconsistent.
  *   - a block whose weights are all zero is empty and its update is skipped;
  *     when both blocks are empty x can no longer change and the solve ends.
  */
@@ -227,12 +230,16 @@ int64_t orc_select_greedy(int64_t len, const double *eps, double emax, double et
 /* LSQR (Paige and Saunders, ACM TOMS 8(1), 1982) for min ||B y - c||, from  */
 /* y = 0, with B an mb x nb CSR matrix.  This is the inner solver the paper  */
 /* uses for the block pseudo-inverse products (Remark 3.1).  fro = ||B||_F.  */
-/* Returns the number of steps taken.                                        */
+/* Returns the number of steps taken; *fit (if not NULL) is set to 1 when   */
+/* it stopped because the residual itself met the tolerance (||r|| <= tol   */
+/* ||c||, or an exact fit), i.e. the block system was found consistent, and  */
+/* to 2 when it ran out of steps.                                            */
 /* ------------------------------------------------------------------------ */
-int orc_lsqr(int64_t mb, int64_t nb, const int64_t *rp, const int32_t *ci,
-             const double *av, const double *c, double tol, double fro, int maxit,
-             double *y)
+int orc_lsqr_fit(int64_t mb, int64_t nb, const int64_t *rp, const int32_t *ci,
+                 const double *av, const double *c, double tol, double fro, int maxit,
+                 double *y, int *fit)
 {
+    if (fit) *fit = 0;
     double *u = (double *)malloc((size_t)(mb > 0 ? mb : 1) * sizeof(double));
     double *v = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
     double *w = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
@@ -291,12 +298,22 @@ int orc_lsqr(int64_t mb, int64_t nb, const int64_t *rp, const int32_t *ci,
             double rnorm = phibar;
             double arnorm = phibar * alpha * fabs(cs);
             if (arnorm <= tol * fro * rnorm || rnorm <= tol * beta1 || alpha == 0.0 ||
-                beta == 0.0)
+                beta == 0.0) {
+                if (fit) *fit = (rnorm <= tol * beta1 || beta == 0.0) ? 1 : 0;
                 break;
+            }
+            if (it == maxit && fit) *fit = 2;
         }
     }
     free(u); free(v); free(w); free(tmp_m); free(tmp_n);
     return steps;
+}
+
+int orc_lsqr(int64_t mb, int64_t nb, const int64_t *rp, const int32_t *ci,
+             const double *av, const double *c, double tol, double fro, int maxit,
+             double *y)
+{
+    return orc_lsqr_fit(mb, nb, rp, ci, av, c, tol, fro, maxit, y, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -519,14 +536,35 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
         }
         int steps_j = 0;
         if (nj > 0) {
+            /* (A^J)^+ r_J by LSQR.  When |J| <= n the block is first solved
+               with its rows scaled to unit norm, D (A^J) d = D r_J with
+               D = diag(1/||A^(i)||): if that system is consistent it has the
+               same solutions as A^J d = r_J, so LSQR from 0 returns the same
+               minimum-norm d.  Only when LSQR finds it inconsistent (it stops
+               on the normal-equation test, not on the residual) is the block
+               solved again unscaled, as (A^J)^+ r_J requires.  A selected row
+               has a positive weight, hence a positive norm. */
             extract_rows(rp, ci, av, nj, J, srp, sci, sav);
             double fro2 = 0.0;
             for (int64_t p = 0; p < nj; ++p) {
                 fro2 += rn2[J[p]];
                 rJ[p] = r[J[p]];
             }
-            steps_j = orc_lsqr(nj, n, srp, sci, sav, rJ, o->inner_tol, sqrt(fro2),
-                               o->inner_max, d);
+            int fit = 0;
+            if (nj <= n) {
+                for (int64_t p = 0; p < nj; ++p) {
+                    const double dr = 1.0 / sqrt(rn2[J[p]]);
+                    for (int64_t e = srp[p]; e < srp[p + 1]; ++e) bsc[e] = sav[e] * dr;
+                    rJ[p] *= dr;
+                }
+                steps_j = orc_lsqr_fit(nj, n, srp, sci, bsc, rJ, o->inner_tol,
+                                       sqrt((double)nj), o->inner_max, d, &fit);
+                if (fit == 0)
+                    for (int64_t p = 0; p < nj; ++p) rJ[p] = r[J[p]];
+            }
+            if (nj > n || fit == 0)
+                steps_j += orc_lsqr(nj, n, srp, sci, sav, rJ, o->inner_tol, sqrt(fro2),
+                                    o->inner_max, d);
             for (int64_t j = 0; j < n; ++j) x[j] += d[j];
         }
         st->inner_u += steps_u;

@@ -34,7 +34,7 @@ struct rgdbek_s {
     double *sav, *scv;
     double *dots, *dots2;
     float *vv32, *uu32;
-    double *vvs, *dsc, *yh;
+    double *vvs, *dsc, *yh, *uus, *dsr;
     double *pd;
     long long *pi;
     Ctrl *ctrl;
@@ -112,6 +112,8 @@ void carve(rgdbek_s *h, Layout &L) {
     h->vvs = L.take<double>(mx);
     h->dsc = L.take<double>(mx);
     h->yh = L.take<double>(mx);
+    h->uus = L.take<double>(mx);
+    h->dsr = L.take<double>(mx);
     h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
     h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
     h->ctrl = L.take<Ctrl>(1);
@@ -216,6 +218,8 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.vvs = h->vvs;
     P.dsc = h->dsc;
     P.yh = h->yh;
+    P.uus = h->uus;
+    P.dsr = h->dsr;
     P.inner_max = h->opt.inner_max;
     P.stop_rule = h->opt.stop_rule;
     P.selection = h->opt.selection;

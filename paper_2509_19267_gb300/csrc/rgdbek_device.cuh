@@ -36,6 +36,8 @@ enum DSlot {
     D_EMAX_R,     // max row weight
     D_ZZ,         // ||z||^2
     D_TT,         // ||t||^2
+    D_FRO_S,      // the block's squared Frobenius norm with unit lines (their count)
+    D_EXTRA_S,    // ||D c||^2 of the line-scaled right-hand side (sum of the weights)
     D_NSLOTS
 };
 enum ISlot {

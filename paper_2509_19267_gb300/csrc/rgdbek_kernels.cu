@@ -31,12 +31,15 @@ struct LsqrState {
     double inv_a, ab, wcoef;     // coefficients of the next rows phase
     double inv_b, ba, phi_rho;   // coefficients of the next cols phase
     int mv, done;
+    int fit;                     // at the end: 1 = the residual met the tolerance (a
+                                 // consistent block), 2 = step cap, 0 = otherwise
 };
 
 // Scalars of the outer iteration, also computed by thread 0 only.
 struct OuterState {
     double bb, tt, zz, atb2, rel, nrm, emax_c, emax_r;
     double beta1, alpha1, fro2, inv_beta1;
+    double beta1s, fro2s;        // row step: the same for the row-scaled block
     int verdict;                 // status to finish with, or kStatusRunning to go on
 };
 
@@ -370,7 +373,8 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot, int 
 template <bool f32>
 __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
                                         const double *c0, const float *c0_32, double *y_g,
-                                        double *xt, const double *csc, bool v_given,
+                                        double *xt, const double *csc, const double *rsc,
+                                        bool v_given,
                                         double alpha1, double beta1, double fro2,
                                         unsigned char *dsmem, long long dsmem_bytes,
                                         SolveSmem &S) {
@@ -385,9 +389,12 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
     double *wown = vown ? A.take<double>(ncl) : nullptr;
     double *yown = wown ? A.take<double>(ncl) : nullptr;
     double *dc = yown ? A.take<double>(ncl) : nullptr;
-    // column scaling D of the v-space (column step): its slice
+    // column scaling D of the v-space (column step), row scaling of the
+    // u-space (row step): their slices
     double *sown = (dc && csc) ? A.take<double>(ncl) : nullptr;
-    const bool st_smem = dc != nullptr && (sown != nullptr || csc == nullptr);
+    double *rown = (dc && rsc) ? A.take<double>(nrl) : nullptr;
+    const bool st_smem = dc != nullptr && (sown != nullptr || csc == nullptr) &&
+                         (rown != nullptr || rsc == nullptr);
     if (!st_smem) {
         A = SmemArena{dsmem, dsmem_bytes, 0};
         uold = nullptr;
@@ -398,7 +405,10 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         dc = P.dots2 + CC.lo;
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = 0.0;
     } else {
-        for (int i = threadIdx.x; i < nrl; i += blockDim.x) uold[i] = c0[RC.lo + i];
+        for (int i = threadIdx.x; i < nrl; i += blockDim.x) {
+            uold[i] = c0[RC.lo + i];
+            if (rown) rown[i] = rsc[RC.lo + i];
+        }
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
             vown[i] = v_given ? P.vv[CC.lo + i] : 0.0;
             yown[i] = 0.0;
@@ -406,6 +416,9 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         }
     }
     const double *dloc = csc ? (sown ? sown : csc + CC.lo) : nullptr;
+    const double *rloc = rsc ? (rown ? rown : rsc + RC.lo) : nullptr;
+    // the cols phase gathers D u~ when the u-space is scaled
+    const double *usrc = rsc ? P.uus : P.uu;
     // the rows phase gathers D v~ when the v-space is scaled
     const double *vsrc = csc ? P.vvs : P.vv;
     const CtaSide R = cache_side<f32>(Rs, A, S.bs, trank(P), tsize(P));
@@ -413,12 +426,13 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
     if (threadIdx.x == 0) {
         L.inv_b = 1.0 / beta1;
         L.done = 0;
+        L.fit = 0;
     }
     __syncthreads();
 
     if (!v_given) {
         // v~_1 = B^T c0 / beta1 (warp 0 has no scalars to update in this phase)
-        cta_dots<f32>(C, c0, c0_32, dc);
+        cta_dots<f32>(C, rsc ? P.uus : c0, c0_32, dc);
         __syncthreads();
         double acc = 0.0;
         for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
@@ -469,9 +483,11 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 L.wcoef = sn * an * L.irho;   // theta / rho
                 const double rnorm = L.phibar;
                 const double arnorm = L.phibar * an * fabs(cs);
-                L.done = arnorm <= P.inner_tol * L.fro * rnorm ||
-                         rnorm <= P.inner_tol * L.beta1 || an == 0.0 || bn == 0.0 ||
-                         it - 1 >= P.inner_max;
+                const bool resid = rnorm <= P.inner_tol * L.beta1 || bn == 0.0;
+                const bool other = arnorm <= P.inner_tol * L.fro * rnorm || an == 0.0;
+                const bool cap = it - 1 >= P.inner_max;
+                L.done = resid || other || cap;
+                L.fit = resid ? 1 : (other ? 0 : (cap ? 2 : 0));
                 L.alpha = an;
                 L.inv_a = ian;
                 L.ab = an * L.inv_b;           // alpha / beta
@@ -488,9 +504,11 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
             const double *uo = st_smem ? uold : (first ? c0 : P.uu) + RC.lo;
             double acc = 0.0;
             for (int li = threadIdx.x; li < nrl; li += blockDim.x) {
-                const double u = dr[li] * inv_a - ab * uo[li];
+                const double rl = rloc ? rloc[li] : 1.0;
+                const double u = (rloc ? dr[li] * rl : dr[li]) * inv_a - ab * uo[li];
                 P.uu[RC.lo + li] = u;
-                if (f32) P.uu32[RC.lo + li] = (float)u;
+                if (rloc) P.uus[RC.lo + li] = u * rl;
+                if (f32) P.uu32[RC.lo + li] = (float)(rloc ? u * rl : u);
                 if (st_smem) uold[li] = u;
                 acc = fma(u, u, acc);
             }
@@ -500,7 +518,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
 
         // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
-        cta_dots<f32>(C, P.uu, P.uu32, dc);
+        cta_dots<f32>(C, usrc, P.uu32, dc);
         if (threadIdx.x < 32) {
             const double uu = warp0_collect(P.pd, D_UU, tsize(P));
             if (threadIdx.x == 0) {
@@ -687,16 +705,16 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 RGD_SYNC(0, 0, 0);
             }
             phase_compact_count(P, P.n, P.cn2, P.g, P.epsc, bs);
-            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
+            RGD_SYNC(DS(D_FRO_S) | DS(D_EXTRA_S), 0, 0);
             if (threadIdx.x == 0) {
                 // LSQR start on B = A_U D (columns scaled to unit norm, D =
                 // diag(1/||A_j||)) with c = z_k: beta1 = ||z_k||, alpha1 =
                 // ||B^T z_k|| / beta1 = sqrt(sum of the selected eps^z) / beta1,
                 // ||B||_F^2 = |U|
-                O.fro2 = S.red_d[D_FRO];
+                O.fro2 = S.red_d[D_FRO_S];
                 O.beta1 = sqrt(O.zz);
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
-                O.alpha1 = sqrt(S.red_d[D_EXTRA]) * O.inv_beta1;
+                O.alpha1 = sqrt(S.red_d[D_EXTRA_S]) * O.inv_beta1;
             }
             nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
@@ -724,7 +742,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
                 const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, P.dsc, true, O.alpha1, O.beta1,
+                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, P.dsc, nullptr, true, O.alpha1, O.beta1,
                                   O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
@@ -757,22 +775,39 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
                 RGD_SYNC(0, 0, 0);
             }
-            phase_compact_count(P, P.m, P.rn2, P.r, nullptr, bs);
-            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA), 0, 0);
+            phase_compact_count(P, P.m, P.rn2, P.r, P.epsr, bs);
+            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA) | DS(D_FRO_S) | DS(D_EXTRA_S), 0, 0);
             if (threadIdx.x == 0) {
-                // LSQR start on A^J with c = r_J: beta1 = ||r_J||
+                // LSQR start on A^J with c = r_J: beta1 = ||r_J||; on D A^J
+                // (unit rows) with c = D r_J: beta1 = sqrt(sum of the weights)
                 O.fro2 = S.red_d[D_FRO];
                 O.beta1 = sqrt(S.red_d[D_EXTRA]);
                 O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
+                O.fro2s = S.red_d[D_FRO_S];
+                O.beta1s = sqrt(S.red_d[D_EXTRA_S]);
             }
             nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
             rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
+            // |J| <= n: first on D A^J (rows scaled to unit norm, D =
+            // diag(1/||A^(i)||)) with c = D r_J, which has the same minimum-norm
+            // solution whenever the block system is consistent
+            const bool rscale = nJ <= P.n;
             for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
                 const int i = P.jlist[p];
-                P.uu[p] = P.r[i];  // u~_1 = r_J
-                if (F32) P.uu32[p] = (float)P.r[i];
+                const double ri = P.r[i];
+                if (rscale) {
+                    const double d = rsqrt(P.rn2[i]);  // selected: ||A^(i)|| > 0
+                    const double u1 = ri * d;          // u~_1 = D r_J
+                    P.dsr[p] = d;
+                    P.uu[p] = u1;
+                    P.uus[p] = u1 * d;
+                    if (F32) P.uu32[p] = (float)(u1 * d);
+                } else {
+                    P.uu[p] = ri;  // u~_1 = r_J
+                    if (F32) P.uu32[p] = (float)ri;
+                }
                 if (rec_j) P.tr_lists[tr_off + nU + p] = i;
             }
             // A^J: the entries of every column of A that lie in J's rows
@@ -785,9 +820,32 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 const SideC rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
                 const SideC cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
                                  pick_lanes_fp64(nnzJ, P.n)};
-                stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, nullptr, false, 0.0, O.beta1, O.fro2,
-                                  dsmem, P.dsmem_bytes, S);
-                if (stepsJ < 0) return;
+                int fit = 0;
+                if (rscale) {
+                    stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, nullptr,
+                                           P.dsr, false, 0.0, O.beta1s, O.fro2s, dsmem,
+                                           P.dsmem_bytes, S);
+                    if (stepsJ < 0) return;
+                    fit = S.lsqr.fit;
+                }
+                if (!rscale || fit == 0) {
+                    if (rscale) {
+                        // found inconsistent: (A^J)^+ r_J needs the unscaled block;
+                        // the scaled attempt's x + y is undone first
+                        for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
+                            const double ri = P.r[P.jlist[p]];
+                            P.uu[p] = ri;
+                            if (F32) P.uu32[p] = (float)ri;
+                        }
+                        for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.xt[j] = P.x[j];
+                        RGD_SYNC(0, 0, 0);
+                    }
+                    const int s2 = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt,
+                                                 nullptr, nullptr, false, 0.0, O.beta1, O.fro2,
+                                                 dsmem, P.dsmem_bytes, S);
+                    if (s2 < 0) return;
+                    stepsJ += s2;
+                }
                 mark(S, PH_ROW_LSQR);
             }
         }

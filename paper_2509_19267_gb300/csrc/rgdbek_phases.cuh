@@ -71,6 +71,7 @@ struct Params {
     float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
     double *vvs, *dsc;      // column step: D v~ and D = 1/||A_j|| per column of U
     double *yh;             // column step: y^ of the scaled block (global fallback)
+    double *uus, *dsr;      // row step: D u~ and D = 1/||A^(i)|| per row of J
     int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
@@ -396,37 +397,44 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 
 // Count of marked indices in the chunk, and over them the sums of norm2 (the
 // block's squared Frobenius norm) and of vec^2 (for the LSQR start).
-// With unit (the column step, whose inner solve runs on A_U with unit
-// columns): fro counts the selected lines and ext sums their weights eps,
-// i.e. the squared Frobenius norm and ||B^T c||^2 of the column-scaled block.
+// Partials over the selected lines: their count, the sums of norm2 (squared
+// Frobenius norm of the block) and of vec^2 (squared norm of the right-hand
+// side, or of B^T c in the column step), and with unit (the weights eps =
+// vec^2 / norm2) the same two sums for the block with its lines scaled to
+// unit norm: the line count and the sum of the weights.
 __device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
                                                     const double *norm2, const double *vec,
                                                     const double *unit, BlockScratch &bs) {
     const Chunk C(len, trank(P), tsize(P));
     long long cnt = 0;
-    double fro = 0.0, ext = 0.0;
+    double fro = 0.0, ext = 0.0, frs = 0.0, exs = 0.0;
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
         const bool f = j < C.hi && P.flag[j];
         cnt += __popc(__ballot_sync(kFull, f)) * ((threadIdx.x & 31) == 0);
         if (f) {
+            fro += __ldg(norm2 + j);
+            const double v = vec[j];
+            ext = fma(v, v, ext);
             if (unit) {
-                fro += 1.0;
-                ext += unit[j];
-            } else {
-                fro += __ldg(norm2 + j);
-                const double v = vec[j];
-                ext = fma(v, v, ext);
+                frs += 1.0;
+                exs += unit[j];
             }
         }
     }
     cnt = block_sum(cnt, bs);
     fro = block_sum(fro, bs);
     ext = block_sum(ext, bs);
+    if (unit) {
+        frs = block_sum(frs, bs);
+        exs = block_sum(exs, bs);
+    }
     if (threadIdx.x == 0) {
         P.pi[I_CNT * tsize(P) + trank(P)] = cnt;
         P.pd[D_FRO * tsize(P) + trank(P)] = fro;
         P.pd[D_EXTRA * tsize(P) + trank(P)] = ext;
+        P.pd[D_FRO_S * tsize(P) + trank(P)] = frs;
+        P.pd[D_EXTRA_S * tsize(P) + trank(P)] = exs;
     }
 }
 
