@@ -76,7 +76,9 @@ typedef struct {
     double time_budget_s;  /* wall-clock cap of one solve on the device, 0 = none   */
     uint64_t system_id;    /* second word of the Philox key                         */
     int blocks_per_sm;     /* persistent grid: CTAs per SM, 0 = largest that fits   */
-    int threads_per_block; /* solve kernels: 0 = 512; a multiple of 32 in [64, 512] */
+    int threads_per_block; /* solve kernels: 0 = automatic (512, or 1024 when
+                              max(m, n) exceeds 2048 per CTA); else a multiple
+                              of 32 in [64, 1024]                                   */
     int precision;         /* RGDBEK_PRECISION_*                                    */
     int batch_team;        /* CTAs per system in rgdbek_solve_batched (read from the
                               first handle): 0 = the size rgdbek_tune_batched found,

@@ -135,14 +135,15 @@ int check_options(const rgdbek_options &o) {
     if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
-         o.threads_per_block > kSolveThreads))
+         o.threads_per_block > kSolveMaxThreads))
         return RGDBEK_ERR_INVALID_ARG;
     return RGDBEK_OK;
 }
 
 // launch shape of the persistent kernels for the handle's options
 int configure_launch(rgdbek_s *h) {
-    const int block = h->opt.threads_per_block ? h->opt.threads_per_block : kSolveThreads;
+    const int block = h->opt.threads_per_block ? h->opt.threads_per_block
+                                               : auto_solve_block(h->m, h->n, h->num_sms);
     int fit = solve_blocks_per_sm(block);
     int fit_s = sample_blocks_per_sm(block);
     if (fit < 1 || fit_s < 1) return RGDBEK_ERR_CUDA;
@@ -368,16 +369,27 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
                 const double *tol, long long max_iter, uint64_t seed, rgdbek_stats *st, int team,
                 float *ms) {
     rgdbek_s *h0 = hs[0];
-    if (!h0 || team < 1 || team > h0->grid) return RGDBEK_ERR_INVALID_ARG;
+    if (!h0 || team < 1) return RGDBEK_ERR_INVALID_ARG;
     for (int i = 0; i < nsys; ++i) {
         if (!hs[i] || !b[i] || !x[i] || !(tol[i] >= 0.0) || max_iter < 0) return RGDBEK_ERR_INVALID_ARG;
-        if (hs[i]->device != h0->device || hs[i]->block != h0->block ||
-            hs[i]->opt.precision != h0->opt.precision)
+        if (hs[i]->device != h0->device || hs[i]->opt.precision != h0->opt.precision)
             return RGDBEK_ERR_INVALID_ARG;
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return RGDBEK_ERR_INVALID_ARG;  // one workspace per system
     }
-    const int nteams = h0->grid / team;
+    // block: hs[0]'s option, else by the largest system's share per CTA; the
+    // grid: as many CTAs of that block as are co-resident
+    int block = h0->opt.threads_per_block;
+    if (block == 0) {
+        long long vmax = 0;
+        for (int i = 0; i < nsys; ++i) vmax = std::max(vmax, std::max(hs[i]->m, hs[i]->n));
+        block = auto_solve_block(vmax, 0, team);
+    }
+    const int fit = solve_blocks_per_sm(block);
+    if (fit < 1) return RGDBEK_ERR_CUDA;
+    const long long gmax = std::min((long long)kMaxGrid, (long long)fit * h0->num_sms);
+    if (team > gmax) return RGDBEK_ERR_INVALID_ARG;
+    const int nteams = (int)(gmax / team);
     std::vector<Params> sys(nsys);
     for (int i = 0; i < nsys; ++i) {
         Params P = make_params(hs[i]);
@@ -427,7 +439,7 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
     if (e == cudaSuccess && ms) e = cudaEventRecord(ev0, s);
     if (e == cudaSuccess)
         e = launch_solve_batched(sys_dev, plan_dev, stride, team, nteams,
-                                 h0->opt.precision == RGDBEK_PRECISION_FP32_INNER, h0->block, s);
+                                 h0->opt.precision == RGDBEK_PRECISION_FP32_INNER, block, s);
     if (e == cudaSuccess && ms) e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess) e = launch_gather_ctrls(sys_dev, nsys, ctrl_dev, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, ctrl_dev, ctrl_bytes, cudaMemcpyDeviceToHost, s);

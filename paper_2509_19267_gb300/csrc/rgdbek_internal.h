@@ -10,10 +10,19 @@
 namespace rgd {
 
 constexpr int kSolveMaxThreads = 1024;  // launch bound of the component kernels and the sampler
-// launch bound and default block of the solve kernels: 512 threads leave 128
-// registers a thread (no spills); measured faster than 1024 threads with 64
-// registers and than 256 threads
-constexpr int kSolveThreads = 512;
+// The solve kernels come in two shapes: 512 threads (128 registers a thread,
+// no spills; fastest while each CTA's share of the vectors fits its shared
+// memory) and 1024 threads (64 registers; faster on large vectors, where the
+// element-wise loops of the inner solves run from global memory).  The
+// automatic choice takes 1024 threads when max(m, n) exceeds
+// kSolveVecPerCta elements per CTA.
+constexpr int kSolveSmallThreads = 512;
+constexpr long long kSolveVecPerCta = 2048;
+inline int auto_solve_block(long long m, long long n, int ctas) {
+    const long long v = m > n ? m : n;
+    return v > kSolveVecPerCta * (long long)(ctas > 0 ? ctas : 1) ? kSolveMaxThreads
+                                                                   : kSolveSmallThreads;
+}
 // dynamic shared memory of a solve CTA: its chunk of the inner-solve block
 constexpr int kSolveDsmemBytes = 96 * 1024;
 
@@ -26,6 +35,11 @@ cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s);
 // system of team t (-1 ends a team's list)
 cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int stride, int team,
                                  int nteams, bool fp32, int block, cudaStream_t s);
+// the solve kernels of one shape (small: the 512-thread launch bound)
+const void *solve_kernel_fn(bool fp32, bool small);
+const void *batched_kernel_fn(bool fp32, bool small);
+const void *solve_kernel_fn_small(bool fp32);      // rgdbek_solve512.cu
+const void *batched_kernel_fn_small(bool fp32);
 // control blocks of a batch: reset before the launch, gathered after it
 cudaError_t launch_reset_ctrls(const Params *sys_dev, int nsys, cudaStream_t s);
 cudaError_t launch_gather_ctrls(const Params *sys_dev, int nsys, Ctrl *out, cudaStream_t s);
