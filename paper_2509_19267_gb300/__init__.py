@@ -6,6 +6,23 @@ randomized column and row blocks drawn from residual-derived probabilities
 this module only marshals arguments (torch tensors for device memory and
 streams) to the functions declared in ``include/rgdbek.h``, under the same
 names.  There is no CPU fallback: importing fails if the library is missing.
+
+Entry points (each a function of the same name as in the header):
+  rgdbek_create / rgdbek_destroy / rgdbek_set_options / rgdbek_get_info
+  rgdbek_solve, rgdbek_solve_host      one solve (device or host buffers)
+  rgdbek_solve_batched                 many systems in one persistent launch
+  rgdbek_tune, rgdbek_tune_batched     measured choice of kernel shape / team
+  rgdbek_backward                      implicit adjoint (dL/db, dL/dA)
+  rgdbek_spmv, rgdbek_spmv_t, rgdbek_weights, rgdbek_sample,
+  rgdbek_sample_noalloc, rgdbek_set_trace, rgdbek_get_norms, rgdbek_get_csc
+and two conveniences built on them: ``Solver`` (owns a handle) and
+``rgdbek_lstsq`` (the solve as a torch.autograd.Function).
+
+Example:
+    s = Solver(m, n, row_ptr, col_idx, vals, eta_col=0.1, eta_row=0.1,
+               stop_rule=STOP_NORMAL)
+    res = s.solve(b_cuda, tol=1e-8)      # res.x (cuda tensor), res.stats
+    gb, gv, status, st = s.backward(b_cuda, res.x, grad_x)
 """
 from __future__ import annotations
 
@@ -90,7 +107,10 @@ SIGNATURES = [
     ("rgdbek_solve_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
                                     ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_tune_batched", _int, [_int, _ptr, _ptr, _ptr, _ptr, _i64, _u64,
-                                    ctypes.POINTER(_int), ctypes.POINTER(_dbl)]),
+                                    ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                    ctypes.POINTER(_dbl)]),
+    ("rgdbek_tune", _int, [_ptr, _ptr, _ptr, _i64, _u64, ctypes.POINTER(_int),
+                           ctypes.POINTER(_dbl)]),
     ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
                                ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
@@ -247,17 +267,31 @@ BATCH_TEAM_CANDIDATES = (1, 2, 4, 8, 19, 38, 76, 152)
 
 
 def rgdbek_tune_batched(hs, bs, xs, tols, probe_iters: int = 3, seed: int = 0):
-    """Times the batch with each team size; returns (best_team, {team: ms})."""
+    """Times the batch with each team size, then each kernel shape at the best
+    one; returns (best_team, best_block (0 = automatic), {team: ms},
+    {block: ms})."""
     n = len(hs)
     H = (_ptr * n)(*hs)
     B = (_ptr * n)(*[_dptr(b) for b in bs])
     X = (_ptr * n)(*[_dptr(x) for x in xs])
     T = (_dbl * n)(*tols)
-    team = _int(0)
-    ms = (_dbl * len(BATCH_TEAM_CANDIDATES))()
-    _check(_lib.rgdbek_tune_batched(n, H, B, X, T, probe_iters, seed, ctypes.byref(team), ms),
-           "rgdbek_tune_batched")
-    return team.value, {c: ms[i] for i, c in enumerate(BATCH_TEAM_CANDIDATES) if ms[i] >= 0}
+    team, block = _int(0), _int(0)
+    nc = len(BATCH_TEAM_CANDIDATES)
+    ms = (_dbl * (nc + 2))(*([-1.0] * (nc + 2)))
+    _check(_lib.rgdbek_tune_batched(n, H, B, X, T, probe_iters, seed, ctypes.byref(team),
+                                    ctypes.byref(block), ms), "rgdbek_tune_batched")
+    return (team.value, block.value,
+            {c: ms[i] for i, c in enumerate(BATCH_TEAM_CANDIDATES) if ms[i] >= 0},
+            {blk: ms[nc + i] for i, blk in enumerate((512, 1024)) if ms[nc + i] >= 0})
+
+
+def rgdbek_tune(h: int, b, x, probe_iters: int = 5, seed: int = 0):
+    """Times both solve-kernel shapes; sets the faster. Returns (block, {block: ms})."""
+    block = _int(0)
+    ms = (_dbl * 2)()
+    _check(_lib.rgdbek_tune(h, _dptr(b), _dptr(x), probe_iters, seed, ctypes.byref(block), ms),
+           "rgdbek_tune")
+    return block.value, {512: ms[0], 1024: ms[1]}
 
 
 ADJ_RANK_TERM = 1
