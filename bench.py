@@ -516,7 +516,7 @@ def run_batched_deblur(args):
     bs = [torch.from_numpy(s.b).cuda() for s in S]
     xs = [torch.empty(s.n, dtype=torch.float64, device="cuda") for s in S]
     tols = [1e-8] * len(S)
-    team, tune_ms = rg.rgdbek_tune_batched(H, bs, xs, tols, probe_iters=2)
+    team, tuned_block, tune_ms, shape_ms = rg.rgdbek_tune_batched(H, bs, xs, tols, probe_iters=2)
     for _ in range(args.warmup):
         rg.rgdbek_solve_batched(H, bs, xs, tols, budget, seed=0)
     clocks = ClockSampler(0)
@@ -549,6 +549,8 @@ def run_batched_deblur(args):
                        "teams": hs[0].info().grid // team,
                        "l2": "inputs larger than L2 (25 GB of CSR)"},
             "tuner_ms": {str(k): v for k, v in tune_ms.items()},
+            "tuner_shape_ms": {str(k): v for k, v in shape_ms.items()},
+            "block": tuned_block or "automatic",
             "sequential": {"value": seq_value, "unit": "system-iters/s",
                            "ms": ms_seq[0], "what": "rgdbek_solve per system, whole GPU each"},
             "speedup_vs_sequential": value / seq_value,

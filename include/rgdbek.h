@@ -200,16 +200,29 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
 
 /* Autotuner of the batched solve: runs the batch for probe_iters outer
  * iterations with each candidate team size (1, 2, 4, 8, 19, 38, 76, 152 CTAs
- * per system, those not above the grid), times each launch with CUDA
- * events, and keeps the fastest in hs[0] for later rgdbek_solve_batched
- * calls with batch_team = 0.  *team_out receives it; ms_out (host
- * double[RGDBEK_BATCH_TEAM_CANDIDATES], may be NULL) the time of each
- * candidate (-1 where skipped).  The x buffers are overwritten by the probe
- * solves.  Returns OK or the first error. */
+ * per system, those not above the grid) and the automatic block, then, at
+ * the fastest team size and unless hs[0] fixes threads_per_block, with each
+ * shape of the solve kernel (512 and 1024 threads).  Each launch is timed
+ * with CUDA events; the fastest team size and block are kept in hs[0] for
+ * later rgdbek_solve_batched calls with batch_team = 0 (and
+ * threads_per_block = 0).  *team_out and *block_out (0 = automatic; may be
+ * NULL) receive them; ms_out (host double[RGDBEK_BATCH_TEAM_CANDIDATES + 2],
+ * may be NULL) the time of each team size and then of the 512- and
+ * 1024-thread shapes (-1 where skipped).  The x buffers are overwritten by
+ * the probe solves.  Returns OK or the first error. */
 #define RGDBEK_BATCH_TEAM_CANDIDATES 8
 int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                         const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
-                        double *ms_out);
+                        int *block_out, double *ms_out);
+
+/* Autotuner of the single solve's kernel shape: runs probe_iters outer
+ * iterations from x0 = 0 on b (device, m) into x (device, n, overwritten)
+ * with 512 and with 1024 threads per CTA, times each with CUDA events, and
+ * sets the handle's threads_per_block to the faster.  *block_out receives it
+ * and ms_out (host double[2], may be NULL) the two times.  Returns OK or the
+ * first error (the options are then left as they were). */
+int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uint64_t seed,
+                int *block_out, double *ms_out);
 
 /* Implicit adjoint of the solve (reverse-mode gradient).  The method
  * converges to x = A^+ b, the minimum-norm least-squares solution (the

@@ -46,7 +46,8 @@ struct rgdbek_s {
     double *adj_ax, *adj_w, *adj_v, *adj_u, *adj_ag, *adj_q;
     // launch shape
     int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
-    int tuned_team = 0;  // team size found by rgdbek_tune_batched (0 = none yet)
+    int tuned_team = 0;   // team size found by rgdbek_tune_batched (0 = none yet)
+    int tuned_block = 0;  // block of the batched solve found by it (0 = automatic)
     // trace
     long long *tr_counts = nullptr;
     long long tr_count_cap = 0;
@@ -367,7 +368,7 @@ void plan_batch(int nsys, rgdbek_t *hs, int nteams, std::vector<int> &plan, int 
 // NOT_CONVERGED if any system hit its cap.
 int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                 const double *tol, long long max_iter, uint64_t seed, rgdbek_stats *st, int team,
-                float *ms) {
+                float *ms, int block_req = 0) {
     rgdbek_s *h0 = hs[0];
     if (!h0 || team < 1) return RGDBEK_ERR_INVALID_ARG;
     for (int i = 0; i < nsys; ++i) {
@@ -379,7 +380,8 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
     }
     // block: hs[0]'s option, else by the largest system's share per CTA; the
     // grid: as many CTAs of that block as are co-resident
-    int block = h0->opt.threads_per_block;
+    int block = block_req ? block_req : h0->opt.threads_per_block;
+    if (block == 0 && h0->tuned_block > 0) block = h0->tuned_block;
     if (block == 0) {
         long long vmax = 0;
         for (int i = 0; i < nsys; ++i) vmax = std::max(vmax, std::max(hs[i]->m, hs[i]->n));
@@ -683,12 +685,15 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
 
 int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                         const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
-                        double *ms_out) {
+                        int *block_out, double *ms_out) {
     if (nsys < 1 || !hs || !b || !x || !tol || probe_iters < 1 || !team_out || !hs[0])
         return RGDBEK_ERR_INVALID_ARG;
-    const int grid = hs[0]->grid;
+    rgdbek_s *h0 = hs[0];
+    const int grid = h0->grid;
+    h0->tuned_block = 0;
     int best = 0;
     float best_ms = 0.f;
+    // team sizes, with the automatic block
     for (int c = 0; c < kNumTeamCandidates; ++c) {
         const int T = kTeamCandidates[c];
         if (ms_out) ms_out[c] = -1.0;
@@ -703,9 +708,80 @@ int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *
         }
     }
     if (best == 0) return RGDBEK_ERR_INVALID_ARG;
-    hs[0]->tuned_team = best;
+    // then the solve kernel's other shape at that team size
+    int best_block = 0;
+    if (h0->opt.threads_per_block == 0) {
+        for (int blk : {kSolveSmallThreads, kSolveMaxThreads}) {
+            float ms = 0.f;
+            const int s0 =
+                run_batched(nsys, hs, b, x, tol, probe_iters, seed, nullptr, best, &ms, blk);
+            if (s0 < 0) return s0;
+            if (ms_out) ms_out[kNumTeamCandidates + (blk == kSolveMaxThreads ? 1 : 0)] = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_block = blk;
+            }
+        }
+    }
+    h0->tuned_team = best;
+    h0->tuned_block = best_block;
     *team_out = best;
+    if (block_out) *block_out = best_block;
     return RGDBEK_OK;
+}
+
+int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uint64_t seed,
+                int *block_out, double *ms_out) {
+    if (!h || !b || !x || probe_iters < 1) return RGDBEK_ERR_INVALID_ARG;
+    const rgdbek_options saved = h->opt;
+    int best = 0;
+    float best_ms = 0.f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int c = 0; e == cudaSuccess && c < 2; ++c) {
+        const int blk = c == 0 ? kSolveSmallThreads : kSolveMaxThreads;
+        h->opt.threads_per_block = blk;
+        int st = configure_launch(h);
+        if (st != RGDBEK_OK) {
+            h->opt = saved;
+            configure_launch(h);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        float ms = 0.f;
+        // the probe solves run from x0 = 0 with a zero tolerance: probe_iters
+        // outer iterations each
+        e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) st = run_solve(h, false, b, x, 0.0, probe_iters, seed, nullptr);
+        if (e == cudaSuccess && st < 0 && st != RGDBEK_ERR_NONFINITE) {
+            h->opt = saved;
+            configure_launch(h);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) ms_out[c] = ms;
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+            best = blk;
+            best_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->opt = saved;
+    if (e != cudaSuccess) {
+        configure_launch(h);
+        return cuda_status(e);
+    }
+    h->opt.threads_per_block = best;
+    const int st = configure_launch(h);
+    if (block_out) *block_out = best;
+    return st;
 }
 
 int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *grad_x,

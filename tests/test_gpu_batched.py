@@ -122,8 +122,9 @@ def test_tuner_and_argument_errors(rg, systems):
     H = [h.handle for h in hs]
     bs = [G.dev(s.b) for s in S]
     xs = [torch.empty(s.n, dtype=torch.float64, device="cuda") for s in S]
-    team, ms = rg.rgdbek_tune_batched(H, bs, xs, [1e-10] * len(S), probe_iters=2)
+    team, block, ms, shape_ms = rg.rgdbek_tune_batched(H, bs, xs, [1e-10] * len(S), probe_iters=2)
     assert team in rg.BATCH_TEAM_CANDIDATES and team in ms and len(ms) >= 4
+    assert block in (0, 512, 1024) and set(shape_ms) == {512, 1024}
     status, st = rg.rgdbek_solve_batched(H, bs, xs, [1e-12] * len(S), 200000, seed=5)
     assert status == rg.OK
     for i in range(len(S)):
@@ -157,3 +158,22 @@ def test_blur_batch_runs_to_its_budget(rg):
         assert st[i].rel_res < 1.0
     for h in hs:
         h.close()
+
+
+def test_single_solve_shape_tuner(rg, systems):
+    """rgdbek_tune times both solve-kernel shapes and keeps the faster; the
+    solve after it still reaches the oracle's solution."""
+    import torch
+    S, refs = systems
+    s0 = S[0]
+    h = rg.Solver(s0.m, s0.n, s0.row_ptr, s0.col_idx, s0.vals, eta_col=0.2, eta_row=0.2,
+                  stop_rule=rg.STOP_NORMAL)
+    b = G.dev(s0.b)
+    x = torch.empty(s0.n, dtype=torch.float64, device="cuda")
+    block, ms = rg.rgdbek_tune(h.handle, b, x, probe_iters=3)
+    assert block in (512, 1024) and ms[512] > 0 and ms[1024] > 0
+    assert h.info().threads_per_block == block
+    res = h.solve(b, tol=1e-12, max_iter=200000, seed=5)
+    assert res.stats.status == rg.OK
+    assert G.rel(G.host(res.x), refs[0]) <= 1e-8
+    h.close()
