@@ -177,3 +177,23 @@ def test_single_solve_shape_tuner(rg, systems):
     assert res.stats.status == rg.OK
     assert G.rel(G.host(res.x), refs[0]) <= 1e-8
     h.close()
+
+
+def test_batched_fp32_inner_matches_oracle(rg, systems):
+    """The FP32-inner instantiation of the batched kernel: full-column-rank
+    systems of the batch reach the FP64 oracle's solutions within 1e-8."""
+    import torch
+    S, refs = systems
+    pick = [0, 1, 3]                     # sparse least squares, full column rank
+    hs = [rg.Solver(S[i].m, S[i].n, S[i].row_ptr, S[i].col_idx, S[i].vals, eta_col=0.2,
+                    eta_row=0.2, stop_rule=rg.STOP_NORMAL, precision=rg.PRECISION_FP32_INNER,
+                    batch_team=8) for i in pick]
+    bs = [G.dev(S[i].b) for i in pick]
+    xs = [torch.empty(S[i].n, dtype=torch.float64, device="cuda") for i in pick]
+    status, st = rg.rgdbek_solve_batched([h.handle for h in hs], bs, xs, [1e-12] * len(pick),
+                                         200000, seed=5)
+    assert status == rg.OK
+    for k, i in enumerate(pick):
+        assert G.rel(G.host(xs[k]), refs[i]) <= 1e-8, i
+    for h in hs:
+        h.close()

@@ -398,3 +398,32 @@ def test_time_budget(rg):
     assert r.stats.status == rg.ERR_TIMEOUT
     assert 0 <= r.stats.iters < 100000
     s.close()
+
+
+def test_inconsistent_row_blocks_take_the_unscaled_solve(rg):
+    """Fat least squares with every row duplicated (rank 20 of 40 rows, b not
+    in the range): row blocks that hold both copies of a row are inconsistent,
+    so the row-scaled inner solve is rejected and the block is solved again
+    unscaled.  In lockstep the GPU makes the same decisions as the oracle
+    (equal LSQR step counts, which include both attempts), and both reach
+    pinv(A) b."""
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((20, 100))
+    D = np.repeat(B, 2, axis=0)
+    b = rng.standard_normal(40)
+    S = workloads.from_dense(D, b)
+    K = 10
+    st, counts, lists, x = _gpu_trace(rg, S, 0.5, seed=4, iters=K)
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.5, eta_row=0.5, stop_rule=2, tol=0.0,
+                                                inner_tol=1e-13, max_iter=K, seed=4),
+                       n=S.n, lock=lists, trace=True)
+    assert G.rel(x, ref.x) <= 1e-10
+    assert np.all(np.abs(ref.counts[:, 2:] - counts[:, 2:]) <= 1)
+    # some row blocks hold both copies of a row (with different residuals:
+    # an inconsistent block system)
+    assert any(len(set(j // 2 for j in J)) < len(J) for _, J in lists)
+    st, x, ref = _solve_both(rg, S, 1e-12, rg.STOP_NORMAL, 0.5, seed=4)
+    xs = np.linalg.pinv(D, rcond=1e-10) @ b
+    assert st.status == rg.OK
+    assert G.rel(x, xs) <= X_TOL
+    assert G.rel(x, ref.x) <= X_TOL
