@@ -120,7 +120,7 @@ typedef struct {
     int lanes_per_row;     /* lanes that share one CSR row in the A x products   */
     int lanes_per_col;     /* lanes that share one CSC column in A^T z products  */
     int num_sms;
-    int64_t device_bytes;  /* device memory held by the handle                   */
+    int64_t device_bytes;  /* device memory the handle uses (with its matrix)    */
 } rgdbek_info_t;
 
 /* Fills *opt with the defaults: eta_col = eta_row = 0.5 (the paper's
@@ -147,6 +147,16 @@ int rgdbek_create(rgdbek_t *h, int64_t m, int64_t n, int64_t nnz, const int64_t 
 
 /* Releases everything the handle owns (after synchronising its stream). */
 void rgdbek_destroy(rgdbek_t h);
+
+/* A new handle for the same matrix as `base`: it shares base's read-only
+ * device arrays (CSR, CSC, squared norms; nothing is copied or rebuilt) and
+ * owns its own workspace and control block, so that several right-hand
+ * sides of one matrix can be solved at once (rgdbek_solve_batched over the
+ * derived handles) with one copy of A in memory.  opt may be NULL (base's
+ * options); stream as in rgdbek_create.  The shared arrays live until the
+ * last handle using them is destroyed, in any order.  The current device
+ * must be base's.  Errors: INVALID_ARG, OOM, CUDA. */
+int rgdbek_create_like(rgdbek_t base, const rgdbek_options *opt, void *stream, rgdbek_t *out);
 
 /* Replaces the options (validated as in rgdbek_create). */
 int rgdbek_set_options(rgdbek_t h, const rgdbek_options *opt);

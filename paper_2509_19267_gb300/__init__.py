@@ -98,6 +98,8 @@ SIGNATURES = [
     ("rgdbek_create", _int, [ctypes.POINTER(_ptr), _i64, _i64, _i64, _ptr, _ptr, _ptr, _int,
                              ctypes.POINTER(rgdbek_options), _ptr]),
     ("rgdbek_destroy", None, [_ptr]),
+    ("rgdbek_create_like", _int, [_ptr, ctypes.POINTER(rgdbek_options), _ptr,
+                                  ctypes.POINTER(_ptr)]),
     ("rgdbek_set_options", _int, [_ptr, ctypes.POINTER(rgdbek_options)]),
     ("rgdbek_set_stream", _int, [_ptr, _ptr]),
     ("rgdbek_get_info", _int, [_ptr, ctypes.POINTER(rgdbek_info_t)]),
@@ -207,6 +209,14 @@ def rgdbek_create(m: int, n: int, row_ptr, col_idx, vals, options: rgdbek_option
                             ctypes.byref(options) if options is not None else None,
                             _stream_ptr(stream))
     _check(st, "rgdbek_create")
+    return h.value
+
+
+def rgdbek_create_like(base: int, options: rgdbek_options | None = None, stream=None) -> int:
+    """A handle sharing base's matrix arrays, with its own workspace."""
+    h = _ptr()
+    _check(_lib.rgdbek_create_like(base, ctypes.byref(options) if options is not None else None,
+                                   _stream_ptr(stream), ctypes.byref(h)), "rgdbek_create_like")
     return h.value
 
 
@@ -374,6 +384,21 @@ class Solver:
         self.m, self.n = m, n
         self.options = default_options(**options)
         self.handle = rgdbek_create(m, n, row_ptr, col_idx, vals, self.options, stream)
+
+    @classmethod
+    def like(cls, base: "Solver", stream=None, **options) -> "Solver":
+        """Another solver for base's matrix (shared on the device, own workspace)."""
+        s = cls.__new__(cls)
+        s.m, s.n = base.m, base.n
+        o = rgdbek_options()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(base.options), ctypes.sizeof(o))
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        s.options = o
+        s.handle = rgdbek_create_like(base.handle, o, stream)
+        return s
 
     def set_options(self, **options):
         for k, v in options.items():

@@ -2,6 +2,7 @@
 // option checks, device memory layout, and the launches of the persistent
 // solve kernel and of the component kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -12,8 +13,17 @@
 
 using namespace rgd;
 
+// The read-only matrix arrays (CSR, CSC, squared norms) of a handle, shared
+// by the handles made from it with rgdbek_create_like; freed with the last.
+struct MatrixStore {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    std::atomic<int> refs{1};
+};
+
 struct rgdbek_s {
     int device = 0, num_sms = 0;
+    MatrixStore *mat = nullptr;
     cudaStream_t stream = nullptr;
     rgdbek_options opt{};
     long long m = 0, n = 0, nnz = 0;
@@ -70,8 +80,9 @@ struct Layout {
     }
 };
 
-void carve(rgdbek_s *h, Layout &L) {
-    const long long m = h->m, n = h->n, nnz = h->nnz, mx = m > n ? m : n;
+// The matrix arrays, in their own allocation (shared by derived handles).
+void carve_matrix(rgdbek_s *h, Layout &L) {
+    const long long m = h->m, n = h->n, nnz = h->nnz;
     h->rp = L.take<long long>(m + 1);
     h->ci = L.take<int>(nnz);
     h->av = L.take<double>(nnz);
@@ -80,6 +91,11 @@ void carve(rgdbek_s *h, Layout &L) {
     h->cv = L.take<double>(nnz);
     h->rn2 = L.take<double>(m);
     h->cn2 = L.take<double>(n);
+}
+
+// The workspace of one handle.
+void carve(rgdbek_s *h, Layout &L) {
+    const long long m = h->m, n = h->n, nnz = h->nnz, mx = m > n ? m : n;
     // Work vectors indexed by rows or by columns are all max(m, n) long, so
     // that the same workspace serves the solves on A^T of rgdbek_backward.
     h->z = L.take<double>(mx);
@@ -468,6 +484,10 @@ void release(rgdbek_s *h) {
     if (!h) return;
     if (h->adj) cudaFree(h->adj);
     if (h->arena) cudaFree(h->arena);
+    if (h->mat && h->mat->refs.fetch_sub(1) == 1) {
+        if (h->mat->mem) cudaFree(h->mat->mem);
+        delete h->mat;
+    }
     if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
     delete h;
 }
@@ -532,14 +552,26 @@ int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_
     h->ipr = pick_lanes_int(nnz, m);
     h->ipc = pick_lanes_int(nnz, n);
 
+    h->mat = new (std::nothrow) MatrixStore();
+    if (!h->mat) {
+        release(h);
+        return RGDBEK_ERR_OOM;
+    }
+    Layout M;
+    carve_matrix(h, M);
+    h->mat->bytes = M.off;
     Layout L;
     carve(h, L);
     h->arena_bytes = L.off;
-    if ((e = cudaMalloc(&h->arena, h->arena_bytes)) != cudaSuccess ||
+    if ((e = cudaMalloc(&h->mat->mem, h->mat->bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&h->arena, h->arena_bytes)) != cudaSuccess ||
         (e = cudaMallocHost(&h->ctrl_host, sizeof(Ctrl))) != cudaSuccess) {
         release(h);
         return cuda_status(e);
     }
+    M = Layout();
+    M.base = static_cast<char *>(h->mat->mem);
+    carve_matrix(h, M);
     L = Layout();
     L.base = static_cast<char *>(h->arena);
     carve(h, L);
@@ -603,6 +635,68 @@ int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_
     return RGDBEK_OK;
 }
 
+int rgdbek_create_like(rgdbek_t base, const rgdbek_options *opt, void *stream, rgdbek_t *out) {
+    if (!out) return RGDBEK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!base || !base->mat) return RGDBEK_ERR_INVALID_ARG;
+    rgdbek_options o = base->opt;
+    if (opt) o = *opt;
+    int st = check_options(o);
+    if (st != RGDBEK_OK) return st;
+    rgdbek_s *h = new (std::nothrow) rgdbek_s();
+    if (!h) return RGDBEK_ERR_OOM;
+    h->device = base->device;
+    h->num_sms = base->num_sms;
+    h->m = base->m;
+    h->n = base->n;
+    h->nnz = base->nnz;
+    h->opt = o;
+    h->stream = (cudaStream_t)stream;
+    h->tpr = base->tpr;
+    h->tpc = base->tpc;
+    h->ipr = base->ipr;
+    h->ipc = base->ipc;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) {
+        delete h;
+        return RGDBEK_ERR_INVALID_ARG;  // the matrix lives on another device
+    }
+    if ((st = configure_launch(h)) != RGDBEK_OK) {
+        delete h;
+        return st;
+    }
+    // share the matrix (pointers into the base's matrix allocation)
+    h->mat = base->mat;
+    h->mat->refs.fetch_add(1);
+    h->rp = base->rp;
+    h->ci = base->ci;
+    h->av = base->av;
+    h->cp = base->cp;
+    h->ri = base->ri;
+    h->cv = base->cv;
+    h->rn2 = base->rn2;
+    h->cn2 = base->cn2;
+    Layout L;
+    carve(h, L);
+    h->arena_bytes = L.off;
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->arena, h->arena_bytes)) != cudaSuccess ||
+        (e = cudaMallocHost(&h->ctrl_host, sizeof(Ctrl))) != cudaSuccess) {
+        release(h);
+        return cuda_status(e);
+    }
+    L = Layout();
+    L.base = static_cast<char *>(h->arena);
+    carve(h, L);
+    // the base's set-up (CSC, norms) must be complete before this handle uses it
+    if ((e = cudaStreamSynchronize(base->stream)) != cudaSuccess) {
+        release(h);
+        return cuda_status(e);
+    }
+    *out = h;
+    return RGDBEK_OK;
+}
+
 void rgdbek_destroy(rgdbek_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
@@ -639,7 +733,7 @@ int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
     info->lanes_per_row = h->tpr;
     info->lanes_per_col = h->tpc;
     info->num_sms = h->num_sms;
-    info->device_bytes = (int64_t)h->arena_bytes;
+    info->device_bytes = (int64_t)(h->arena_bytes + (h->mat ? h->mat->bytes : 0));
     return RGDBEK_OK;
 }
 

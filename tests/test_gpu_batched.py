@@ -197,3 +197,32 @@ def test_batched_fp32_inner_matches_oracle(rg, systems):
         assert G.rel(G.host(xs[k]), refs[i]) <= 1e-8, i
     for h in hs:
         h.close()
+
+
+def test_many_right_hand_sides_share_one_matrix(rg, systems):
+    """rgdbek_create_like: four right-hand sides of one matrix, each on a
+    handle that shares the base's matrix arrays, solved in one batched launch;
+    the base can be destroyed first and the others keep working."""
+    import torch
+    S, refs = systems
+    s0 = S[0]
+    rng = np.random.default_rng(11)
+    base = rg.Solver(s0.m, s0.n, s0.row_ptr, s0.col_idx, s0.vals, eta_col=0.2, eta_row=0.2,
+                     stop_rule=rg.STOP_NORMAL)
+    derived = [rg.Solver.like(base) for _ in range(3)]
+    hs = [base] + derived
+    B = [s0.b] + [rng.standard_normal(s0.m) for _ in range(3)]
+    bs = [G.dev(b) for b in B]
+    xs = [torch.empty(s0.n, dtype=torch.float64, device="cuda") for _ in hs]
+    status, st = rg.rgdbek_solve_batched([h.handle for h in hs], bs, xs, [1e-12] * 4, 200000,
+                                         seed=2)
+    assert status == rg.OK
+    o = oracle.Options(eta_col=0.2, eta_row=0.2, stop_rule=2, tol=1e-13, max_iter=200000)
+    want = [oracle.solve(s0.A, b, o, n=s0.n).x for b in B]
+    for k in range(4):
+        assert G.rel(G.host(xs[k]), want[k]) <= 1e-8, k
+    base.close()
+    res = derived[1].solve(bs[2], tol=1e-12, max_iter=200000, seed=9)
+    assert res.stats.status == rg.OK and G.rel(G.host(res.x), want[2]) <= 1e-8
+    for h in derived:
+        h.close()
