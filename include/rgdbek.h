@@ -83,6 +83,9 @@ typedef struct {
     int batch_team;        /* CTAs per system in rgdbek_solve_batched (read from the
                               first handle): 0 = the size rgdbek_tune_batched found,
                               else about one system per team                        */
+    int warm_start;        /* 1: x holds x_0 on entry to rgdbek_solve (z_0 = b still);
+                              the limit is then A^+ b + (I - A^+ A) x_0, since the
+                              method never changes x_0's null-space part.  0: x_0 = 0 */
 } rgdbek_options;
 
 typedef struct {

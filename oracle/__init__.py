@@ -54,6 +54,7 @@ class _Opts(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", ctypes.c_int),
         ("inner_tol", _dbl), ("inner_max", ctypes.c_int), ("stop_rule", ctypes.c_int),
         ("tol", _dbl), ("max_iter", _i64), ("seed", _u64), ("sysid", _u64),
+        ("warm", ctypes.c_int),
     ]
 
 
@@ -280,13 +281,14 @@ class Result:
 
 
 def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool = False,
-          keep_iterates: bool = False, lock: list | None = None) -> Result:
+          keep_iterates: bool = False, lock: list | None = None, x0=None) -> Result:
     """Run Algorithm 1 on A = (row_ptr, col_idx, vals) with right-hand side b.
 
     trace          record |U_k|, |J_k|, LSQR step counts and the index sets
     keep_iterates  also record z_k and x_k (small problems only)
     lock           list of (U_k, J_k) index arrays to use instead of sampling
                    (lockstep replay); iterations past the list sample again
+    x0             initial x (a warm start; default 0)
     """
     opts = opts or Options()
     rp, ci, av = _csr(A)
@@ -295,8 +297,11 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
         n = int(ci.max()) + 1 if len(ci) else 0
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(max(n, 1))
+    if x0 is not None:
+        x[:n] = np.asarray(x0, dtype=np.float64)
     o = _Opts(opts.eta_col, opts.eta_row, opts.selection, opts.inner_tol, opts.inner_max,
-              opts.stop_rule, opts.tol, opts.max_iter, opts.seed, opts.sysid)
+              opts.stop_rule, opts.tol, opts.max_iter, opts.seed, opts.sysid,
+              1 if x0 is not None else 0)
     st = _Stats()
     tr = None
     keep = {}

@@ -371,6 +371,7 @@ typedef struct {
     double tol;
     int64_t max_iter;
     uint64_t seed, sysid;
+    int warm;                 /* 1: x holds x_0 on entry (else x_0 = 0)       */
 } OrcOpts;
 
 typedef struct {
@@ -435,8 +436,9 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
     orc_row_norms2(m, rp, av, rn2);
     orc_col_norms2(m, n, rp, ci, av, cn2);
 
-    /* x_0 = 0, z_0 = b */
-    for (int64_t j = 0; j < n; ++j) x[j] = 0.0;
+    /* x_0 = 0 (or the given x_0), z_0 = b */
+    if (!o->warm)
+        for (int64_t j = 0; j < n; ++j) x[j] = 0.0;
     for (int64_t i = 0; i < m; ++i) z[i] = b[i];
     const double bnorm = sqrt(dot(m, b, b));
     orc_spmv_t(m, n, rp, ci, av, b, h);

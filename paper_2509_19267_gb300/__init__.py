@@ -66,7 +66,7 @@ class rgdbek_options(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", _int), ("inner_tol", _dbl),
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
         ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
-        ("batch_team", _int),
+        ("batch_team", _int), ("warm_start", _int),
     ]
 
 
@@ -411,8 +411,8 @@ class Solver:
     def solve(self, b, tol: float = 1e-8, max_iter: int = 10000, seed: int = 0, x=None,
               raise_on_error: bool = True) -> SolveResult:
         import torch
-        if x is None:
-            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        if x is None:  # (with warm_start, x is read as x_0: zeros unless given)
+            x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
         st = rgdbek_solve(self.handle, b, x, tol, max_iter, seed, raise_on_error)
         return SolveResult(x, st)
 

@@ -150,6 +150,7 @@ int check_options(const rgdbek_options &o) {
     if (o.precision != RGDBEK_PRECISION_FP64 && o.precision != RGDBEK_PRECISION_FP32_INNER)
         return RGDBEK_ERR_INVALID_ARG;
     if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
+    if (o.warm_start != 0 && o.warm_start != 1) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -228,6 +229,7 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.eta_col = h->opt.eta_col;
     P.eta_row = h->opt.eta_row;
     P.fp32_inner = h->opt.precision == RGDBEK_PRECISION_FP32_INNER;
+    P.warm = h->opt.warm_start != 0;
     P.inner_tol = P.fp32_inner && h->opt.inner_tol < RGDBEK_FP32_INNER_TOL
                       ? RGDBEK_FP32_INNER_TOL
                       : h->opt.inner_tol;
@@ -299,8 +301,9 @@ void fill_stats(const Ctrl &c, int status, rgdbek_stats *st);
 // One persistent-kernel solve of A x = b (or of A^T x = b when transposed),
 // x0 = 0; reads the control block back into *st.
 int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double tol,
-              long long max_iter, uint64_t seed, rgdbek_stats *st) {
+              long long max_iter, uint64_t seed, rgdbek_stats *st, bool from_zero = false) {
     Params P = make_params(h, transposed);
+    if (from_zero) P.warm = 0;  // the adjoint's inner solves and the tuner's probes
     P.b = b;
     P.x = x;
     P.tol = tol;
@@ -510,6 +513,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->threads_per_block = 0;
     opt->precision = RGDBEK_PRECISION_FP64;
     opt->batch_team = 0;
+    opt->warm_start = 0;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
@@ -758,6 +762,9 @@ int rgdbek_solve_host(rgdbek_t h, const double *b_host, double *x_host, double t
     if (!h || !b_host || !x_host) return RGDBEK_ERR_INVALID_ARG;
     cudaError_t e = cudaMemcpyAsync(h->b_stage, b_host, (size_t)h->m * sizeof(double),
                                     cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->opt.warm_start)  // x_0 from the host buffer
+        e = cudaMemcpyAsync(h->x_stage, x_host, (size_t)h->n * sizeof(double),
+                            cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     const int status = rgdbek_solve(h, h->b_stage, h->x_stage, tol, max_iter, seed, st);
     if (status < 0 && status != RGDBEK_ERR_NONFINITE && status != RGDBEK_ERR_TIMEOUT) return status;
@@ -848,7 +855,7 @@ int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uin
         // the probe solves run from x0 = 0 with a zero tolerance: probe_iters
         // outer iterations each
         e = cudaEventRecord(e0, h->stream);
-        if (e == cudaSuccess) st = run_solve(h, false, b, x, 0.0, probe_iters, seed, nullptr);
+        if (e == cudaSuccess) st = run_solve(h, false, b, x, 0.0, probe_iters, seed, nullptr, true);
         if (e == cudaSuccess && st < 0 && st != RGDBEK_ERR_NONFINITE) {
             h->opt = saved;
             configure_launch(h);
@@ -914,7 +921,7 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
         else if (s == RGDBEK_NOT_CONVERGED && worst == RGDBEK_OK) worst = s;
     };
     // w = A^+T g: the minimum-norm solution of A^T w = g
-    int s0 = run_solve(h, true, grad_x, h->adj_w, tol, max_iter, seed, S + 0);
+    int s0 = run_solve(h, true, grad_x, h->adj_w, tol, max_iter, seed, S + 0, true);
     fold(s0);
     if (s0 < 0) return s0;
     if (grad_b) {
@@ -927,18 +934,18 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
         return e == cudaSuccess ? worst : cuda_status(e);
     }
     // v = A^+ w
-    int s1 = run_solve(h, false, h->adj_w, h->adj_v, tol, max_iter, seed + 1, S + 1);
+    int s1 = run_solve(h, false, h->adj_w, h->adj_v, tol, max_iter, seed + 1, S + 1, true);
     fold(s1);
     if (s1 < 0) return s1;
     const Params P = make_params(h);
     if (rank_term) {
         // u = A^+T x and q = A^+ (A g), so that p = g - q = (I - A^+ A) g
-        int s2 = run_solve(h, true, x, h->adj_u, tol, max_iter, seed + 2, S + 2);
+        int s2 = run_solve(h, true, x, h->adj_u, tol, max_iter, seed + 2, S + 2, true);
         fold(s2);
         if (s2 < 0) return s2;
         if ((e = launch_spmv(P, h->num_sms, kSolveMaxThreads, grad_x, h->adj_ag, h->stream)) != cudaSuccess)
             return cuda_status(e);
-        int s3 = run_solve(h, false, h->adj_ag, h->adj_q, tol, max_iter, seed + 3, S + 3);
+        int s3 = run_solve(h, false, h->adj_ag, h->adj_q, tol, max_iter, seed + 3, S + 3, true);
         fold(s3);
         if (s3 < 0) return s3;
     }

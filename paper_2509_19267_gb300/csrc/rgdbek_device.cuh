@@ -38,6 +38,7 @@ enum DSlot {
     D_TT,         // ||t||^2
     D_FRO_S,      // the block's squared Frobenius norm with unit lines (their count)
     D_EXTRA_S,    // ||D c||^2 of the line-scaled right-hand side (sum of the weights)
+    D_GG,         // ||A^T z||^2 (at k = 0, z_0 = b: ||A^T b||^2)
     D_NSLOTS
 };
 enum ISlot {

@@ -68,6 +68,7 @@ struct Params {
     int inner_max, stop_rule, selection;
     int fp32_inner;         // inner LSQR products in FP32 (Kahan dots)
     int team;               // CTAs that work on this system (rank = blockIdx.x % team)
+    int warm;               // x holds x_0 on entry (else x_0 = 0)
     float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
     double *vvs, *dsc;      // column step: D v~ and D = 1/||A_j|| per column of U
     double *yh;             // column step: y^ of the scaled block (global fallback)
@@ -256,10 +257,10 @@ __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, 
 //   x_k = xt (x_{k-1} plus the row update of the previous iteration),
 //   g = A^T z_k, h = A^T t_k with t_k = b - A x_k (for the stopping test),
 //   eps^z_j = g_j^2 / ||A_j||^2.
-// Partials: max eps^z, ||h||^2, non-finite flag.
+// Partials: max eps^z, ||h||^2, ||g||^2, non-finite flag.
 __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
     const Grp G(P.tpc);
-    double emax = 0.0, hh = 0.0;
+    double emax = 0.0, hh = 0.0, gg = 0.0;
     long long bad = 0;
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
@@ -278,14 +279,17 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
             if (!isfinite(e)) bad = 1;
             else emax = max_nonneg(emax, e);
             hh = fma(sh, sh, hh);
+            gg = fma(sg, sg, gg);
         }
     }
     emax = block_max(emax, bs);
     hh = block_sum(hh, bs);
+    gg = block_sum(gg, bs);
     bad = block_sum(bad, bs);
     if (threadIdx.x == 0) {
         P.pd[D_EMAX_C * tsize(P) + trank(P)] = emax;
         P.pd[D_HH * tsize(P) + trank(P)] = hh;
+        P.pd[D_GG * tsize(P) + trank(P)] = gg;
         P.pi[I_BAD_C * tsize(P) + trank(P)] = bad;
     }
 }

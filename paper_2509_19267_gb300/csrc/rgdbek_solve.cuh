@@ -643,9 +643,12 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             bb = fma(bi, bi, bb);
             if (!isfinite(bi)) bad = 1;
         }
+        // x_0 = 0, or the caller's x (warm start)
         for (long long j = tthread(P); j < P.n; j += tthreads(P)) {
-            P.x[j] = 0.0;
-            P.xt[j] = 0.0;
+            const double x0 = P.warm ? P.x[j] : 0.0;
+            if (!isfinite(x0)) bad = 1;
+            P.x[j] = x0;
+            P.xt[j] = x0;
         }
         bb = block_sum(bb, bs);
         bad = block_sum(bad, bs);
@@ -656,9 +659,14 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
     }
     RGD_SYNC(DS(D_BB), 0, DS(I_BAD_R));
     mark(S, PH_SETUP);
+    if (P.warm) {
+        // t_0 = b - A x_0 for the first stopping test
+        phase_residual(P, bs);
+        RGD_SYNC(DS(D_TT), 0, 0);
+    }
     if (threadIdx.x == 0) {
         O.bb = S.red_d[D_BB];
-        O.tt = O.bb;  // t_0 = z_0 = b
+        O.tt = P.warm ? S.red_d[D_TT] : O.bb;  // t_0 = b - A x_0 (= b from x_0 = 0)
         O.zz = O.bb;
         O.atb2 = 0.0;
         O.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(O.bb)) ? RGDBEK_ERR_NONFINITE
@@ -678,12 +686,12 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             (double)(globaltimer_ns() - t_start) > P.time_budget_ns)
             P.ctrl->stop_req = 1;
         phase_col(P, bs);
-        RGD_SYNC(DS(D_EMAX_C) | DS(D_HH), DS(D_EMAX_C), DS(I_BAD_C));
+        RGD_SYNC(DS(D_EMAX_C) | DS(D_HH) | DS(D_GG), DS(D_EMAX_C), DS(I_BAD_C));
         mark(S, PH_COL);
         if (threadIdx.x == 0) {
             const double hh = S.red_d[D_HH];
             O.emax_c = S.red_d[D_EMAX_C];
-            if (k == 0) O.atb2 = hh;
+            if (k == 0) O.atb2 = S.red_d[D_GG];  // g = A^T z_0 = A^T b
             O.rel = O.bb > 0.0 ? sqrt(O.tt / O.bb) : 0.0;
             O.nrm = O.atb2 > 0.0 ? sqrt(hh / O.atb2) : 0.0;
             int v = kStatusRunning;

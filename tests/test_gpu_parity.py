@@ -427,3 +427,41 @@ def test_inconsistent_row_blocks_take_the_unscaled_solve(rg):
     assert st.status == rg.OK
     assert G.rel(x, xs) <= X_TOL
     assert G.rel(x, ref.x) <= X_TOL
+
+
+def test_warm_start(rg):
+    """x read as x_0: the GPU follows the oracle from the same x_0 to
+    A^+ b + (I - A^+ A) x_0; from the solution it takes no iteration; the host
+    entry point reads x_0 from the host buffer; a non-finite x_0 is reported."""
+    import torch
+    rng = np.random.default_rng(21)
+    D = rng.standard_normal((30, 80))
+    b = rng.standard_normal(30)
+    x0 = rng.standard_normal(80)
+    S = workloads.from_dense(D, b)
+    Ap = np.linalg.pinv(D)
+    want = Ap @ b + (np.eye(80) - Ap @ D) @ x0
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=0.5, eta_row=0.5, stop_rule=rg.STOP_NORMAL,
+                  inner_tol=1e-13, warm_start=1)
+    xd = G.dev(x0)
+    res = s.solve(G.dev(b), tol=1e-12, max_iter=100000, seed=3, x=xd)
+    ref = oracle.solve(S.A, b, oracle.Options(eta_col=0.5, eta_row=0.5, stop_rule=2, tol=1e-12,
+                                              inner_tol=1e-13, max_iter=100000, seed=3),
+                       n=S.n, x0=x0)
+    assert res.stats.status == rg.OK
+    assert G.rel(G.host(res.x), want) <= 1e-8
+    assert G.rel(G.host(res.x), ref.x) <= 1e-8
+    # from the solution: no iteration, x unchanged
+    xs = G.dev(want)
+    res2 = s.solve(G.dev(b), tol=1e-8, max_iter=100, seed=3, x=xs)
+    assert res2.stats.iters == 0 and np.array_equal(G.host(xs), want)
+    # host buffers
+    xh = x0.copy()
+    st = rg.rgdbek_solve_host(s.handle, b.copy(), xh, 1e-12, 100000, 3)
+    assert st.status == rg.OK and G.rel(xh, want) <= 1e-8
+    # non-finite x_0
+    bad = x0.copy()
+    bad[5] = np.inf
+    st = rg.rgdbek_solve(s.handle, G.dev(b), G.dev(bad), 1e-8, 10, 0, raise_on_error=False)
+    assert st.status == rg.ERR_NONFINITE
+    s.close()
