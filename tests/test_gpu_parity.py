@@ -263,7 +263,7 @@ def _gpu_trace(rg, S, eta, seed, iters, rule=2, inner_tol=1e-13):
 def test_lockstep_against_oracle(rg):
     """Same blocks on both sides: the oracle replays the GPU's U_k, J_k."""
     S = workloads.sparse_ls(5000, 1200, 15, sigma=1e-2, seed=21)
-    K = 12
+    K = 20
     st, counts, lists, x = _gpu_trace(rg, S, 0.2, seed=9, iters=K)
     assert st.status == rg.NOT_CONVERGED and st.iters == K
     ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.2, eta_row=0.2, stop_rule=2, tol=0.0,
