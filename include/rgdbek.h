@@ -12,8 +12,13 @@
  *   4. row weights eps^x_i = (b_i - z_{k+1,i} - A^(i) x_k)^2 / ||A^(i)||^2
  *   5. draw ceil(eta_row * m) rows the same way -> row block J_k
  *   6. x_{k+1} = x_k + (A^J)^+ (b^J - z_{k+1}^J - A^J x_k)           (Eq. 4)
- * with x_0 = 0 and z_0 = b.  The block pseudo-inverse products are computed
- * by LSQR started from zero (Remark 3.1), which gives minimum-norm solutions.
+ * with x_0 = 0 (or a given x_0, option warm_start) and z_0 = b.  The block
+ * pseudo-inverse products are computed by LSQR started from zero (Remark
+ * 3.1), which gives minimum-norm solutions: in the column step on A_U with
+ * unit columns (the projection A_U A_U^+ z does not depend on the
+ * least-squares solution taken), in the row step first on A^J with unit rows
+ * (the same minimum-norm solution whenever the block system is consistent;
+ * solved again unscaled when it is not).
  *
  * Every pointer argument marked "device" is CUDA device memory of the
  * current device; "host" pointers are ordinary CPU memory.  All device work
