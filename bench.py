@@ -369,6 +369,13 @@ def run_ours(args):
                                   "achieved_tflops": fp64_tflops,
                                   "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal",
                                   "frac": fp64_tflops / FP64_PEAK_TFLOPS}},
+            # the solve is a chain of grid-synchronised phases: per outer
+            # iteration 13 (passes, selections, extractions, z update) plus one
+            # for the row step's first LSQR vector, and two per LSQR step
+            "grid_phases": {
+                "per_solve": (lambda st: 14 * st.iters + 2 * (st.inner_u + st.inner_j))(st0),
+                "us_per_phase": 1e6 * statistics.median(ms) / 1e3 / max(
+                    1, 14 * st0.iters + 2 * (st0.inner_u + st0.inner_j))},
             "spmv": spmv,
             "cpu_baseline": cpu,
             "e2e": e2e,
