@@ -54,7 +54,7 @@ class _Opts(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", ctypes.c_int),
         ("inner_tol", _dbl), ("inner_max", ctypes.c_int), ("stop_rule", ctypes.c_int),
         ("tol", _dbl), ("max_iter", _i64), ("seed", _u64), ("sysid", _u64),
-        ("warm", ctypes.c_int),
+        ("warm", ctypes.c_int), ("inner_adapt", _dbl),
     ]
 
 
@@ -262,6 +262,7 @@ class Options:
     max_iter: int = 10000
     seed: int = 0
     sysid: int = 0
+    inner_adapt: float = 0.0    # > 0: inner tolerance tied to the outer residual
 
 
 @dataclass
@@ -301,7 +302,7 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
         x[:n] = np.asarray(x0, dtype=np.float64)
     o = _Opts(opts.eta_col, opts.eta_row, opts.selection, opts.inner_tol, opts.inner_max,
               opts.stop_rule, opts.tol, opts.max_iter, opts.seed, opts.sysid,
-              1 if x0 is not None else 0)
+              1 if x0 is not None else 0, opts.inner_adapt)
     st = _Stats()
     tr = None
     keep = {}

@@ -372,6 +372,9 @@ typedef struct {
     int64_t max_iter;
     uint64_t seed, sysid;
     int warm;                 /* 1: x holds x_0 on entry (else x_0 = 0)       */
+    double inner_adapt;       /* > 0: inner tolerance of iteration k is
+                                 max(inner_tol, min(0.1, inner_adapt * r_k)),
+                                 r_k the stopping rule's measure of x_k       */
 } OrcOpts;
 
 typedef struct {
@@ -479,6 +482,15 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
             break;
         }
         const int lock = tr && tr->lock_counts && k < tr->lock_iters;
+        /* inner tolerance of this iteration: fixed, or tied to how far x_k is
+           from the stopping rule (looser block solves while far away) */
+        double itol = o->inner_tol;
+        if (o->inner_adapt > 0.0) {
+            const double rk = o->stop_rule == 1 ? rel : (o->stop_rule == 3 ? rel * rel : nrm);
+            double a = o->inner_adapt * rk;
+            if (a > 0.1) a = 0.1;
+            if (a > itol) itol = a;
+        }
 
         /* column step: eps^z_j = (A_j^T z_k)^2 / ||A_j||^2, sample U_k,
            z_{k+1} = z_k - A_U A_U^+ z_k */
@@ -510,7 +522,7 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
             extract_columns(m, n, rp, ci, av, nu, U, srp, sci, sav);
             for (int64_t p = 0; p < nu; ++p) dcol[p] = 1.0 / sqrt(cn2[U[p]]);
             for (int64_t e = 0; e < srp[m]; ++e) bsc[e] = sav[e] * dcol[sci[e]];
-            steps_u = orc_lsqr(m, nu, srp, sci, bsc, z, o->inner_tol, sqrt((double)nu),
+            steps_u = orc_lsqr(m, nu, srp, sci, bsc, z, itol, sqrt((double)nu),
                                o->inner_max, y);
             for (int64_t p = 0; p < nu; ++p) y[p] *= dcol[p];
             orc_spmv(m, srp, sci, sav, y, Ax); /* A_U y */
@@ -559,13 +571,13 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
                     for (int64_t e = srp[p]; e < srp[p + 1]; ++e) bsc[e] = sav[e] * dr;
                     rJ[p] *= dr;
                 }
-                steps_j = orc_lsqr_fit(nj, n, srp, sci, bsc, rJ, o->inner_tol,
+                steps_j = orc_lsqr_fit(nj, n, srp, sci, bsc, rJ, itol,
                                        sqrt((double)nj), o->inner_max, d, &fit);
                 if (fit == 0)
                     for (int64_t p = 0; p < nj; ++p) rJ[p] = r[J[p]];
             }
             if (nj > n || fit == 0)
-                steps_j += orc_lsqr(nj, n, srp, sci, sav, rJ, o->inner_tol, sqrt(fro2),
+                steps_j += orc_lsqr(nj, n, srp, sci, sav, rJ, itol, sqrt(fro2),
                                     o->inner_max, d);
             for (int64_t j = 0; j < n; ++j) x[j] += d[j];
         }
