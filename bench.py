@@ -65,6 +65,8 @@ def parse():
                     help="cap on outer iterations per solve (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the secondary solve with the adaptive inner tolerance")
     ap.add_argument("--workload", default="sparse_ls",
                     choices=["sparse_ls", "batched_deblur", "poisson_mixed", "deblur_adjoint"])
     ap.add_argument("--batch-count", type=int, default=256)
@@ -324,6 +326,12 @@ def run_ours(args):
     # standalone SpMV kernels (the a1 / a5 products), L2 flushed before each launch
     spmv = spmv_rooflines(rg, solver, S, dev, flush, peak)
 
+    # secondary figure: the same solve with the inner tolerance tied to the
+    # outer residual (inner_adapt = 0.01); the headline keeps the fixed one
+    adaptive = None
+    if not args.no_adaptive:
+        adaptive = adaptive_inner(rg, S, opts, w, max_iter, b, x, flush, stream, args)
+
     # end to end through the public API with host buffers: create from pinned
     # host CSR (H2D of A and the CSC/norm set-up), solve with host b and x
     e2e = None
@@ -377,6 +385,7 @@ def run_ours(args):
                 "us_per_phase": 1e6 * statistics.median(ms) / 1e3 / max(
                     1, 14 * st0.iters + 2 * (st0.inner_u + st0.inner_j))},
             "spmv": spmv,
+            "adaptive_inner": adaptive,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
@@ -444,6 +453,37 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
         gbs = nbytes / t / 1e9
         out[name] = {"us": t * 1e6, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / peak}
     return out
+
+
+def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.01):
+    """Time the solve with inner_adapt = c (inner tolerance
+    max(1e-10, min(0.1, c * r_k))) under the same L2 flush, and compare its
+    solution with the fixed-tolerance one left in x_ref."""
+    import torch
+    s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, inner_adapt=c, **opts)
+    x = torch.empty_like(x_ref)
+    st = rg.rgdbek_solve(s.handle, b, x, w["tol"], max_iter, 77)
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(rg.rgdbek_solve(s.handle, b, x, w["tol"], max_iter, i))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s.close()
+    its = sum(t.iters for t in stats)
+    st = stats[0]
+    return {"inner_adapt": c, "value": its / (sum(ms) / 1e3), "unit": UNIT,
+            "time_to_tol_s": statistics.median(ms) / 1e3,
+            "iters_per_solve": [t.iters for t in stats],
+            "lsqr_steps_per_solve": [t.inner_u + t.inner_j for t in stats],
+            "status": [t.status for t in stats],
+            "rel_diff_to_fixed_tol_x": float(torch.linalg.norm(x - x_ref) /
+                                             torch.linalg.norm(x_ref)),
+            "final_normal_res": st.normal_res}
 
 
 def end_to_end(rg, S, opts, w, max_iter, args):

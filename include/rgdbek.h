@@ -91,6 +91,11 @@ typedef struct {
     int warm_start;        /* 1: x holds x_0 on entry to rgdbek_solve (z_0 = b still);
                               the limit is then A^+ b + (I - A^+ A) x_0, since the
                               method never changes x_0's null-space part.  0: x_0 = 0 */
+    double inner_adapt;    /* > 0: the inner tolerance of outer iteration k is
+                              max(inner_tol, min(0.1, inner_adapt * r_k)), r_k the
+                              stopping rule's measure of x_k (looser block solves
+                              while x_k is far from the target; the outer test and
+                              its tolerance are unchanged).  0 (default): inner_tol */
 } rgdbek_options;
 
 typedef struct {

@@ -66,7 +66,7 @@ class rgdbek_options(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", _int), ("inner_tol", _dbl),
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
         ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
-        ("batch_team", _int), ("warm_start", _int),
+        ("batch_team", _int), ("warm_start", _int), ("inner_adapt", _dbl),
     ]
 
 

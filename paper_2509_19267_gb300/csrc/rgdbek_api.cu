@@ -151,6 +151,7 @@ int check_options(const rgdbek_options &o) {
         return RGDBEK_ERR_INVALID_ARG;
     if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.warm_start != 0 && o.warm_start != 1) return RGDBEK_ERR_INVALID_ARG;
+    if (!(o.inner_adapt >= 0.0)) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -230,6 +231,7 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.eta_row = h->opt.eta_row;
     P.fp32_inner = h->opt.precision == RGDBEK_PRECISION_FP32_INNER;
     P.warm = h->opt.warm_start != 0;
+    P.inner_adapt = h->opt.inner_adapt;
     P.inner_tol = P.fp32_inner && h->opt.inner_tol < RGDBEK_FP32_INNER_TOL
                       ? RGDBEK_FP32_INNER_TOL
                       : h->opt.inner_tol;
@@ -514,6 +516,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->precision = RGDBEK_PRECISION_FP64;
     opt->batch_team = 0;
     opt->warm_start = 0;
+    opt->inner_adapt = 0.0;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,

@@ -62,6 +62,7 @@ struct Params {
     long long tr_list_cap;
     // options
     double tol, inner_tol, eta_col, eta_row;
+    double inner_adapt;     // > 0: per-iteration inner tolerance tied to the outer residual
     double time_budget_ns;
     long long max_iter, s_col, s_row;
     unsigned long long seed, sysid;

@@ -36,6 +36,7 @@ struct LsqrState {
     double irho, cs, sn;         // plane rotation of the current step (1/rho, c, s)
     double inv_a, ab, wcoef;     // coefficients of the next rows phase
     double inv_b, ba, phi_rho;   // coefficients of the next cols phase
+    double itol;                 // inner tolerance of this solve
     int mv, done;
     int fit;                     // at the end: 1 = the residual met the tolerance (a
                                  // consistent block), 2 = step cap, 0 = otherwise
@@ -46,6 +47,7 @@ struct OuterState {
     double bb, tt, zz, atb2, rel, nrm, emax_c, emax_r;
     double beta1, alpha1, fro2, inv_beta1;
     double beta1s, fro2s;        // row step: the same for the row-scaled block
+    double itol;                 // inner tolerance of this iteration
     int verdict;                 // status to finish with, or kStatusRunning to go on
 };
 
@@ -433,6 +435,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         L.inv_b = 1.0 / beta1;
         L.done = 0;
         L.fit = 0;
+        L.itol = S.o.itol;
     }
     __syncthreads();
 
@@ -489,8 +492,8 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 L.wcoef = sn * an * L.irho;   // theta / rho
                 const double rnorm = L.phibar;
                 const double arnorm = L.phibar * an * fabs(cs);
-                const bool resid = rnorm <= P.inner_tol * L.beta1 || bn == 0.0;
-                const bool other = arnorm <= P.inner_tol * L.fro * rnorm || an == 0.0;
+                const bool resid = rnorm <= L.itol * L.beta1 || bn == 0.0;
+                const bool other = arnorm <= L.itol * L.fro * rnorm || an == 0.0;
                 const bool cap = it - 1 >= P.inner_max;
                 L.done = resid || other || cap;
                 L.fit = resid ? 1 : (other ? 0 : (cap ? 2 : 0));
@@ -694,6 +697,16 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             if (k == 0) O.atb2 = S.red_d[D_GG];  // g = A^T z_0 = A^T b
             O.rel = O.bb > 0.0 ? sqrt(O.tt / O.bb) : 0.0;
             O.nrm = O.atb2 > 0.0 ? sqrt(hh / O.atb2) : 0.0;
+            // inner tolerance of this iteration: fixed, or tied to how far x_k
+            // is from the stopping rule (looser block solves while far away)
+            O.itol = P.inner_tol;
+            if (P.inner_adapt > 0.0) {
+                const double rk = P.stop_rule == RGDBEK_STOP_REL_RES
+                                      ? O.rel
+                                      : (P.stop_rule == RGDBEK_STOP_RSE ? O.rel * O.rel : O.nrm);
+                const double a = fmin(0.1, P.inner_adapt * rk);
+                if (a > O.itol) O.itol = a;
+            }
             int v = kStatusRunning;
             if (S.red_i[I_BAD_C] != 0 || !isfinite(hh) || !isfinite(O.tt)) v = RGDBEK_ERR_NONFINITE;
             else if (stop_rule_holds(P.stop_rule, P.tol, O.rel, O.nrm)) v = RGDBEK_OK;

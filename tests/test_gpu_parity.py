@@ -241,9 +241,10 @@ def test_greedy_mode_solve(rg):
     assert G.rel(x, S.x_true) <= X_TOL
 
 
-def _gpu_trace(rg, S, eta, seed, iters, rule=2, inner_tol=1e-13):
+def _gpu_trace(rg, S, eta, seed, iters, rule=2, inner_tol=1e-13, **opts):
     import torch
-    s = rg.Solver(S.m, S.n, *S.A, eta_col=eta, eta_row=eta, stop_rule=rule, inner_tol=inner_tol)
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=eta, eta_row=eta, stop_rule=rule, inner_tol=inner_tol,
+                  **opts)
     counts = torch.zeros((iters + 1, 4), dtype=torch.int64, device="cuda")
     lists = torch.zeros(iters * (S.m + S.n) + 1, dtype=torch.int32, device="cuda")
     rg.rgdbek_set_trace(s.handle, counts, lists)
@@ -465,3 +466,30 @@ def test_warm_start(rg):
     st = rg.rgdbek_solve(s.handle, G.dev(b), G.dev(bad), 1e-8, 10, 0, raise_on_error=False)
     assert st.status == rg.ERR_NONFINITE
     s.close()
+
+
+def test_adaptive_inner_tolerance_lockstep_and_solution(rg):
+    """inner_adapt > 0: the GPU and the oracle derive the inner tolerance of
+    iteration k from the same residual measure, so in lockstep their x and LSQR
+    step counts agree; the free-running solve reaches the least-squares
+    solution with fewer LSQR steps than at the fixed inner tolerance."""
+    S = workloads.sparse_ls(5000, 1200, 15, sigma=1e-2, seed=22)
+    K = 12
+    st, counts, lists, x = _gpu_trace(rg, S, 0.2, seed=9, iters=K, inner_adapt=0.01)
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.2, eta_row=0.2, stop_rule=2, tol=0.0,
+                                                inner_tol=1e-13, inner_adapt=0.01, max_iter=K,
+                                                seed=9),
+                       n=S.n, lock=lists, trace=True)
+    assert G.rel(x, ref.x) <= 1e-10
+    assert np.all(np.abs(ref.counts[:, 2:] - counts[:, 2:]) <= 1)
+    xs = np.linalg.lstsq(S.dense(), S.b, rcond=None)[0]
+    steps = []
+    for adapt in (0.0, 0.01):
+        s = rg.Solver(S.m, S.n, *S.A, eta_col=0.2, eta_row=0.2, stop_rule=rg.STOP_NORMAL,
+                      inner_tol=1e-13, inner_adapt=adapt)
+        res = s.solve(G.dev(S.b), tol=1e-12, max_iter=100000, seed=9)
+        s.close()
+        assert res.stats.status == rg.OK
+        assert G.rel(G.host(res.x), xs) <= X_TOL
+        steps.append(res.stats.inner_u + res.stats.inner_j)
+    assert steps[1] < 0.8 * steps[0]
