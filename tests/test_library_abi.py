@@ -58,6 +58,13 @@ def test_host_only_calls():
                                  av.ctypes.data, 0, ctypes.byref(bad), None) \
         == rg.ERR_INVALID_ARG
     assert rg.default_options().precision == rg.PRECISION_FP64
+    # the adaptive inner tolerance factor must be a finite c >= 0 (default 0: off)
+    assert rg.default_options().inner_adapt == 0.0
+    for c in (-0.5, float("nan")):
+        bad = rg.default_options(inner_adapt=c)
+        assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 1, rp.ctypes.data, ci.ctypes.data,
+                                     av.ctypes.data, 0, ctypes.byref(bad), None) \
+            == rg.ERR_INVALID_ARG
 
 
 def test_size_limits_rejected_before_any_device_call():
