@@ -327,7 +327,7 @@ def run_ours(args):
     spmv = spmv_rooflines(rg, solver, S, dev, flush, peak)
 
     # secondary figure: the same solve with the inner tolerance tied to the
-    # outer residual (inner_adapt = 0.01); the headline keeps the fixed one
+    # outer residual (inner_adapt = 0.1); the headline keeps the fixed one
     adaptive = None
     if not args.no_adaptive:
         adaptive = adaptive_inner(rg, S, opts, w, max_iter, b, x, flush, stream, args)
@@ -455,7 +455,7 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
     return out
 
 
-def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.01):
+def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.1):
     """Time the solve with inner_adapt = c (inner tolerance
     max(1e-10, min(0.1, c * r_k))) under the same L2 flush, and compare its
     solution with the fixed-tolerance one left in x_ref."""

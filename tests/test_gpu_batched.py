@@ -226,3 +226,33 @@ def test_many_right_hand_sides_share_one_matrix(rg, systems):
     assert res.stats.status == rg.OK and G.rel(G.host(res.x), want[2]) <= 1e-8
     for h in derived:
         h.close()
+
+
+def test_batched_per_system_adaptive_inner_tolerance(rg, systems):
+    """Each handle brings its own options into the shared launch: every other
+    system uses the adaptive inner tolerance (c = 0.1); all reach the oracle's
+    solution, and the adaptive ones take no more LSQR steps in total than the
+    same systems at the fixed tolerance."""
+    import torch
+    S, refs = systems
+    hs = [rg.Solver(s.m, s.n, s.row_ptr, s.col_idx, s.vals, eta_col=0.2, eta_row=0.2,
+                    stop_rule=rg.STOP_NORMAL, batch_team=4, inner_adapt=0.1 if i % 2 else 0.0)
+          for i, s in enumerate(S)]
+    bs = [G.dev(s.b) for s in S]
+    xs = [torch.empty(s.n, dtype=torch.float64, device="cuda") for s in S]
+    status, st = rg.rgdbek_solve_batched([h.handle for h in hs], bs, xs, [1e-12] * len(S),
+                                         200000, seed=5)
+    assert status == rg.OK
+    for i in range(len(S)):
+        assert st[i].status == rg.OK and st[i].normal_res <= 1e-12
+        assert G.rel(G.host(xs[i]), refs[i]) <= 1e-8, i
+    for h in hs:
+        h.set_options(inner_adapt=0.0)
+    status, st0 = rg.rgdbek_solve_batched([h.handle for h in hs], bs, xs, [1e-12] * len(S),
+                                          200000, seed=5)
+    assert status == rg.OK
+    odd = range(1, len(S), 2)
+    assert sum(st[i].inner_u + st[i].inner_j for i in odd) \
+        <= sum(st0[i].inner_u + st0[i].inner_j for i in odd)
+    for h in hs:
+        h.close()

@@ -3,8 +3,8 @@ options, each solved on the GPU and by the FP64 oracle to a tight tolerance.
 
 Cases (seeded): tall, fat and square; sparse and dense; consistent and
 inconsistent; full rank and rank deficient (duplicated or zero rows and
-columns); random eta, selection rule, stopping rule, inner precision and
-launch shape (threads per CTA).  The bar is the FP64 one, 1e-8 relative to
+columns); random eta, selection rule, stopping rule, inner precision,
+adaptive inner tolerance and launch shape (threads per CTA).  The bar is the FP64 one, 1e-8 relative to
 the oracle's solution and to pinv(A) b, except for FP32 inner products on
 systems with a null space (their stated bound, 1e-6).
 """
@@ -51,7 +51,8 @@ def _case(rng):
                 stop_rule=2,
                 precision=int(rng.random() < 0.3),
                 threads=int(rng.choice([0, 256, 512, 1024])),
-                seed=int(rng.integers(1 << 30)))
+                seed=int(rng.integers(1 << 30)),
+                inner_adapt=float(rng.choice([0.0, 0.0, 0.01, 1.0])))
     return kind, defect, D, b, opts
 
 
@@ -65,14 +66,16 @@ def test_random_case_matches_oracle_and_pinv(case):
         pytest.skip("empty matrix")
     s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=o["eta"], eta_row=o["eta"],
                   selection=o["selection"], stop_rule=o["stop_rule"], inner_tol=1e-13,
-                  precision=o["precision"], threads_per_block=o["threads"])
+                  precision=o["precision"], threads_per_block=o["threads"],
+                  inner_adapt=o["inner_adapt"])
     res = s.solve(G.dev(S.b), tol=1e-12, max_iter=200000, seed=o["seed"])
     x = G.host(res.x).copy()
     s.close()
     ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=o["eta"], eta_row=o["eta"],
                                                 selection=o["selection"], stop_rule=2,
                                                 tol=1e-12, inner_tol=1e-13, max_iter=200000,
-                                                seed=o["seed"]), n=S.n)
+                                                seed=o["seed"], inner_adapt=o["inner_adapt"]),
+                       n=S.n)
     xs = np.linalg.pinv(D, rcond=1e-10) @ b
     label = f"{kind}/{defect}/{o}"
     assert res.stats.status == rg.OK, label
