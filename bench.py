@@ -332,6 +332,12 @@ def run_ours(args):
     if not args.no_adaptive:
         adaptive = adaptive_inner(rg, S, opts, w, max_iter, b, x, flush, stream, args)
 
+    # secondary figure: eta chosen by the measured tuner, and the time to the
+    # tolerance at every candidate (the headline keeps eta = 0.1)
+    eta = None
+    if not args.no_adaptive:
+        eta = eta_tuning(rg, S, opts, w, max_iter, b, flush, stream)
+
     # end to end through the public API with host buffers: create from pinned
     # host CSR (H2D of A and the CSC/norm set-up), solve with host b and x
     e2e = None
@@ -386,6 +392,7 @@ def run_ours(args):
                     1, 14 * st0.iters + 2 * (st0.inner_u + st0.inner_j))},
             "spmv": spmv,
             "adaptive_inner": adaptive,
+            "eta_tuning": eta,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
@@ -484,6 +491,34 @@ def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.
             "rel_diff_to_fixed_tol_x": float(torch.linalg.norm(x - x_ref) /
                                              torch.linalg.norm(x_ref)),
             "final_normal_res": st.normal_res}
+
+
+def eta_tuning(rg, S, opts, w, max_iter, b, flush, stream, probe_iters=20):
+    """rgdbek_tune_eta over its default candidates (probe_iters iterations
+    each), then one L2-flushed solve to the tolerance at every candidate, so
+    the tuner's choice can be checked against the measured best."""
+    import torch
+    o = dict(opts)
+    o.pop("eta_col", None)
+    o.pop("eta_row", None)
+    s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=w["eta"], eta_row=w["eta"], **o)
+    x = torch.empty(S.n, dtype=torch.float64, device=b.device)
+    best, scores = s.tune_eta(b, probe_iters=probe_iters, seed=5)
+    per = {}
+    for c in rg.ETA_CANDIDATES:
+        s.set_options(eta_col=c, eta_row=c)
+        flush.fill_(c)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = rg.rgdbek_solve(s.handle, b, x, w["tol"], max_iter, 3, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per[str(c)] = {"time_to_tol_s": e0.elapsed_time(e1) / 1e3, "iters": st.iters,
+                       "status": st.status, "tuner_score": scores[c]}
+    s.close()
+    fastest = min(per, key=lambda k: per[k]["time_to_tol_s"] if per[k]["status"] == 0 else 1e30)
+    return {"probe_iters": probe_iters, "tuned_eta": best, "fastest_eta": float(fastest),
+            "by_eta": per}
 
 
 def end_to_end(rg, S, opts, w, max_iter, args):

@@ -238,6 +238,23 @@ int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *
                         const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
                         int *block_out, double *ms_out);
 
+/* Autotuner of the block fraction eta (Section 2: a larger eta gives larger
+ * blocks, so costlier iterations but fewer of them; which wins depends on the
+ * matrix and on the GPU).  For each candidate c (host array of ncand values in
+ * (0, 1]; candidates NULL with ncand 0 takes the RGDBEK_ETA_CANDIDATES values
+ * 0.05, 0.1, 0.2, 0.3, 0.5) it runs probe_iters outer iterations with
+ * eta_col = eta_row = c from x0 = 0 on b (device, m) into x (device, n,
+ * overwritten), times them with CUDA events, and scores the decrease of the
+ * stopping rule's measure (1 at x0 = 0) as -ln(measure) per second.  The
+ * handle keeps the best candidate as eta_col and eta_row; *eta_out receives
+ * it and rate_out (host double[ncand], may be NULL) every score.  The probe
+ * is short, so the score favours the early rate of decrease.  Returns OK or
+ * the first error (the options are then left as they were). */
+#define RGDBEK_ETA_CANDIDATES 5
+int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candidates,
+                    int ncand, int64_t probe_iters, uint64_t seed, double *eta_out,
+                    double *rate_out);
+
 /* Autotuner of the single solve's kernel shape: runs probe_iters outer
  * iterations from x0 = 0 on b (device, m) into x (device, n, overwritten)
  * with 512 and with 1024 threads per CTA, times each with CUDA events, and

@@ -12,6 +12,7 @@ Entry points (each a function of the same name as in the header):
   rgdbek_solve, rgdbek_solve_host      one solve (device or host buffers)
   rgdbek_solve_batched                 many systems in one persistent launch
   rgdbek_tune, rgdbek_tune_batched     measured choice of kernel shape / team
+  rgdbek_tune_eta                      measured choice of the block fraction eta
   rgdbek_backward                      implicit adjoint (dL/db, dL/dA)
   rgdbek_spmv, rgdbek_spmv_t, rgdbek_weights, rgdbek_sample,
   rgdbek_sample_noalloc, rgdbek_set_trace, rgdbek_get_norms, rgdbek_get_csc
@@ -113,6 +114,8 @@ SIGNATURES = [
                                     ctypes.POINTER(_dbl)]),
     ("rgdbek_tune", _int, [_ptr, _ptr, _ptr, _i64, _u64, ctypes.POINTER(_int),
                            ctypes.POINTER(_dbl)]),
+    ("rgdbek_tune_eta", _int, [_ptr, _ptr, _ptr, _ptr, _int, _i64, _u64,
+                               ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
                                ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
@@ -304,6 +307,23 @@ def rgdbek_tune(h: int, b, x, probe_iters: int = 5, seed: int = 0):
     return block.value, {512: ms[0], 1024: ms[1]}
 
 
+ETA_CANDIDATES = (0.05, 0.1, 0.2, 0.3, 0.5)
+
+
+def rgdbek_tune_eta(h: int, b, x, candidates=None, probe_iters: int = 20, seed: int = 0):
+    """Scores each candidate eta by -ln(stopping measure) per second over
+    probe_iters iterations from x0 = 0; the handle keeps the best.  Returns
+    (best_eta, {eta: score})."""
+    cands = tuple(ETA_CANDIDATES if candidates is None else candidates)
+    C = (_dbl * len(cands))(*cands)
+    rate = (_dbl * len(cands))()
+    best = _dbl(0.0)
+    _check(_lib.rgdbek_tune_eta(h, _dptr(b), _dptr(x), None if candidates is None else C,
+                                0 if candidates is None else len(cands), probe_iters, seed,
+                                ctypes.byref(best), rate), "rgdbek_tune_eta")
+    return best.value, {c: rate[i] for i, c in enumerate(cands)}
+
+
 ADJ_RANK_TERM = 1
 
 
@@ -407,6 +427,15 @@ class Solver:
 
     def info(self) -> rgdbek_info_t:
         return rgdbek_get_info(self.handle)
+
+    def tune_eta(self, b, candidates=None, probe_iters: int = 20, seed: int = 0):
+        """Measured choice of eta (rgdbek_tune_eta); the solver keeps it.
+        Returns (best_eta, {eta: score})."""
+        import torch
+        x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        best, scores = rgdbek_tune_eta(self.handle, b, x, candidates, probe_iters, seed)
+        self.options.eta_col = self.options.eta_row = best
+        return best, scores
 
     def solve(self, b, tol: float = 1e-8, max_iter: int = 10000, seed: int = 0, x=None,
               raise_on_error: bool = True) -> SolveResult:

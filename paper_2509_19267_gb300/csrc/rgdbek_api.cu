@@ -888,6 +888,66 @@ int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uin
     return st;
 }
 
+int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candidates,
+                    int ncand, int64_t probe_iters, uint64_t seed, double *eta_out,
+                    double *rate_out) {
+    static const double kDefault[RGDBEK_ETA_CANDIDATES] = {0.05, 0.1, 0.2, 0.3, 0.5};
+    if (!h || !b || !x || probe_iters < 1 || ncand < 0 || (ncand > 0 && !candidates))
+        return RGDBEK_ERR_INVALID_ARG;
+    if (ncand == 0) {
+        candidates = kDefault;
+        ncand = RGDBEK_ETA_CANDIDATES;
+    }
+    for (int c = 0; c < ncand; ++c)
+        if (!(candidates[c] > 0.0 && candidates[c] <= 1.0)) return RGDBEK_ERR_INVALID_ARG;
+    const rgdbek_options saved = h->opt;
+    int best = -1;
+    double best_rate = 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int c = 0; e == cudaSuccess && c < ncand; ++c) {
+        h->opt.eta_col = candidates[c];
+        h->opt.eta_row = candidates[c];
+        rgdbek_stats st{};
+        float ms = 0.f;
+        // probe_iters outer iterations from x0 = 0 with a zero tolerance
+        e = cudaEventRecord(e0, h->stream);
+        int rs = RGDBEK_OK;
+        if (e == cudaSuccess) rs = run_solve(h, false, b, x, 0.0, probe_iters, seed, &st, true);
+        if (e == cudaSuccess && rs < 0) {
+            h->opt = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rs;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        // the stopping rule's measure of x_K (it is 1 at x_0 = 0): its decrease
+        // in natural-log units per second of device time
+        const double r = h->opt.stop_rule == RGDBEK_STOP_REL_RES
+                             ? st.rel_res
+                             : (h->opt.stop_rule == RGDBEK_STOP_RSE ? st.rse : st.normal_res);
+        const double t = ms > 0.f ? 1e-3 * ms : 1e-9;
+        const double rate = r > 0.0 ? -std::log(r) / t : HUGE_VAL;
+        if (rate_out) rate_out[c] = rate;
+        if (best < 0 || rate > best_rate) {
+            best = c;
+            best_rate = rate;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->opt = saved;
+    if (e != cudaSuccess) return cuda_status(e);
+    h->opt.eta_col = candidates[best];
+    h->opt.eta_row = candidates[best];
+    if (eta_out) *eta_out = candidates[best];
+    return RGDBEK_OK;
+}
+
 int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *grad_x,
                     double *grad_b, double *grad_vals, double tol, int64_t max_iter,
                     uint64_t seed, int flags, rgdbek_stats *st) {

@@ -493,3 +493,39 @@ def test_adaptive_inner_tolerance_lockstep_and_solution(rg):
         assert G.rel(G.host(res.x), xs) <= X_TOL
         steps.append(res.stats.inner_u + res.stats.inner_j)
     assert steps[1] < 0.8 * steps[0]
+
+
+def test_eta_tuner(rg):
+    """rgdbek_tune_eta scores each candidate by the decrease of the stopping
+    measure per second over a short probe and keeps the best: afterwards the
+    handle solves exactly as a fresh handle with that eta; bad candidates and
+    probe lengths are rejected with the options left as they were."""
+    import ctypes
+    S = workloads.sparse_ls(5000, 1200, 15, sigma=1e-2, seed=23)
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=0.3, eta_row=0.3, stop_rule=rg.STOP_NORMAL)
+    b = G.dev(S.b)
+    best, scores = s.tune_eta(b, candidates=(0.1, 0.5), probe_iters=10)
+    assert best in (0.1, 0.5) and set(scores) == {0.1, 0.5}
+    assert all(np.isfinite(v) and v > 0 for v in scores.values())
+    assert scores[best] == max(scores.values())
+    r1 = s.solve(b, tol=1e-10, max_iter=100000, seed=4)
+    f = rg.Solver(S.m, S.n, *S.A, eta_col=best, eta_row=best, stop_rule=rg.STOP_NORMAL)
+    r2 = f.solve(b, tol=1e-10, max_iter=100000, seed=4)
+    assert r1.stats.iters == r2.stats.iters
+    assert np.array_equal(G.host(r1.x), G.host(r2.x))
+    f.close()
+    best_d, scores_d = s.tune_eta(b, probe_iters=5)
+    assert best_d in rg.ETA_CANDIDATES and len(scores_d) == len(rg.ETA_CANDIDATES)
+    x = G.dev(np.zeros(S.n))
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    for cands, iters in (((0.0, 0.2), 5), ((1.5,), 5), ((0.2,), 0)):
+        C = (ctypes.c_double * len(cands))(*cands)
+        assert rg._lib.rgdbek_tune_eta(s.handle, P(b), P(x), C, len(cands), iters, 0, None,
+                                       None) == rg.ERR_INVALID_ARG
+    # a rejected call changed nothing: the handle still solves with best_d
+    r3 = s.solve(b, tol=1e-10, max_iter=100000, seed=4)
+    g = rg.Solver(S.m, S.n, *S.A, eta_col=best_d, eta_row=best_d, stop_rule=rg.STOP_NORMAL)
+    r4 = g.solve(b, tol=1e-10, max_iter=100000, seed=4)
+    assert np.array_equal(G.host(r3.x), G.host(r4.x))
+    g.close()
+    s.close()
