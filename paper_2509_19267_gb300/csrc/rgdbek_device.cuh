@@ -377,11 +377,13 @@ __device__ __forceinline__ int ceil_log2_ll(long long v) {
 
 // Lanes to put on one row/column of a matrix with nnz nonzeros in `lines`
 // rows/columns, integer arithmetic only.
-// pick_lanes_int: for integer-only passes (counting, extraction), where only
-// latency matters: the largest power of two L <= 32 with 2L <= nnz / lines.
+// pick_lanes_int: for the adjoint's pass over the entries, where each lane
+// does little per entry: the largest power of two L <= 32 with 2L <= nnz / lines.
 // pick_lanes_fp64: for passes with FP64 multiply-adds, where GB300's low FP64
-// issue rate makes idle lanes and group shuffle-adds expensive: about eight
-// entries per lane (the largest power of two L <= 32 with 8L <= nnz / lines).
+// issue rate makes idle lanes and group shuffle-adds expensive, and for the
+// block extractions, where fewer lanes per line keep more lines in flight:
+// about eight entries per lane (the largest power of two L <= 32 with
+// 8L <= nnz / lines).
 __host__ __device__ __forceinline__ int pick_lanes_int(long long nnz, long long lines) {
     int L = 1;
     while (L < 32 && 4ll * L * lines <= nnz) L *= 2;

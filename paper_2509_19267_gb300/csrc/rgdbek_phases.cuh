@@ -526,13 +526,16 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
         nit = (int)__reduce_max_sync(kFull, (unsigned)nit);
         long long pos = e0;
         for (int it = 0; it < nit; ++it) {
-            // four entries per lane per trip: index loads, then map gathers
+            // four entries per lane per trip: index and value loads, then map gathers
             const long long e = e0 + (long long)it * 4 * L + G.sl;
             int p[4];
+            double vq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const long long f = e + q * L;
-                p[q] = (valid && f < e1) ? __ldg(A.idx + f) : -1;
+                const bool in = valid && f < e1;
+                p[q] = in ? __ldg(A.idx + f) : -1;
+                vq[q] = in ? __ldg(A.val + f) : 0.0;   // with the index: one round trip less
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) p[q] = p[q] >= 0 ? map[p[q]] : -1;
@@ -542,7 +545,7 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
                 if (p[q] >= 0) {
                     const long long o = pos + __popc(gm & ((1u << G.sl) - 1u));
                     oidx[o] = p[q];
-                    oval[o] = __ldg(A.val + e + q * L);
+                    oval[o] = vq[q];
                 }
                 pos += __popc(gm);
             }

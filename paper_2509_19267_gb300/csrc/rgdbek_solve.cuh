@@ -760,7 +760,9 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 if (rec_u) P.tr_lists[tr_off + p] = j;
             }
             // A_U: the entries of every row of A that lie in U's columns
-            const Lines Arows{P.rp, P.ci, P.av, P.m, P.ipr};
+            // about ten entries per lane, as in the FP64 passes (measured: fewer
+            // lanes per line keep more lines, and so more loads, in flight)
+            const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
             phase_extract(P, Arows, P.colpos, P.srn, P.sci, P.sav, bs);
             RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_COL_EXT);
@@ -838,7 +840,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 if (rec_j) P.tr_lists[tr_off + nU + p] = i;
             }
             // A^J: the entries of every column of A that lie in J's rows
-            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.ipc};
+            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
             phase_extract(P, Acols, P.rowpos, P.scn, P.sri, P.scv, bs);
             RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_ROW_EXT);
