@@ -332,6 +332,11 @@ def run_ours(args):
     if not args.no_adaptive:
         adaptive = adaptive_inner(rg, S, opts, w, max_iter, b, x, flush, stream, args)
 
+    # secondary figure: the same solve with FP32 inner products
+    fp32 = None
+    if not args.no_adaptive:
+        fp32 = fp32_inner(rg, S, opts, w, max_iter, b, x, flush, stream, args)
+
     # secondary figure: eta chosen by the measured tuner, and the time to the
     # tolerance at every candidate (the headline keeps eta = 0.1)
     eta = None
@@ -393,6 +398,7 @@ def run_ours(args):
             "spmv": spmv,
             "adaptive_inner": adaptive,
             "eta_tuning": eta,
+            "fp32_inner": fp32,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
@@ -491,6 +497,32 @@ def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.
             "rel_diff_to_fixed_tol_x": float(torch.linalg.norm(x - x_ref) /
                                              torch.linalg.norm(x_ref)),
             "final_normal_res": st.normal_res}
+
+
+def fp32_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args):
+    """The benchmark solve with precision = FP32_INNER (the inner LSQR block
+    products in FP32), L2 flushed before each timed solve."""
+    import torch
+    s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, precision=rg.PRECISION_FP32_INNER,
+                  **opts)
+    x = torch.empty_like(x_ref)
+    rg.rgdbek_solve(s.handle, b, x, w["tol"], max_iter, 77)
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(rg.rgdbek_solve(s.handle, b, x, w["tol"], max_iter, i))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s.close()
+    return {"time_to_tol_s": statistics.median(ms) / 1e3,
+            "iters_per_solve": [t.iters for t in stats],
+            "lsqr_steps_per_solve": [t.inner_u + t.inner_j for t in stats],
+            "status": [t.status for t in stats],
+            "rel_diff_to_fp64_x": float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))}
 
 
 def eta_tuning(rg, S, opts, w, max_iter, b, flush, stream, probe_iters=20):
