@@ -315,13 +315,16 @@ def run_ours(args):
     achieved = sum(bytes_per) / total_s / 1e9
     flops_per = [algorithmic_flops(s, S.nnz) for s in stats]
     fp64_tflops = sum(flops_per) / total_s / 1e12
+    # DRAM bytes per launch: ncu's dram__bytes_read + dram__bytes_write per outer
+    # iteration of this kernel (from a short capture of the same system), times
+    # the iterations of the timed solves; null once the kernel sources changed
     traffic = None
     tp = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
         if tj.get("kernel_source_hash") == source_hash():
-            traffic = tj.get("dram_bytes_per_launch")
+            traffic = tj["dram_bytes_per_outer_iteration"] * iters / len(stats)
 
     # standalone SpMV kernels (the a1 / a5 products), L2 flushed before each launch
     spmv = spmv_rooflines(rg, solver, S, dev, flush, peak)
