@@ -468,6 +468,27 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
         t = statistics.median(ts)
         gbs = nbytes / t / 1e9
         out[name] = {"us": t * 1e6, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / peak}
+    # context: a torch copy moving the same number of bytes (half read, half
+    # written), timed the same way; the measured copy peak comes from a 4 GiB
+    # copy, which a one-shot transfer of about 50 MB after an L2 flush cannot reach
+    half = out["csr_Ax"]["algorithmic_bytes"] // 16
+    src = torch.randn(half, dtype=torch.float64, device=dev)
+    dst = torch.empty_like(src)
+    ts = []
+    for i in range(20):
+        a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(float(i))
+        torch.cuda._sleep(400000)
+        a.record(stream)
+        dst.copy_(src)
+        bb.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(bb) / 1e3)
+    t = statistics.median(ts)
+    out["same_size_copy"] = {"us": t * 1e6, "bytes": 16 * half, "GB/s": 16 * half / t / 1e9,
+                             "frac": 16 * half / t / 1e9 / peak}
+    for name in ("csr_Ax", "csc_ATz"):
+        out[name]["frac_of_same_size_copy"] = out[name]["GB/s"] / out["same_size_copy"]["GB/s"]
     return out
 
 
