@@ -98,8 +98,8 @@ void carve(rgdbek_s *h, Layout &L) {
     const long long m = h->m, n = h->n, nnz = h->nnz, mx = m > n ? m : n;
     // Work vectors indexed by rows or by columns are all max(m, n) long, so
     // that the same workspace serves the solves on A^T of rgdbek_backward.
-    h->z = L.take<double>(mx);
-    h->t = L.take<double>(mx);
+    h->z = L.take<double>(2 * mx);  // (z_i, t_i) pairs
+    h->t = h->z + 1;
     h->r = L.take<double>(mx);
     h->epsr = L.take<double>(mx);
     h->uu = L.take<double>(mx);

@@ -37,9 +37,11 @@ struct Params {
     // right-hand side and solution
     const double *b;
     double *x;
-    // work vectors: z (m), t = b - A x (m), r (m), g = A^T z (n), weights,
-    // LSQR vectors u (m), v, w, y (n), the row-step solution dx (n) and the
-    // trial iterate xt = x + dx (n) that the next column pass adopts
+    // work vectors: z (m) and t = b - A x (m), stored as (z_i, t_i) pairs
+    // (z_i at z[2 i], t_i at t[2 i] = z[2 i + 1]: the column pass gathers both
+    // with one 16-byte load), r (m), g = A^T z (n), weights, LSQR vectors u (m),
+    // v, w, y (n), the row-step solution dx (n) and the trial iterate
+    // xt = x + dx (n) that the next column pass adopts
     double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx, *xt;
     unsigned long long *Q;  // chunk-local inclusive prefix of quantised weights
     unsigned char *flag;    // drawn / selected marks
@@ -178,10 +180,11 @@ __device__ __forceinline__ double lane_dot(long long e, long long e1, long long 
     return s;
 }
 
-// Two dot products sharing the index/value loads (A^T z and A^T t).
-template <typename F, typename G>
+// Two dot products sharing the index/value loads (A^T z and A^T t): the two
+// vectors are stored as (z_i, t_i) pairs, so one 16-byte gather serves both.
 __device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L, const int *idx,
-                                          const double *val, F f, G g, double &sf, double &sg) {
+                                          const double *val, const double2 *zt, double &sf,
+                                          double &sg) {
     for (; e < e1; e += 4 * L) {
         const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
         const int i0 = __ldg(idx + e);
@@ -192,15 +195,15 @@ __device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L
         const double a1 = v1 ? __ldg(val + e + L) : 0.0;
         const double a2 = v2 ? __ldg(val + e + 2 * L) : 0.0;
         const double a3 = v3 ? __ldg(val + e + 3 * L) : 0.0;
-        const double x0 = f(i0), y0 = g(i0);
-        const double x1 = v1 ? f(i1) : 0.0, y1 = v1 ? g(i1) : 0.0;
-        const double x2 = v2 ? f(i2) : 0.0, y2 = v2 ? g(i2) : 0.0;
-        const double x3 = v3 ? f(i3) : 0.0, y3 = v3 ? g(i3) : 0.0;
-        sf = fma(a0, x0, sf);
-        sg = fma(a0, y0, sg);
-        if (v1) { sf = fma(a1, x1, sf); sg = fma(a1, y1, sg); }
-        if (v2) { sf = fma(a2, x2, sf); sg = fma(a2, y2, sg); }
-        if (v3) { sf = fma(a3, x3, sf); sg = fma(a3, y3, sg); }
+        const double2 p0 = zt[i0];
+        const double2 p1 = v1 ? zt[i1] : make_double2(0.0, 0.0);
+        const double2 p2 = v2 ? zt[i2] : make_double2(0.0, 0.0);
+        const double2 p3 = v3 ? zt[i3] : make_double2(0.0, 0.0);
+        sf = fma(a0, p0.x, sf);
+        sg = fma(a0, p0.y, sg);
+        if (v1) { sf = fma(a1, p1.x, sf); sg = fma(a1, p1.y, sg); }
+        if (v2) { sf = fma(a2, p2.x, sf); sg = fma(a2, p2.y, sg); }
+        if (v3) { sf = fma(a3, p3.x, sf); sg = fma(a3, p3.y, sg); }
     }
 }
 
@@ -268,7 +271,7 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
         double sg = 0.0, sh = 0.0;
         if (j < P.n)
             lane_dot2(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
-                      [&](int i) { return P.z[i]; }, [&](int i) { return P.t[i]; }, sg, sh);
+                      reinterpret_cast<const double2 *>(P.z), sg, sh);
         sg = group_sum(sg, G.L);
         sh = group_sum(sh, G.L);
         if (j < P.n && G.sl == 0) {
@@ -308,7 +311,7 @@ __device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
             const double ti = __ldg(P.b + i) - s;
-            P.t[i] = ti;
+            P.t[2 * i] = ti;
             tt = fma(ti, ti, tt);
         }
     }

@@ -364,7 +364,7 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot, int 
 }
 
 // LSQR from y = 0 on the block (R, C) with right-hand side c0 (u-space,
-// global), beta1 = ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in
+// global, element i at c0[i * c0s]; without v_given c0s must be 1), beta1 = ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in
 // P.vv and alpha1 is passed; otherwise it is computed first (one more
 // phase).  fro2 = ||B||_F^2.  y_g (v-space) receives the solution; with xt
 // given (the row step, v-space = x-space) also xt = x + y, so the residual
@@ -380,7 +380,7 @@ __device__ __forceinline__ double warp0_collect(const double *pd, int slot, int 
 // __syncthreads | all threads combine element-wise and form the partial.
 template <bool f32>
 __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
-                                        const double *c0, const float *c0_32, double *y_g,
+                                        const double *c0, int c0s, const float *c0_32, double *y_g,
                                         double *xt, const double *csc, const double *rsc,
                                         bool v_given,
                                         double alpha1, double beta1, double fro2,
@@ -414,7 +414,7 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = 0.0;
     } else {
         for (int i = threadIdx.x; i < nrl; i += blockDim.x) {
-            uold[i] = c0[RC.lo + i];
+            uold[i] = c0[(RC.lo + i) * c0s];
             if (rown) rown[i] = rsc[RC.lo + i];
         }
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
@@ -510,11 +510,12 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
                 const double vn = vown[li] * inv_a;
                 wown[li] = first ? vn : vn - wcoef * wown[li];
             }
-            const double *uo = st_smem ? uold : (first ? c0 : P.uu) + RC.lo;
             double acc = 0.0;
             for (int li = threadIdx.x; li < nrl; li += blockDim.x) {
                 const double rl = rloc ? rloc[li] : 1.0;
-                const double u = (rloc ? dr[li] * rl : dr[li]) * inv_a - ab * uo[li];
+                const double uo = st_smem ? uold[li]
+                                          : (first ? c0[(RC.lo + li) * c0s] : P.uu[RC.lo + li]);
+                const double u = (rloc ? dr[li] * rl : dr[li]) * inv_a - ab * uo;
                 P.uu[RC.lo + li] = u;
                 if (rloc) P.uus[RC.lo + li] = u * rl;
                 if (f32) P.uu32[RC.lo + li] = (float)(rloc ? u * rl : u);
@@ -590,9 +591,9 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
                                 [&](int p) { return P.yy[p]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
-            const double zi = P.z[i] - s;
-            P.z[i] = zi;
-            const double ri = P.t[i] - zi;
+            const double zi = P.z[2 * i] - s;
+            P.z[2 * i] = zi;
+            const double ri = P.t[2 * i] - zi;
             P.r[i] = ri;
             const double c = __ldg(P.rn2 + i);
             const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(ri, ri), c) : 0.0;
@@ -641,8 +642,8 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
         long long bad = 0;
         for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
             const double bi = __ldg(P.b + i);
-            P.z[i] = bi;
-            P.t[i] = bi;
+            P.z[2 * i] = bi;
+            P.t[2 * i] = bi;
             bb = fma(bi, bi, bb);
             if (!isfinite(bi)) bad = 1;
         }
@@ -771,7 +772,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
                 const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
                 const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr<F32>(P, rows, cols, P.z, nullptr, P.yy, nullptr, P.dsc, nullptr, true, O.alpha1, O.beta1,
+                stepsU = run_lsqr<F32>(P, rows, cols, P.z, 2, nullptr, P.yy, nullptr, P.dsc, nullptr, true, O.alpha1, O.beta1,
                                   O.fro2, dsmem, P.dsmem_bytes, S);
                 if (stepsU < 0) return;
                 mark(S, PH_COL_LSQR);
@@ -851,7 +852,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                                  pick_lanes_fp64(nnzJ, P.n)};
                 int fit = 0;
                 if (rscale) {
-                    stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt, nullptr,
+                    stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, 1, P.uu32, P.dx, P.xt, nullptr,
                                            P.dsr, false, 0.0, O.beta1s, O.fro2s, dsmem,
                                            P.dsmem_bytes, S);
                     if (stepsJ < 0) return;
@@ -869,7 +870,7 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                         for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.xt[j] = P.x[j];
                         RGD_SYNC(0, 0, 0);
                     }
-                    const int s2 = run_lsqr<F32>(P, rows, cols, P.uu, P.uu32, P.dx, P.xt,
+                    const int s2 = run_lsqr<F32>(P, rows, cols, P.uu, 1, P.uu32, P.dx, P.xt,
                                                  nullptr, nullptr, false, 0.0, O.beta1, O.fro2,
                                                  dsmem, P.dsmem_bytes, S);
                     if (s2 < 0) return;
