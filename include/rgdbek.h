@@ -232,7 +232,8 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
  * NULL) receive them; ms_out (host double[RGDBEK_BATCH_TEAM_CANDIDATES + 2],
  * may be NULL) the time of each team size and then of the 512- and
  * 1024-thread shapes (-1 where skipped).  The x buffers are overwritten by
- * the probe solves.  Returns OK or the first error. */
+ * the probe solves, which run their full length whatever the handles'
+ * time_budget_s.  Returns OK or the first error. */
 #define RGDBEK_BATCH_TEAM_CANDIDATES 8
 int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                         const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
@@ -248,8 +249,9 @@ int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *
  * stopping rule's measure (1 at x0 = 0) as -ln(measure) per second.  The
  * handle keeps the best candidate as eta_col and eta_row; *eta_out receives
  * it and rate_out (host double[ncand], may be NULL) every score.  The probe
- * is short, so the score favours the early rate of decrease.  Returns OK or
- * the first error (the options are then left as they were). */
+ * is short, so the score favours the early rate of decrease; the probes run
+ * their full length whatever the handle's time_budget_s.  Returns OK or the
+ * first error (the options are then left as they were). */
 #define RGDBEK_ETA_CANDIDATES 5
 int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candidates,
                     int ncand, int64_t probe_iters, uint64_t seed, double *eta_out,
@@ -259,7 +261,8 @@ int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candid
  * iterations from x0 = 0 on b (device, m) into x (device, n, overwritten)
  * with 512 and with 1024 threads per CTA, times each with CUDA events, and
  * sets the handle's threads_per_block to the faster.  *block_out receives it
- * and ms_out (host double[2], may be NULL) the two times.  Returns OK or the
+ * and ms_out (host double[2], may be NULL) the two times; the probes run
+ * their full length whatever the handle's time_budget_s.  Returns OK or the
  * first error (the options are then left as they were). */
 int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uint64_t seed,
                 int *block_out, double *ms_out);

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "rgdbek_internal.h"
@@ -787,11 +788,28 @@ int rgdbek_solve_batched(int nsys, rgdbek_t *hs, const double *const *b, double 
     return run_batched(nsys, hs, b, x, tol, max_iter, seed, st, team, nullptr);
 }
 
+// Time budgets of the given handles switched off for the life of the object
+// (a tuner's probes run their full length), then restored.
+struct BudgetsOff {
+    std::vector<std::pair<rgdbek_s *, double>> saved;
+    BudgetsOff(int n, rgdbek_t *hs) {
+        for (int i = 0; i < n; ++i)
+            if (hs[i]) {
+                saved.emplace_back(hs[i], hs[i]->opt.time_budget_s);
+                hs[i]->opt.time_budget_s = 0.0;
+            }
+    }
+    ~BudgetsOff() {
+        for (auto &p : saved) p.first->opt.time_budget_s = p.second;
+    }
+};
+
 int rgdbek_tune_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x,
                         const double *tol, int64_t probe_iters, uint64_t seed, int *team_out,
                         int *block_out, double *ms_out) {
     if (nsys < 1 || !hs || !b || !x || !tol || probe_iters < 1 || !team_out || !hs[0])
         return RGDBEK_ERR_INVALID_ARG;
+    const BudgetsOff budgets_off(nsys, hs);
     rgdbek_s *h0 = hs[0];
     const int grid = h0->grid;
     h0->tuned_block = 0;
@@ -843,6 +861,7 @@ int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uin
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    h->opt.time_budget_s = 0.0;  // the probes run their full length
     for (int c = 0; e == cudaSuccess && c < 2; ++c) {
         const int blk = c == 0 ? kSolveSmallThreads : kSolveMaxThreads;
         h->opt.threads_per_block = blk;
@@ -906,6 +925,7 @@ int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candid
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    h->opt.time_budget_s = 0.0;  // the probes run their full length
     for (int c = 0; e == cudaSuccess && c < ncand; ++c) {
         h->opt.eta_col = candidates[c];
         h->opt.eta_row = candidates[c];

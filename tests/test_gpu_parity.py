@@ -529,3 +529,20 @@ def test_eta_tuner(rg):
     assert np.array_equal(G.host(r3.x), G.host(r4.x))
     g.close()
     s.close()
+
+
+def test_tuners_ignore_the_time_budget(rg):
+    """A handle with a tiny time budget still tunes (the probes run their full
+    length) and keeps its budget afterwards: the next solve stops on it."""
+    S = workloads.sparse_ls(5000, 1200, 15, sigma=1e-2, seed=24)
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=0.2, eta_row=0.2, stop_rule=rg.STOP_NORMAL,
+                  time_budget_s=1e-5)
+    b = G.dev(S.b)
+    best, scores = s.tune_eta(b, candidates=(0.1, 0.3), probe_iters=5)
+    assert best in (0.1, 0.3) and all(np.isfinite(v) and v > 0 for v in scores.values())
+    x = G.dev(np.zeros(S.n))
+    block, ms = rg.rgdbek_tune(s.handle, b, x, probe_iters=3)
+    assert block in (512, 1024) and all(v > 0 for v in ms.values())
+    res = s.solve(b, tol=1e-12, max_iter=100000, seed=1, raise_on_error=False)
+    assert res.stats.status == rg.ERR_TIMEOUT
+    s.close()
