@@ -546,3 +546,18 @@ def test_tuners_ignore_the_time_budget(rg):
     res = s.solve(b, tol=1e-12, max_iter=100000, seed=1, raise_on_error=False)
     assert res.stats.status == rg.ERR_TIMEOUT
     s.close()
+
+
+@pytest.mark.parametrize("rule", [1, 3])
+def test_adaptive_inner_tolerance_lockstep_other_rules(rg, rule):
+    """The inner tolerance follows the relative residual (rule 1) or its square
+    (RSE, rule 3) on both sides: lockstep agreement on a consistent system."""
+    S = workloads.sprandn_like(3000, 800, 0.01, seed=25)
+    K = 10
+    st, counts, lists, x = _gpu_trace(rg, S, 0.3, seed=5, iters=K, rule=rule, inner_adapt=0.1)
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.3, eta_row=0.3, stop_rule=rule, tol=0.0,
+                                                inner_tol=1e-13, inner_adapt=0.1, max_iter=K,
+                                                seed=5),
+                       n=S.n, lock=lists, trace=True)
+    assert G.rel(x, ref.x) <= 1e-10
+    assert np.all(np.abs(ref.counts[:, 2:] - counts[:, 2:]) <= 1)

@@ -27,3 +27,19 @@ def test_adaptive_inner_tolerance_reaches_the_same_solutions_with_fewer_steps():
                                               inner_adapt=1.0), n=C.n)
     assert r.status == 0
     assert np.linalg.norm(r.x - C.x_true) <= 1e-9 * np.linalg.norm(C.x_true)
+
+
+def test_adaptive_inner_tolerance_under_each_stopping_rule():
+    # consistent sparse system: every rule's measure (relative residual, its
+    # square for RSE, normal-equation residual) drives the inner tolerance,
+    # and each run reaches x* with fewer LSQR steps than the fixed tolerance
+    S = workloads.sprandn_like(1500, 400, 0.02, seed=9)
+    for rule, tol in ((1, 1e-11), (2, 1e-11), (3, 1e-22)):
+        base = oracle.Options(eta_col=0.3, eta_row=0.3, stop_rule=rule, tol=tol, inner_tol=1e-13)
+        fixed = oracle.solve(S.A, S.b, base, n=S.n)
+        adapt = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.3, eta_row=0.3, stop_rule=rule,
+                                                      tol=tol, inner_tol=1e-13, inner_adapt=0.1),
+                             n=S.n)
+        assert fixed.status == 0 and adapt.status == 0, rule
+        assert np.linalg.norm(adapt.x - S.x_true) <= 1e-8 * np.linalg.norm(S.x_true), rule
+        assert adapt.inner_u + adapt.inner_j < fixed.inner_u + fixed.inner_j, rule
