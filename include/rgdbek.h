@@ -17,8 +17,9 @@
  * 3.1), which gives minimum-norm solutions: in the column step on A_U with
  * unit columns (the projection A_U A_U^+ z does not depend on the
  * least-squares solution taken), in the row step first on A^J with unit rows
- * (the same minimum-norm solution whenever the block system is consistent;
- * solved again unscaled when it is not).
+ * (the same minimum-norm solution whenever the block system is consistent,
+ * which it is in exact arithmetic since the row residual lies in range(A);
+ * solved again unscaled when LSQR finds it inconsistent at rounding level).
  *
  * Every pointer argument marked "device" is CUDA device memory of the
  * current device; "host" pointers are ordinary CPU memory.  All device work

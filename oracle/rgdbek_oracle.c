@@ -556,8 +556,10 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
                same solutions as A^J d = r_J, so LSQR from 0 returns the same
                minimum-norm d.  Only when LSQR finds it inconsistent (it stops
                on the normal-equation test, not on the residual) is the block
-               solved again unscaled, as (A^J)^+ r_J requires.  A selected row
-               has a positive weight, hence a positive norm. */
+               solved again unscaled, as (A^J)^+ r_J requires.  In exact
+               arithmetic r lies in range(A) (b - z_{k+1} is a sum of
+               projections onto it), so this happens at rounding level only.
+               A selected row has a positive weight, hence a positive norm. */
             extract_rows(rp, ci, av, nj, J, srp, sci, sav);
             double fro2 = 0.0;
             for (int64_t p = 0; p < nj; ++p) {

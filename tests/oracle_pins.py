@@ -22,6 +22,9 @@ What the facts are:
   * The Pythagoras identity ||z_{k+1} - r||^2 = ||z_k - r||^2 -
     ||P_U (z_k - r)||^2 of Eq. (5) at every iteration, with P_U computed by
     numpy pinv, and P_U r = 0.
+  * Each block update of Eq. (4) with the blocks fixed, against numpy pinv:
+    unit-scaled columns and rows, a singular row block (duplicated rows), tall
+    and rank-deficient blocks.
   * The linear rate of Theorem 2.3(a): the mean of ||z_k - r||^2/||z_0 - r||^2
     over seeds stays below gamma^k, gamma = 1 - sigma_min^2/||A||_2^2.
   * The mean iteration counts of Tables 1 and 2 (random 99%-sparse matrices,
@@ -342,6 +345,61 @@ def pin_tables_1_2(sizes=((8000, 500), (500, 8000), (8000, 1000)), seeds=10,
             assert abs(mean - paper) <= 0.2 * paper, (m, n, meth, mean, paper)
 
 
+# --------------------------------------------------------------------------
+# The two block updates of Eq. (4), one outer iteration at a time
+# --------------------------------------------------------------------------
+def _block_steps(D, b, blocks):
+    """Run the oracle with the blocks locked and compare every step with the
+    closed form z_{k+1} = z_k - A_U pinv(A_U) z_k,
+    x_{k+1} = x_k + pinv(A^J)(b_J - z_{k+1,J} - A^J x_k)."""
+    m, n = D.shape
+    res = oracle.solve(_csr(D), b, oracle.Options(max_iter=len(blocks), stop_rule=2, tol=0.0,
+                                                  inner_tol=1e-14, inner_max=2000),
+                       n=n, lock=[(np.asarray(u, np.int32), np.asarray(j, np.int32))
+                                  for u, j in blocks],
+                       trace=True, keep_iterates=True)
+    assert res.iters == len(blocks)
+    z, x = b.copy(), np.zeros(n)
+    for k, (U, J) in enumerate(blocks):
+        AU, AJ = D[:, U], D[J, :]
+        z_next = z - AU @ (np.linalg.pinv(AU, rcond=1e-12) @ z)
+        x_next = x + np.linalg.pinv(AJ, rcond=1e-12) @ (b[J] - z_next[J] - AJ @ x)
+        assert np.linalg.norm(res.zs[k + 1] - z_next) <= 1e-10 * max(np.linalg.norm(z_next), 1.0)
+        assert np.linalg.norm(res.xs[k + 1] - x_next) <= 1e-10 * max(np.linalg.norm(x_next), 1.0)
+        z, x = res.zs[k + 1], res.xs[k + 1]
+
+
+def pin_block_updates():
+    rng = np.random.default_rng(0)
+    # uneven column and row norms: the unit scalings of the inner solves matter
+    D = rng.standard_normal((40, 25)) * np.exp(rng.uniform(-2, 2, (1, 25)))
+    D *= np.exp(rng.uniform(-2, 2, (40, 1)))
+    b = rng.standard_normal(40)
+    _block_steps(D, b, [(sorted(rng.choice(25, 6, replace=False)),
+                         sorted(rng.choice(40, 10, replace=False))) for _ in range(4)])
+    # a singular row block: J holds both copies of duplicated rows (the copies
+    # scaled by 3, so unit scaling makes them identical rows); b is not in
+    # range(A), yet the block system is consistent, since r_k = (b - z_{k+1}) -
+    # A x_k lies in range(A)
+    B = rng.standard_normal((15, 30))
+    D = np.repeat(B, 2, axis=0)
+    D[1::2] *= 3.0
+    b = rng.standard_normal(30)
+    J = list(range(10))
+    _block_steps(D, b, [(sorted(rng.choice(30, 8, replace=False)), J),
+                        (sorted(rng.choice(30, 8, replace=False)),
+                         sorted(rng.choice(30, 12, replace=False)))])
+    # tall row blocks (|J| > n), full rank and rank 6
+    for (m, n), rank in (((30, 12), None), ((50, 30), 6)):
+        D = rng.standard_normal((m, n))
+        if rank is not None:
+            D = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n))
+        b = rng.standard_normal(m)
+        _block_steps(D, b, [(sorted(rng.choice(n, max(2, n // 3), replace=False)),
+                             sorted(rng.choice(m, min(m, n + 5), replace=False)))
+                            for _ in range(3)])
+
+
 ALL_PINS = [pin_philox, pin_spmv, pin_weights, pin_sample_law, pin_sample_sets, pin_greedy,
             pin_lsqr, pin_solve_min_norm, pin_one_iteration_closed_forms, pin_degenerate,
-            pin_pythagoras_eq5, pin_rate_theorem]
+            pin_pythagoras_eq5, pin_block_updates, pin_rate_theorem]

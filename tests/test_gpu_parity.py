@@ -403,11 +403,12 @@ def test_time_budget(rg):
 
 def test_inconsistent_row_blocks_take_the_unscaled_solve(rg):
     """Fat least squares with every row duplicated (rank 20 of 40 rows, b not
-    in the range): row blocks that hold both copies of a row are inconsistent,
-    so the row-scaled inner solve is rejected and the block is solved again
-    unscaled.  In lockstep the GPU makes the same decisions as the oracle
-    (equal LSQR step counts, which include both attempts), and both reach
-    pinv(A) b."""
+    in the range): row blocks that hold both copies of a row are singular;
+    their systems are consistent in exact arithmetic (the row residual lies in
+    range(A)) but only to rounding in floating point, so LSQR may reject the
+    row-scaled solve and solve the block again unscaled.  In lockstep the GPU
+    makes the same decisions as the oracle (equal LSQR step counts, which
+    include both attempts), and both reach pinv(A) b."""
     rng = np.random.default_rng(3)
     B = rng.standard_normal((20, 100))
     D = np.repeat(B, 2, axis=0)
@@ -420,8 +421,7 @@ def test_inconsistent_row_blocks_take_the_unscaled_solve(rg):
                        n=S.n, lock=lists, trace=True)
     assert G.rel(x, ref.x) <= 1e-10
     assert np.all(np.abs(ref.counts[:, 2:] - counts[:, 2:]) <= 1)
-    # some row blocks hold both copies of a row (with different residuals:
-    # an inconsistent block system)
+    # some row blocks hold both copies of a row (a singular block)
     assert any(len(set(j // 2 for j in J)) < len(J) for _, J in lists)
     st, x, ref = _solve_both(rg, S, 1e-12, rg.STOP_NORMAL, 0.5, seed=4)
     xs = np.linalg.pinv(D, rcond=1e-10) @ b
