@@ -325,8 +325,15 @@ int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g);
  * or Inf. */
 int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *eps_max);
 
+/* Largest number of draws per weight that the samplers accept: s must not
+ * exceed RGDBEK_MAX_DRAWS_PER_ENTRY * len (Algorithm 1 itself draws at most
+ * len, since eta <= 1).  Each draw costs a search over the prefix sums, so a
+ * bound on s is a bound on the time one sampling kernel can run. */
+#define RGDBEK_MAX_DRAWS_PER_ENTRY 16
+
 /* Block selection of Algorithm 1 on given weights eps (device double[len],
- * nonnegative, finite; len <= max(m, n)): s draws with probability
+ * nonnegative, finite; len <= max(m, n)): s draws (0 <= s <=
+ * RGDBEK_MAX_DRAWS_PER_ENTRY * len, else INVALID_ARG) with probability
  * eps_j / sum eps, Philox key (seed, sysid), counter (k, phase, t/4, 0);
  * the sorted distinct drawn indices go to idx (device int32[len]) and their
  * number to *count (host).  All-zero weights give an empty block.  With
@@ -347,6 +354,8 @@ int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_
  * counterpart; this is an entry point for deploying the sampler.
  *   eps    device double[len], nonnegative and finite, 1 <= len <=
  *          RGDBEK_NOALLOC_MAX_LEN (larger len: INVALID_ARG, nothing launched)
+ *   s      number of draws, 0 <= s <= RGDBEK_MAX_DRAWS_PER_ENTRY * len (else
+ *          INVALID_ARG, nothing launched)
  *   idx    device int32[len] output: the sorted distinct drawn indices
  *   count  device int64 output: their number, -1 if a weight is negative or
  *          not finite, -2 if the kernel gave up a device wait
@@ -362,7 +371,8 @@ int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_
  * must be ordered by the caller.  The first call on a device, with that
  * device current, looks up the array's device address and the launch shape
  * (cudaGetSymbolAddress, occupancy queries); make that first call before any
- * stream capture.  Returns OK, INVALID_ARG or CUDA. */
+ * stream capture.  If that look-up fails the call returns CUDA and the next
+ * call on the device tries it again.  Returns OK, INVALID_ARG or CUDA. */
 int rgdbek_sample_noalloc(const double *eps, int64_t len, int64_t s, uint64_t seed,
                           uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count,
                           void *stream);

@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import warnings
 from dataclasses import dataclass
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -487,6 +488,15 @@ def _autograd_function():
                     rank_term, options):
             solver = Solver(m, n, row_ptr, col_idx, vals.detach().contiguous(), **options)
             res = solver.solve(b.detach().contiguous(), tol=tol, max_iter=max_iter, seed=seed)
+            if res.stats.status == NOT_CONVERGED:
+                warnings.warn(f"rgdbek_lstsq: the forward solve stopped at its cap of "
+                              f"{max_iter} outer iterations before reaching tol={tol:g} "
+                              f"(normal-equation residual {res.stats.normal_res:.3e}); the "
+                              f"implicit gradient assumes a converged solution",
+                              RuntimeWarning, stacklevel=3)
+            # the handle lives as long as this graph node: every backward through
+            # it (retain_graph=True allows several) reuses it, and it is released
+            # with the node when the graph is freed (Solver.__del__)
             ctx.solver = solver
             ctx.nnz = vals.shape[0]
             ctx.adj = (adj_tol, max_iter, seed + 1, rank_term)
@@ -498,12 +508,20 @@ def _autograd_function():
         def backward(ctx, grad_x):
             b, x = ctx.saved_tensors
             adj_tol, max_iter, seed, rank_term = ctx.adj
-            gb, gv, _, _ = ctx.solver.backward(b.detach().contiguous(), x,
-                                               grad_x.contiguous(), tol=adj_tol,
-                                               max_iter=max_iter, seed=seed,
-                                               rank_term=rank_term,
-                                               want_vals=ctx.needs_input_grad[0], nnz=ctx.nnz)
-            ctx.solver.close()
+            if ctx.solver.handle is None:
+                raise RuntimeError("rgdbek_lstsq: the solver of this graph node was closed")
+            gb, gv, status, st = ctx.solver.backward(b.detach().contiguous(), x,
+                                                     grad_x.contiguous(), tol=adj_tol,
+                                                     max_iter=max_iter, seed=seed,
+                                                     rank_term=rank_term,
+                                                     want_vals=ctx.needs_input_grad[0],
+                                                     nnz=ctx.nnz)
+            if status == NOT_CONVERGED:
+                caps = [i for i, s in enumerate(st) if s.status == NOT_CONVERGED]
+                warnings.warn(f"rgdbek_lstsq: adjoint solve(s) {caps} stopped at the cap of "
+                              f"{max_iter} outer iterations before reaching tol={adj_tol:g}; "
+                              f"the gradients are those of the unconverged iterates",
+                              RuntimeWarning, stacklevel=2)
             return (gv if ctx.needs_input_grad[0] else None,
                     gb if ctx.needs_input_grad[1] else None,
                     None, None, None, None, None, None, None, None, None, None)
@@ -521,8 +539,10 @@ def rgdbek_lstsq(row_ptr, col_idx, vals, b, m: int, n: int, tol: float = 1e-10,
 
     row_ptr (int64, m+1), col_idx (int32, nnz), vals (float64, nnz) and b
     (float64, m) are CUDA tensors; gradients flow to vals (on A's pattern) and
-    to b.  Each call creates a handle for the given values; the backward pass
-    reuses it and closes it."""
+    to b.  Each call creates a handle for the given values; every backward pass
+    through the result (several with retain_graph=True) reuses it, and it is
+    released with the graph.  A solve or an adjoint solve that stops at
+    max_iter before its tolerance issues a RuntimeWarning."""
     global _LSTSQ
     if _LSTSQ is None:
         _LSTSQ = _autograd_function()

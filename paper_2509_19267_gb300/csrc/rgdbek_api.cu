@@ -1068,8 +1068,8 @@ int rgdbek_weights(rgdbek_t h, int which, const double *v, double *eps, double *
 int rgdbek_sample(rgdbek_t h, const double *eps, int64_t len, int64_t s, uint64_t seed,
                   uint64_t sysid, int64_t k, int phase, int32_t *idx, int64_t *count) {
     const long long mx = h ? (h->m > h->n ? h->m : h->n) : 0;
-    if (!h || !eps || !idx || !count || len < 1 || len > mx || s < 0 || k < 0 ||
-        (phase != 0 && phase != 1))
+    if (!h || !eps || !idx || !count || len < 1 || len > mx || s < 0 ||
+        s > (long long)RGDBEK_MAX_DRAWS_PER_ENTRY * len || k < 0 || (phase != 0 && phase != 1))
         return RGDBEK_ERR_INVALID_ARG;
     const bool greedy = h->opt.selection == RGDBEK_SELECT_GREEDY;
     const double eta = phase == 0 ? h->opt.eta_col : h->opt.eta_row;

@@ -48,15 +48,15 @@ __global__ void noalloc_count_kernel(const Ctrl *c, int64_t *count) {
 struct DeviceSetup {
     unsigned char *scratch = nullptr;  // device address of g_sample_scratch
     int grid = 0;
-    int status = RGDBEK_OK;
-    bool done = false;
+    bool done = false;                 // set only once the set-up has succeeded
 };
 
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
 // Once per device, with that device current: the scratch address and the
-// cooperative grid of the sampling kernel.
+// cooperative grid of the sampling kernel.  A failed set-up is not recorded:
+// the next call on the device tries again.
 int device_setup(DeviceSetup **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RGDBEK_ERR_CUDA;
@@ -64,22 +64,22 @@ int device_setup(DeviceSetup **out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup &d = g_setup[dev];
     if (!d.done) {
-        d.done = true;
         void *p = nullptr;
         int sms = 0;
         const int fit = sample_blocks_per_sm(kSolveMaxThreads);
         if (cudaGetSymbolAddress(&p, g_sample_scratch) != cudaSuccess || p == nullptr ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             fit < 1) {
-            d.status = RGDBEK_ERR_CUDA;
-        } else {
-            d.scratch = static_cast<unsigned char *>(p);
-            long long g = (long long)fit * sms;
-            d.grid = (int)(g > kMaxGrid ? kMaxGrid : g);
+            cudaGetLastError();  // clear the recorded error: the caller's next call must not see it
+            return RGDBEK_ERR_CUDA;
         }
+        d.scratch = static_cast<unsigned char *>(p);
+        const long long g = (long long)fit * sms;
+        d.grid = (int)(g > kMaxGrid ? kMaxGrid : g);
+        d.done = true;
     }
     *out = &d;
-    return d.status;
+    return RGDBEK_OK;
 }
 
 }  // namespace
@@ -93,6 +93,7 @@ extern "C" int rgdbek_sample_noalloc(const double *eps, int64_t len, int64_t s, 
     if (!eps || !idx || !count || s < 0 || k < 0 || (phase != 0 && phase != 1))
         return RGDBEK_ERR_INVALID_ARG;
     if (len < 1 || len > kNoAllocMaxLen) return RGDBEK_ERR_INVALID_ARG;
+    if (s > (long long)RGDBEK_MAX_DRAWS_PER_ENTRY * len) return RGDBEK_ERR_INVALID_ARG;
     DeviceSetup *d = nullptr;
     const int st = device_setup(&d);
     if (st != RGDBEK_OK) return st;

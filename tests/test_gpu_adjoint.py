@@ -210,3 +210,51 @@ def test_autograd_function_gradients_wrt_b_lambda_and_values(rg):
     rows = np.repeat(np.arange(S.m), np.diff(S.row_ptr))
     assert _rel(G.host(bb.grad), gb_d[:nb]) <= 1e-8
     assert _rel(G.host(va.grad), Gd[rows[:nnz_a], S.col_idx[:nnz_a]]) <= 1e-8
+
+
+def test_autograd_second_backward_and_handle_release(rg):
+    """A second backward through the same graph (retain_graph=True) reuses the
+    forward's handle and gives the same gradients; the handle is released with
+    the graph (no close inside backward), and a solve that stops at its cap
+    warns instead of passing silently."""
+    import gc
+    import warnings as W
+
+    import torch
+    S = workloads.deblur_regularised(16)
+    dev = "cuda"
+    rp = torch.tensor(S.row_ptr, device=dev)
+    ci = torch.tensor(S.col_idx, device=dev)
+    vals = torch.tensor(S.vals, device=dev, requires_grad=True)
+    b = torch.tensor(S.b, device=dev, requires_grad=True)
+    xt = torch.tensor(S.x_true, device=dev)
+    x = rg.rgdbek_lstsq(rp, ci, vals, b, S.m, S.n, tol=1e-12, eta_col=ETA, eta_row=ETA,
+                        stop_rule=rg.STOP_NORMAL)
+    node = x.grad_fn
+    solver = node.solver
+    assert solver.handle is not None
+    loss = ((x - xt) ** 2).sum()
+    loss.backward(retain_graph=True)
+    g1v, g1b = G.host(vals.grad).copy(), G.host(b.grad).copy()
+    assert solver.handle is not None          # still usable after the first backward
+    vals.grad = None
+    b.grad = None
+    loss.backward()
+    assert np.array_equal(G.host(vals.grad), g1v)
+    assert np.array_equal(G.host(b.grad), g1b)
+    # the graph (and with it the handle) goes away with the last reference
+    import weakref
+    ref = weakref.ref(solver)
+    del x, loss, node, solver
+    gc.collect()
+    assert ref() is None
+
+    # an iteration cap below what the tolerance needs: a warning, not silence
+    with W.catch_warnings(record=True) as caught:
+        W.simplefilter("always")
+        x2 = rg.rgdbek_lstsq(rp, ci, vals, b, S.m, S.n, tol=1e-14, max_iter=3,
+                             eta_col=ETA, eta_row=ETA, stop_rule=rg.STOP_NORMAL)
+        ((x2 - xt) ** 2).sum().backward()
+    msgs = [str(w.message) for w in caught if issubclass(w.category, RuntimeWarning)]
+    assert any("forward solve stopped at its cap" in m for m in msgs), msgs
+    assert any("adjoint solve" in m for m in msgs), msgs

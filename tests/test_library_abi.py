@@ -81,3 +81,25 @@ def test_size_limits_rejected_before_any_device_call():
     bad = rg.default_options(eta_col=1.5)
     assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 0, rp.ctypes.data, None, None, 0,
                                  ctypes.byref(bad), None) == rg.ERR_INVALID_ARG
+
+
+def test_sampler_draw_bound_rejected_before_any_device_call():
+    """s above RGDBEK_MAX_DRAWS_PER_ENTRY (16) draws per weight, or a length
+    beyond the static scratch, is refused by the argument checks, which run
+    before the allocation-free sampler touches the device (fake non-null
+    pointers are never dereferenced on this path)."""
+    gpu_util.build_library()
+    import paper_2509_19267_gb300 as rg
+    fake = ctypes.c_void_p(0x1000)
+    lib = rg._lib
+    assert lib.rgdbek_sample_noalloc(fake, 1000, 16 * 1000 + 1, 0, 0, 0, 0, fake, fake,
+                                     None) == rg.ERR_INVALID_ARG
+    assert lib.rgdbek_sample_noalloc(fake, 1000, 2**62, 0, 0, 0, 0, fake, fake,
+                                     None) == rg.ERR_INVALID_ARG
+    assert lib.rgdbek_sample_noalloc(fake, 262145, 10, 0, 0, 0, 0, fake, fake,
+                                     None) == rg.ERR_INVALID_ARG
+    assert lib.rgdbek_sample_noalloc(fake, 1000, -1, 0, 0, 0, 0, fake, fake,
+                                     None) == rg.ERR_INVALID_ARG
+    # rgdbek_sample checks the same bound after its handle check
+    assert lib.rgdbek_sample(None, fake, 1000, 16001, 0, 0, 0, 0, fake, None) \
+        == rg.ERR_INVALID_ARG
