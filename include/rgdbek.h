@@ -309,6 +309,19 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
 int rgdbek_set_trace(rgdbek_t h, int64_t *counts, int64_t count_cap, int32_t *lists,
                      int64_t list_cap);
 
+/* Records, for each of the first iters_cap outer iterations k of the next
+ * solves, the two vectors the blocks of iteration k are drawn from (Section 2,
+ * Algorithm 1), so that a caller can replay the selections on the host:
+ *   g  device double[iters_cap][n]: row k = A^T z_k, whose squares over the
+ *      squared column norms are the column weights eps^z
+ *   r  device double[iters_cap][m]: row k = b - z_{k+1} - A x_k, whose squares
+ *      over the squared row norms are the row weights eps^x
+ * Either may be NULL; both NULL turns recording off (iters_cap is then
+ * ignored).  With either given, iters_cap >= 1 (else INVALID_ARG).  The caller
+ * owns the buffers and keeps them alive while recording is on; rgdbek_solve
+ * (not the transposed or batched solves) writes them. */
+int rgdbek_set_trace_vectors(rgdbek_t h, double *g, double *r, int64_t iters_cap);
+
 /* ---- component entry points (each runs the same device code the solve
  *      kernel uses; for tests and measurement) ------------------------------ */
 

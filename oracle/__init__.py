@@ -54,7 +54,7 @@ class _Opts(ctypes.Structure):
         ("eta_col", _dbl), ("eta_row", _dbl), ("selection", ctypes.c_int),
         ("inner_tol", _dbl), ("inner_max", ctypes.c_int), ("stop_rule", ctypes.c_int),
         ("tol", _dbl), ("max_iter", _i64), ("seed", _u64), ("sysid", _u64),
-        ("warm", ctypes.c_int), ("inner_adapt", _dbl),
+        ("warm", ctypes.c_int), ("inner_adapt", _dbl), ("k0", _i64), ("z_state", _ptr),
     ]
 
 
@@ -279,10 +279,12 @@ class Result:
     lists: list | None = None          # [(U_k, J_k)]
     zs: np.ndarray | None = None
     xs: np.ndarray | None = None
+    z: np.ndarray | None = None        # z at the end of a resumed solve
 
 
 def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool = False,
-          keep_iterates: bool = False, lock: list | None = None, x0=None) -> Result:
+          keep_iterates: bool = False, lock: list | None = None, x0=None,
+          resume: tuple | None = None) -> Result:
     """Run Algorithm 1 on A = (row_ptr, col_idx, vals) with right-hand side b.
 
     trace          record |U_k|, |J_k|, LSQR step counts and the index sets
@@ -290,6 +292,11 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
     lock           list of (U_k, J_k) index arrays to use instead of sampling
                    (lockstep replay); iterations past the list sample again
     x0             initial x (a warm start; default 0)
+    resume         (x_k, z_k, k) of an earlier piece of the same solve: the solve
+                   continues from iteration k (max_iter is then the number of the
+                   last iteration, not a count) and Result.z holds z at its end, so
+                   that a solve cut into pieces computes exactly what one
+                   uninterrupted solve does
     """
     opts = opts or Options()
     rp, ci, av = _csr(A)
@@ -300,9 +307,18 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
     x = np.zeros(max(n, 1))
     if x0 is not None:
         x[:n] = np.asarray(x0, dtype=np.float64)
+    k0 = 0
+    zst = None
+    if resume is not None:
+        xr, zr, k0 = resume
+        x[:n] = np.asarray(xr, dtype=np.float64)
+        zst = np.ascontiguousarray(np.array(zr, dtype=np.float64))
+        if zst.shape != (m,):
+            raise ValueError("resume: z must have length m")
     o = _Opts(opts.eta_col, opts.eta_row, opts.selection, opts.inner_tol, opts.inner_max,
               opts.stop_rule, opts.tol, opts.max_iter, opts.seed, opts.sysid,
-              1 if x0 is not None else 0, opts.inner_adapt)
+              1 if (x0 is not None or resume is not None) else 0, opts.inner_adapt,
+              int(k0), _p(zst) if zst is not None else None)
     st = _Stats()
     tr = None
     keep = {}
@@ -337,7 +353,8 @@ def solve(A, b, opts: Options | None = None, n: int | None = None, trace: bool =
                       ctypes.byref(st), ctypes.byref(tr) if tr is not None else None)
     res = Result(x=x[:n].copy(), iters=int(st.iters), inner_u=int(st.inner_u),
                  inner_j=int(st.inner_j), rel_res=float(st.rel_res),
-                 normal_res=float(st.normal_res), rse=float(st.rse), status=int(st.status))
+                 normal_res=float(st.normal_res), rse=float(st.rse), status=int(st.status),
+                 z=zst.copy() if zst is not None else None)
     if tr is not None:
         nrec = int(tr.n_iters)
         counts = keep["counts"][:nrec].copy()

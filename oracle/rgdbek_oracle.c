@@ -375,6 +375,14 @@ typedef struct {
     double inner_adapt;       /* > 0: inner tolerance of iteration k is
                                  max(inner_tol, min(0.1, inner_adapt * r_k)),
                                  r_k the stopping rule's measure of x_k       */
+    int64_t k0;               /* number of the first iteration (0 for a fresh solve);
+                                 max_iter caps the iteration number, not the count */
+    double *z_state;          /* NULL: z_0 = b.  Otherwise z at iteration k0 on
+                                 entry (a resumed solve; x holds x_k0 with warm = 1)
+                                 and z at the last iteration on return, so that a
+                                 solve cut into pieces draws and computes exactly
+                                 what one uninterrupted solve does (the draws depend
+                                 on (seed, k) only)                             */
 } OrcOpts;
 
 typedef struct {
@@ -439,10 +447,10 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
     orc_row_norms2(m, rp, av, rn2);
     orc_col_norms2(m, n, rp, ci, av, cn2);
 
-    /* x_0 = 0 (or the given x_0), z_0 = b */
+    /* x_0 = 0 (or the given x_0), z_0 = b (or the given z of a resumed solve) */
     if (!o->warm)
         for (int64_t j = 0; j < n; ++j) x[j] = 0.0;
-    for (int64_t i = 0; i < m; ++i) z[i] = b[i];
+    for (int64_t i = 0; i < m; ++i) z[i] = o->z_state ? o->z_state[i] : b[i];
     const double bnorm = sqrt(dot(m, b, b));
     orc_spmv_t(m, n, rp, ci, av, b, h);
     const double atbnorm = sqrt(dot(n, h, h));
@@ -464,7 +472,7 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
         free(srp); free(sci); free(sav); free(bsc); free(dcol);
         return -2;
     }
-    for (k = 0;; ++k) {
+    for (k = o->k0;; ++k) {
         /* stopping test on x_k: t = b - A x_k */
         orc_spmv(m, rp, ci, av, x, Ax);
         for (int64_t i = 0; i < m; ++i) t[i] = b[i] - Ax[i];
@@ -611,6 +619,8 @@ int orc_solve(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci,
         tr->list_len = list_len;
         tr->n_iters = n_rec;
     }
+    if (o->z_state)
+        for (int64_t i = 0; i < m; ++i) o->z_state[i] = z[i];
     st->iters = k;
     st->rel_res = rel;
     st->normal_res = nrm;

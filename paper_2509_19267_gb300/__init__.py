@@ -120,6 +120,7 @@ SIGNATURES = [
     ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
                                ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
+    ("rgdbek_set_trace_vectors", _int, [_ptr, _ptr, _ptr, _i64]),
     ("rgdbek_spmv", _int, [_ptr, _ptr, _ptr]),
     ("rgdbek_spmv_t", _int, [_ptr, _ptr, _ptr]),
     ("rgdbek_weights", _int, [_ptr, _int, _ptr, _ptr, ctypes.POINTER(_dbl)]),
@@ -348,6 +349,19 @@ def rgdbek_set_trace(h: int, counts=None, lists=None) -> None:
     _check(_lib.rgdbek_set_trace(h, _dptr(counts), counts.shape[0] if counts is not None else 0,
                                  _dptr(lists), lists.shape[0] if lists is not None else 0),
            "rgdbek_set_trace")
+
+
+def rgdbek_set_trace_vectors(h: int, g=None, r=None) -> None:
+    """g: float64 CUDA tensor (cap, n) for A^T z_k; r: float64 CUDA tensor
+    (cap, m) for the row residual of iteration k; None, None turns it off."""
+    cap = 0
+    for t in (g, r):
+        if t is not None:
+            if t.dim() != 2:
+                raise ValueError("trace vectors must be 2-D (iterations, length)")
+            cap = t.shape[0] if cap == 0 else min(cap, t.shape[0])
+    _check(_lib.rgdbek_set_trace_vectors(h, _dptr(g), _dptr(r), cap),
+           "rgdbek_set_trace_vectors")
 
 
 def rgdbek_spmv(h: int, x, y) -> None:

@@ -64,6 +64,8 @@ struct rgdbek_s {
     long long tr_count_cap = 0;
     int *tr_lists = nullptr;
     long long tr_list_cap = 0;
+    double *tr_g = nullptr, *tr_r = nullptr;
+    long long tr_vec_cap = 0;
 };
 
 namespace {
@@ -228,6 +230,9 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.tr_count_cap = h->tr_count_cap;
     P.tr_lists = h->tr_lists;
     P.tr_list_cap = h->tr_list_cap;
+    P.tr_g = h->tr_g;
+    P.tr_r = h->tr_r;
+    P.tr_vec_cap = h->tr_vec_cap;
     P.eta_col = h->opt.eta_col;
     P.eta_row = h->opt.eta_row;
     P.fp32_inner = h->opt.precision == RGDBEK_PRECISION_FP32_INNER;
@@ -273,6 +278,9 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
         P.tr_count_cap = 0;
         P.tr_lists = nullptr;
         P.tr_list_cap = 0;
+        P.tr_g = nullptr;
+        P.tr_r = nullptr;
+        P.tr_vec_cap = 0;
     }
     return P;
 }
@@ -430,6 +438,9 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
         P.tr_count_cap = 0;
         P.tr_lists = nullptr;
         P.tr_list_cap = 0;
+        P.tr_g = nullptr;
+        P.tr_r = nullptr;
+        P.tr_vec_cap = 0;
         sys[i] = P;
     }
     std::vector<int> plan;
@@ -752,6 +763,14 @@ int rgdbek_set_trace(rgdbek_t h, int64_t *counts, int64_t count_cap, int32_t *li
     h->tr_count_cap = counts ? count_cap : 0;
     h->tr_lists = lists;
     h->tr_list_cap = lists ? list_cap : 0;
+    return RGDBEK_OK;
+}
+
+int rgdbek_set_trace_vectors(rgdbek_t h, double *g, double *r, int64_t iters_cap) {
+    if (!h || iters_cap < 0 || ((g || r) && iters_cap == 0)) return RGDBEK_ERR_INVALID_ARG;
+    h->tr_g = g;
+    h->tr_r = r;
+    h->tr_vec_cap = (g || r) ? iters_cap : 0;
     return RGDBEK_OK;
 }
 

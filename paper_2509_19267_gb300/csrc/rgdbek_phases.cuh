@@ -62,6 +62,8 @@ struct Params {
     long long tr_count_cap;
     int *tr_lists;
     long long tr_list_cap;
+    double *tr_g, *tr_r;    // per-iteration copies of g = A^T z_k and of r (or null)
+    long long tr_vec_cap;   // iterations those buffers hold
     // options
     double tol, inner_tol, eta_col, eta_row;
     double inner_adapt;     // > 0: per-iteration inner tolerance tied to the outer residual

@@ -692,6 +692,8 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
         phase_col(P, bs);
         RGD_SYNC(DS(D_EMAX_C) | DS(D_HH) | DS(D_GG), DS(D_EMAX_C), DS(I_BAD_C));
         mark(S, PH_COL);
+        if (P.tr_g && k < P.tr_vec_cap)  // trace: g = A^T z_k, complete after the barrier
+            for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.tr_g[k * P.n + j] = P.g[j];
         if (threadIdx.x == 0) {
             const double hh = S.red_d[D_HH];
             O.emax_c = S.red_d[D_EMAX_C];
@@ -783,6 +785,8 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
         phase_zupdate(P, nU > 0, Lsub_u, bs);
         RGD_SYNC(DS(D_EMAX_R) | DS(D_ZZ), DS(D_EMAX_R), DS(I_BAD_R));
         mark(S, PH_ZUPD);
+        if (P.tr_r && k < P.tr_vec_cap)  // trace: the row residual r = b - z_{k+1} - A x_k
+            for (long long i = tthread(P); i < P.m; i += tthreads(P)) P.tr_r[k * P.m + i] = P.r[i];
         if (threadIdx.x == 0) {
             O.emax_r = S.red_d[D_EMAX_R];
             O.zz = S.red_d[D_ZZ];

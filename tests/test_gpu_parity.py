@@ -553,11 +553,15 @@ def test_adaptive_inner_tolerance_lockstep_other_rules(rg, rule):
     """The inner tolerance follows the relative residual (rule 1) or its square
     (RSE, rule 3) on both sides: over 10 lockstep iterations of a consistent
     system the GPU and the oracle take the same LSQR step counts (the
-    decisions τ_k drives), and after 5 iterations x agrees to 1e-10.  Later
-    row solves under the RSE rule stop after 20-40 LSQR steps at a loose
-    tolerance, before LSQR has converged; there rounding differences between
-    the two implementations grow with the loss of orthogonality (about 1e-5
-    after 10 iterations with identical step counts), so x is compared early."""
+    decisions tau_k drives) and x agrees.  Under rule 1 the bar is 1e-10
+    after 10 iterations.  Under the RSE rule later row solves stop after
+    20-40 LSQR steps at a loose tolerance, before LSQR has converged, and
+    there the Krylov recurrence amplifies rounding: two CPU builds of the
+    oracle that differ only in the order of their dot-product sums drift
+    apart by 1.15e-5 after 10 iterations with identical step counts
+    (tests/test_oracle_rounding_drift.py).  So under rule 3 x is held to
+    1e-10 after 5 iterations and to 1e-4 (ten times that CPU-to-CPU drift)
+    after 10."""
     S = workloads.sprandn_like(3000, 800, 0.01, seed=25)
 
     def both(K):
@@ -569,7 +573,50 @@ def test_adaptive_inner_tolerance_lockstep_other_rules(rg, rule):
                            n=S.n, lock=lists, trace=True)
         return counts, x, ref
 
-    counts, _, ref = both(10)
+    counts, x10, ref = both(10)
     assert np.all(np.abs(ref.counts[:, 2:] - counts[:, 2:]) <= 1)
-    _, x, ref = both(5)
-    assert G.rel(x, ref.x) <= 1e-10
+    d10 = G.rel(x10, ref.x)
+    print(f"rule {rule}: |x_gpu - x_oracle| / |x_oracle| after 10 lockstep iterations = {d10:.3e}")
+    assert d10 <= (1e-10 if rule == 1 else 1e-4), d10
+    _, x5, ref5 = both(5)
+    assert G.rel(x5, ref5.x) <= 1e-10
+
+
+def _replay(rg, blocks, g, r, rn2, cn2, eta_c, eta_r, seed, sysid=0, greedy=False):
+    """Replays every iteration's selections on the host (SURVEY's bit-exact
+    replay): the oracle's weights on the GPU's own g_k and r_k and the GPU's
+    squared norms, then the oracle's sampler (or greedy threshold) with the
+    same Philox key and counter; each block must equal the GPU's byte for
+    byte."""
+    for k, (U, J) in enumerate(blocks):
+        ec, emax_c, bad_c = oracle.weights(g[k], cn2)
+        er, emax_r, bad_r = oracle.weights(r[k], rn2)
+        assert not bad_c and not bad_r
+        if greedy:
+            Ur = oracle.select_greedy(ec, eta_c, emax_c)
+            Jr = oracle.select_greedy(er, eta_r, emax_r)
+        else:
+            Ur = oracle.sample(ec, oracle.num_draws(eta_c, len(ec)), seed, sysid, k, 0, emax_c)
+            Jr = oracle.sample(er, oracle.num_draws(eta_r, len(er)), seed, sysid, k, 1, emax_r)
+        assert Ur.dtype == U.dtype and Ur.tobytes() == U.tobytes(), f"U_{k} differs"
+        assert Jr.dtype == J.dtype and Jr.tobytes() == J.tobytes(), f"J_{k} differs"
+
+
+@pytest.mark.parametrize("selection", [0, 1])
+def test_selection_replay_over_a_whole_run(rg, selection):
+    """Every block of 20 outer iterations (not only the first few) is what the
+    oracle's sampler draws when it is replayed on the GPU's own column and row
+    residuals g_k = A^T z_k, r_k = b - z_{k+1} - A x_k and the same Philox
+    counter (k, phase): the quantised weights, the prefix sums, the draws and
+    the compaction are bit-exact on both sides.  Random (Algorithm 1) and
+    greedy (GDBEK) selection."""
+    S = workloads.sparse_ls(6000, 1500, 20, sigma=1e-2, seed=31)
+    eta = 0.1 if selection == 0 else 0.5
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=eta, eta_row=eta, stop_rule=rg.STOP_NORMAL,
+                  selection=selection)
+    rn2, cn2 = G.gpu_norms(rg, s, S)
+    st, counts, blocks, g, r, _ = G.traced_solve(rg, s, S, 20, seed=17)
+    s.close()
+    assert st.iters == 20 and len(blocks) == 20
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(r))
+    _replay(rg, blocks, g, r, rn2, cn2, eta, eta, seed=17, greedy=selection == 1)
