@@ -565,8 +565,10 @@ def adaptive_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args, c=0.
 
 
 def fp32_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args):
-    """The benchmark solve with precision = FP32_INNER (the inner LSQR block
-    products in FP32), L2 flushed before each timed solve."""
+    """The benchmark solve with precision = FP32_INNER: Algorithm 1 in FP32
+    (float A values, vectors, weights, LSQR with Kahan dots) inside FP64
+    iterative refinement, to the same FP64 normal-equation residual, L2
+    flushed before each timed solve."""
     import torch
     s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, precision=rg.PRECISION_FP32_INNER,
                   **opts)
@@ -583,10 +585,16 @@ def fp32_inner(rg, S, opts, w, max_iter, b, x_ref, flush, stream, args):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     s.close()
+    st = stats[-1]
     return {"time_to_tol_s": statistics.median(ms) / 1e3,
             "iters_per_solve": [t.iters for t in stats],
+            "refinements_per_solve": [t.refinements for t in stats],
             "lsqr_steps_per_solve": [t.inner_u + t.inner_j for t in stats],
             "status": [t.status for t in stats],
+            "final_normal_res": st.normal_res,
+            "phase_ms": {k: round(v, 3) for k, v in st.as_dict()["phase_ms"].items()},
+            "us_per_grid_phase": 1e6 * statistics.median(ms) / 1e3 / max(
+                1, 14 * st.iters + 2 * (st.inner_u + st.inner_j) + 4 * st.refinements),
             "rel_diff_to_fp64_x": float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))}
 
 

@@ -56,18 +56,26 @@ extern "C" {
 #define RGDBEK_STOP_NORMAL 2   /* ||A^T (b - A x)|| / ||A^T b|| <= tol            */
 #define RGDBEK_STOP_RSE 3      /* ||A x - b||^2 / ||b||^2 <= tol (Section 3.1)    */
 
-/* ---- arithmetic of the inner solves --------------------------------------- */
+/* ---- arithmetic of the solve ------------------------------------------------ */
 #define RGDBEK_PRECISION_FP64 0  /* everything in FP64                          */
-/* The inner LSQR products B v and B^T u run in FP32: the block's values are
- * held as float, the gathered vectors as float copies, and each dot product
- * accumulates with Kahan compensation.  The outer iteration stays FP64 (the
- * products A^T z and b - A x, the norms, weights, LSQR scalars and vectors,
- * and the stopping test), so it refines the FP32 block solves: the limit and
- * the stopping rule are those of the FP64 solve.  The inner tolerance is
- * raised to at least RGDBEK_FP32_INNER_TOL, below which FP32 products carry
- * no information. */
+/* FP32 inner iterations wrapped in FP64 iterative refinement.  Every update
+ * of x lies in range(A^T), so A^+ (b - A x) = x* - x for the limit x* = A^+ b
+ * (Theorem 2.3): the solve repeats, in FP64,
+ *   t = b - A x, ||A^T t||, the stopping test on x
+ * and then runs Algorithm 1 entirely in FP32 (A's values rounded to float,
+ * float vectors, weights, sampling, LSQR with Kahan-compensated dot
+ * products) on A d = t / ||t|| from d = 0, to the stopping rule's relative
+ * measure tau = min(0.5, max(RGDBEK_FP32_REFINE_TOL_MIN, 0.5 tol / measure))
+ * or until that inner solve stops making progress, and adds ||t|| d to x in
+ * FP64.  The returned x, the stopping rule and its tolerance are FP64; the
+ * limit is A^+ b up to FP64 rounding when A has full column rank.  With a
+ * nontrivial null space, FP32 rounding leaves components in it that no
+ * refinement removes (relative size about 1e-7).  The inner LSQR tolerance
+ * is raised to at least RGDBEK_FP32_INNER_TOL.  stats.iters counts the outer
+ * iterations of all inner solves, stats.refinements the FP64 steps. */
 #define RGDBEK_PRECISION_FP32_INNER 1
 #define RGDBEK_FP32_INNER_TOL 1e-6
+#define RGDBEK_FP32_REFINE_TOL_MIN 1e-5
 
 typedef struct rgdbek_s *rgdbek_t;
 
@@ -118,14 +126,15 @@ typedef struct {
     /* device time (ms, globaltimer of CTA 0) spent per phase kind, in the order
      * of RGDBEK_PHASE_NAMES: set-up, column pass, column selection, A_U
      * extraction, LSQR on A_U, z update, row selection, A^J extraction, LSQR on
-     * A^J, residual pass */
-    double phase_ms[10];
+     * A^J, residual pass, and the FP64 refinement steps of the FP32 form */
+    double phase_ms[11];
+    int64_t refinements; /* FP64 refinement steps (RGDBEK_PRECISION_FP32_INNER)   */
 } rgdbek_stats;
 
-#define RGDBEK_NUM_PHASES 10
+#define RGDBEK_NUM_PHASES 11
 #define RGDBEK_PHASE_NAMES                                                            \
     "setup", "col_pass", "col_select", "col_extract", "col_lsqr", "z_update", "row_select", \
-        "row_extract", "row_lsqr", "residual_pass"
+        "row_extract", "row_lsqr", "residual_pass", "refine"
 
 typedef struct {
     int64_t m, n, nnz;

@@ -51,10 +51,11 @@ STOP_REL_RES = 1
 STOP_NORMAL = 2
 STOP_RSE = 3
 PHASE_NAMES = ("setup", "col_pass", "col_select", "col_extract", "col_lsqr", "z_update",
-               "row_select", "row_extract", "row_lsqr", "residual_pass")
+               "row_select", "row_extract", "row_lsqr", "residual_pass", "refine")
 PRECISION_FP64 = 0
-PRECISION_FP32_INNER = 1
+PRECISION_FP32_INNER = 1          # FP32 inner RGDBEK inside FP64 iterative refinement
 FP32_INNER_TOL = 1e-6
+FP32_REFINE_TOL_MIN = 1e-5
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -77,7 +78,7 @@ class rgdbek_stats(ctypes.Structure):
         ("iters", _i64), ("inner_u", _i64), ("inner_j", _i64), ("sum_nu", _i64), ("sum_nj", _i64),
         ("sum_nnz_u", _i64), ("sum_nnz_j", _i64), ("lsqr_nnz_u", _i64), ("lsqr_nnz_j", _i64),
         ("lsqr_n_u", _i64), ("lsqr_n_j", _i64), ("rel_res", _dbl), ("normal_res", _dbl),
-        ("rse", _dbl), ("status", _int), ("phase_ms", _dbl * 10),
+        ("rse", _dbl), ("status", _int), ("phase_ms", _dbl * 11), ("refinements", _i64),
     ]
 
     def as_dict(self) -> dict:

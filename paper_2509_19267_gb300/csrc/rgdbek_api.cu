@@ -20,6 +20,10 @@ struct MatrixStore {
     void *mem = nullptr;
     size_t bytes = 0;
     std::atomic<int> refs{1};
+    // A's values and squared norms rounded to float, for the FP32 form: made
+    // by the first FP32 solve on any handle that shares this matrix
+    void *mem32 = nullptr;
+    float *av32 = nullptr, *cv32 = nullptr, *rn2f = nullptr, *cn2f = nullptr;
 };
 
 struct rgdbek_s {
@@ -44,10 +48,14 @@ struct rgdbek_s {
     int *sci, *sri;
     double *sav, *scv;
     double *dots, *dots2;
-    float *vv32, *uu32;
     double *vvs, *dsc, *yh, *uus, *dsr;
     double *pd;
     long long *pi;
+    // float work vectors of the FP32 form's inner solves (each max(m, n) long;
+    // f_z holds the (z_i, t_i) pairs); the extracted block values share the
+    // FP64 arrays sav / scv, which the FP32 form does not otherwise use
+    float *f_z, *f_r, *f_g, *f_epsc, *f_epsr, *f_uu, *f_vv, *f_ww, *f_yy, *f_dx, *f_xt, *f_x, *f_b;
+    float *f_dots, *f_dots2, *f_vvs, *f_dsc, *f_yh, *f_uus, *f_dsr, *f_pd;
     Ctrl *ctrl;
     double *b_stage, *x_stage;
     // implicit adjoint scratch, allocated by the first rgdbek_backward call:
@@ -127,8 +135,6 @@ void carve(rgdbek_s *h, Layout &L) {
     h->scv = L.take<double>(nnz);
     h->dots = L.take<double>(mx);
     h->dots2 = L.take<double>(mx);
-    h->vv32 = L.take<float>(mx);
-    h->uu32 = L.take<float>(mx);
     h->vvs = L.take<double>(mx);
     h->dsc = L.take<double>(mx);
     h->yh = L.take<double>(mx);
@@ -136,6 +142,13 @@ void carve(rgdbek_s *h, Layout &L) {
     h->dsr = L.take<double>(mx);
     h->pd = L.take<double>((long long)D_NSLOTS * kMaxGrid);
     h->pi = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
+    h->f_z = L.take<float>(2 * mx);
+    float **fv[] = {&h->f_r,  &h->f_g,    &h->f_epsc, &h->f_epsr, &h->f_uu,  &h->f_vv,
+                    &h->f_ww, &h->f_yy,   &h->f_dx,   &h->f_xt,   &h->f_x,   &h->f_b,
+                    &h->f_dots, &h->f_dots2, &h->f_vvs, &h->f_dsc, &h->f_yh, &h->f_uus,
+                    &h->f_dsr};
+    for (float **p : fv) *p = L.take<float>(mx);
+    h->f_pd = L.take<float>((long long)D_NSLOTS * kMaxGrid);
     h->ctrl = L.take<Ctrl>(1);
     h->b_stage = L.take<double>(m);
     h->x_stage = L.take<double>(n);
@@ -235,14 +248,11 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.tr_vec_cap = h->tr_vec_cap;
     P.eta_col = h->opt.eta_col;
     P.eta_row = h->opt.eta_row;
-    P.fp32_inner = h->opt.precision == RGDBEK_PRECISION_FP32_INNER;
+    P.precision = h->opt.precision;
     P.warm = h->opt.warm_start != 0;
     P.inner_adapt = h->opt.inner_adapt;
-    P.inner_tol = P.fp32_inner && h->opt.inner_tol < RGDBEK_FP32_INNER_TOL
-                      ? RGDBEK_FP32_INNER_TOL
-                      : h->opt.inner_tol;
-    P.vv32 = h->vv32;
-    P.uu32 = h->uu32;
+    P.inner_tol = h->opt.inner_tol;
+    P.k0 = 0;
     P.vvs = h->vvs;
     P.dsc = h->dsc;
     P.yh = h->yh;
@@ -285,6 +295,127 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     return P;
 }
 
+// The FP32 view of the same system for the inner solves of the FP32 form:
+// A's values and norms rounded to float (the matrix store's copies, which
+// ensure_f32_matrix makes), float work vectors, and everything else shared
+// with the FP64 view P (indices, selection scratch, int64 partials, control
+// block, trace).  The inner solves start from d = 0 on their own right-hand
+// side f_b and take the inner LSQR tolerance no lower than
+// RGDBEK_FP32_INNER_TOL.
+ParamsF make_params_f(const rgdbek_s *h, const Params &P, bool transposed) {
+    ParamsF F{};
+    const MatrixStore *M = h->mat;
+    F.m = P.m;
+    F.n = P.n;
+    F.nnz = P.nnz;
+    F.rp = P.rp;
+    F.ci = P.ci;
+    F.cp = P.cp;
+    F.ri = P.ri;
+    F.av = transposed ? M->cv32 : M->av32;
+    F.cv = transposed ? M->av32 : M->cv32;
+    F.rn2 = transposed ? M->cn2f : M->rn2f;
+    F.cn2 = transposed ? M->rn2f : M->cn2f;
+    F.b = h->f_b;
+    F.x = h->f_x;
+    F.z = h->f_z;
+    F.t = h->f_z + 1;
+    F.r = h->f_r;
+    F.g = h->f_g;
+    F.epsc = h->f_epsc;
+    F.epsr = h->f_epsr;
+    F.uu = h->f_uu;
+    F.vv = h->f_vv;
+    F.ww = h->f_ww;
+    F.yy = h->f_yy;
+    F.dx = h->f_dx;
+    F.xt = h->f_xt;
+    F.Q = P.Q;
+    F.flag = P.flag;
+    F.colpos = P.colpos;
+    F.rowpos = P.rowpos;
+    F.ulist = P.ulist;
+    F.jlist = P.jlist;
+    F.srn = P.srn;
+    F.sci = P.sci;
+    F.sav = reinterpret_cast<float *>(h->sav);
+    F.scn = P.scn;
+    F.sri = P.sri;
+    F.scv = reinterpret_cast<float *>(h->scv);
+    F.dots = h->f_dots;
+    F.dots2 = h->f_dots2;
+    F.pd = h->f_pd;
+    F.pi = P.pi;
+    F.ctrl = P.ctrl;
+    F.tr_counts = P.tr_counts;
+    F.tr_count_cap = P.tr_count_cap;
+    F.tr_lists = P.tr_lists;
+    F.tr_list_cap = P.tr_list_cap;
+    F.tr_g = P.tr_g;
+    F.tr_r = P.tr_r;
+    F.tr_vec_cap = P.tr_vec_cap;
+    F.tol = P.tol;
+    F.inner_tol = P.inner_tol < RGDBEK_FP32_INNER_TOL ? RGDBEK_FP32_INNER_TOL : P.inner_tol;
+    F.eta_col = P.eta_col;
+    F.eta_row = P.eta_row;
+    F.inner_adapt = P.inner_adapt;
+    F.time_budget_ns = P.time_budget_ns;
+    F.max_iter = P.max_iter;
+    F.s_col = P.s_col;
+    F.s_row = P.s_row;
+    F.k0 = 0;
+    F.seed = P.seed;
+    F.sysid = P.sysid;
+    F.inner_max = P.inner_max;
+    F.stop_rule = P.stop_rule;
+    F.selection = P.selection;
+    F.precision = P.precision;
+    F.team = P.team;
+    F.warm = 0;
+    F.vvs = h->f_vvs;
+    F.dsc = h->f_dsc;
+    F.yh = h->f_yh;
+    F.uus = h->f_uus;
+    F.dsr = h->f_dsr;
+    F.tpr = P.tpr;
+    F.tpc = P.tpc;
+    F.ipr = P.ipr;
+    F.ipc = P.ipc;
+    F.dsmem_bytes = P.dsmem_bytes;
+    return F;
+}
+
+// The float copies of A's values and squared norms for the FP32 form, made
+// once per matrix (and shared by the handles that share it).
+int ensure_f32_matrix(rgdbek_s *h) {
+    MatrixStore *M = h->mat;
+    if (M->mem32) return RGDBEK_OK;
+    Layout L;
+    for (int pass = 0; pass < 2; ++pass) {
+        M->av32 = L.take<float>(h->nnz);
+        M->cv32 = L.take<float>(h->nnz);
+        M->rn2f = L.take<float>(h->m);
+        M->cn2f = L.take<float>(h->n);
+        if (pass == 0) {
+            void *p = nullptr;
+            const cudaError_t e = cudaMalloc(&p, L.off);
+            if (e != cudaSuccess) {
+                M->av32 = M->cv32 = M->rn2f = M->cn2f = nullptr;
+                return e == cudaErrorMemoryAllocation ? RGDBEK_ERR_OOM : RGDBEK_ERR_CUDA;
+            }
+            M->mem32 = p;
+            L = Layout();
+            L.base = static_cast<char *>(p);
+        }
+    }
+    cudaError_t e = launch_to_float(h->av, h->nnz, M->av32, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->cv, h->nnz, M->cv32, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->rn2, h->m, M->rn2f, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->cn2, h->n, M->cn2f, h->stream);
+    if (e != cudaSuccess) return RGDBEK_ERR_CUDA;
+    return RGDBEK_OK;
+}
+
 // ceil(eta * len) draws, at least one (Algorithm 1 selects eta*n columns)
 long long num_draws(double eta, long long len) {
     if (len <= 0) return 0;
@@ -322,8 +453,15 @@ int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double t
     P.seed = seed;
     P.s_col = num_draws(h->opt.eta_col, P.n);
     P.s_row = num_draws(h->opt.eta_row, P.m);
+    ParamsF F{};
+    if (P.precision == RGDBEK_PRECISION_FP32_INNER) {
+        const int st32 = ensure_f32_matrix(h);
+        if (st32 != RGDBEK_OK) return st32;
+        P.team = h->grid;
+        F = make_params_f(h, P, transposed);
+    }
     cudaError_t e = launch_reset_ctrl(h->ctrl, h->stream);
-    if (e == cudaSuccess) e = launch_solve(P, h->grid, h->block, h->stream);
+    if (e == cudaSuccess) e = launch_solve(P, F, h->grid, h->block, h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     int rs = read_ctrl(h);
     if (rs != RGDBEK_OK) return rs;
@@ -351,6 +489,7 @@ void fill_stats(const Ctrl &c, int status, rgdbek_stats *st) {
         st->rse = c.rse;
         st->status = status;
         for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
+        st->refinements = c.refinements;
     }
 }
 
@@ -422,8 +561,13 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
     const long long gmax = std::min((long long)kMaxGrid, (long long)fit * h0->num_sms);
     if (team > gmax) return RGDBEK_ERR_INVALID_ARG;
     const int nteams = (int)(gmax / team);
-    std::vector<Params> sys(nsys);
+    const bool f32 = h0->opt.precision == RGDBEK_PRECISION_FP32_INNER;
+    std::vector<SysPair> sys(nsys);
     for (int i = 0; i < nsys; ++i) {
+        if (f32) {
+            const int st32 = ensure_f32_matrix(hs[i]);
+            if (st32 != RGDBEK_OK) return st32;
+        }
         Params P = make_params(hs[i]);
         P.b = b[i];
         P.x = x[i];
@@ -441,12 +585,13 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
         P.tr_g = nullptr;
         P.tr_r = nullptr;
         P.tr_vec_cap = 0;
-        sys[i] = P;
+        sys[i].p = P;
+        sys[i].f = f32 ? make_params_f(hs[i], P, false) : ParamsF{};
     }
     std::vector<int> plan;
     int stride = 1;
     plan_batch(nsys, hs, nteams, plan, stride);
-    const size_t sys_bytes = (sizeof(Params) * nsys + 255) & ~(size_t)255;
+    const size_t sys_bytes = (sizeof(SysPair) * nsys + 255) & ~(size_t)255;
     const size_t plan_bytes = (sizeof(int) * plan.size() + 255) & ~(size_t)255;
     const size_t ctrl_bytes = sizeof(Ctrl) * nsys;
     char *dev = nullptr;
@@ -459,22 +604,21 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
         e = cudaEventCreate(&ev0);
         if (e == cudaSuccess) e = cudaEventCreate(&ev1);
     }
-    Params *sys_dev = reinterpret_cast<Params *>(dev);
+    SysPair *sys_dev = reinterpret_cast<SysPair *>(dev);
     int *plan_dev = reinterpret_cast<int *>(dev + sys_bytes);
     Ctrl *ctrl_dev = reinterpret_cast<Ctrl *>(dev + sys_bytes + plan_bytes);
     // the handles' own streams must have finished their earlier work
     for (int i = 0; e == cudaSuccess && i < nsys; ++i)
         if (hs[i]->stream != s) e = cudaStreamSynchronize(hs[i]->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sys_dev, sys.data(), sizeof(Params) * nsys, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(sys_dev, sys.data(), sizeof(SysPair) * nsys, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(plan_dev, plan.data(), sizeof(int) * plan.size(),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_reset_ctrls(sys_dev, nsys, s);
     if (e == cudaSuccess && ms) e = cudaEventRecord(ev0, s);
     if (e == cudaSuccess)
-        e = launch_solve_batched(sys_dev, plan_dev, stride, team, nteams,
-                                 h0->opt.precision == RGDBEK_PRECISION_FP32_INNER, block, s);
+        e = launch_solve_batched(sys_dev, plan_dev, stride, team, nteams, f32, block, s);
     if (e == cudaSuccess && ms) e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess) e = launch_gather_ctrls(sys_dev, nsys, ctrl_dev, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, ctrl_dev, ctrl_bytes, cudaMemcpyDeviceToHost, s);
@@ -503,6 +647,7 @@ void release(rgdbek_s *h) {
     if (h->arena) cudaFree(h->arena);
     if (h->mat && h->mat->refs.fetch_sub(1) == 1) {
         if (h->mat->mem) cudaFree(h->mat->mem);
+        if (h->mat->mem32) cudaFree(h->mat->mem32);
         delete h->mat;
     }
     if (h->ctrl_host) cudaFreeHost(h->ctrl_host);

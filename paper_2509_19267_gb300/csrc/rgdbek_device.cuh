@@ -68,6 +68,7 @@ struct Ctrl {
     double emax_out;         // maximum returned by the standalone weights kernel
     int bad_out;
     int pad3[15];
+    long long refinements;   // FP64 refinement steps of the FP32 form
 };
 
 // ---------------------------------------------------------------------------
@@ -150,6 +151,10 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
     return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
 }
 
+__device__ __forceinline__ float max_nonneg(float a, float b) {
+    return __int_as_float(max(__float_as_int(a), __float_as_int(b)));
+}
+
 // maximum over the warp of nonnegative finite doubles (integer compare of the
 // bit patterns, which order like the values; no FP64 instructions)
 __device__ __forceinline__ double warp_max(double v) {
@@ -157,6 +162,12 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(kFull, b, o));
     return __longlong_as_double(b);
+}
+__device__ __forceinline__ float warp_max(float v) {
+    int b = __float_as_int(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(kFull, b, o));
+    return __int_as_float(b);
 }
 // sum over the L consecutive lanes of a group (L a power of two, <= 32); all
 // 32 lanes must call it
@@ -170,6 +181,7 @@ struct BlockScratch {
     double d[34];
     long long i[34];
     unsigned long long u[34];
+    float f[34];
     double big[kMaxThreads];      // one partial per thread (FP64 block sums)
     double mid[kMaxThreads / 4];  // first level of the FP64 block-sum tree
 };
@@ -184,6 +196,8 @@ template <>
 __device__ __forceinline__ unsigned long long *scratch_of<unsigned long long>(BlockScratch &s) {
     return s.u;
 }
+template <>
+__device__ __forceinline__ float *scratch_of<float>(BlockScratch &s) { return s.f; }
 
 // Integer block sum: warp shuffles, then warp 0 over the warp totals.
 template <typename T>
@@ -250,6 +264,25 @@ __device__ __forceinline__ double block_max(double v, BlockScratch &bs) {
     return __longlong_as_double(bs.i[32]);
 }
 
+// The same for nonnegative finite floats (bit patterns compared as integers).
+__device__ __forceinline__ float block_max(float v, BlockScratch &bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int b = __float_as_int(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(kFull, b, o));
+    __syncthreads();
+    if (lane == 0) bs.i[warp] = b;
+    __syncthreads();
+    if (warp == 0) {
+        int r = lane < nw ? (int)bs.i[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(kFull, r, o));
+        if (lane == 0) bs.i[32] = r;
+    }
+    __syncthreads();
+    return __int_as_float((int)bs.i[32]);
+}
+
 // Exclusive scan of one value per thread in thread order; *total gets the sum.
 template <typename T>
 __device__ __forceinline__ T block_excl_scan(T v, BlockScratch &bs, T *total) {
@@ -283,20 +316,21 @@ __device__ __forceinline__ T block_excl_scan(T v, BlockScratch &bs, T *total) {
 // w-th requested slot (sums in a fixed order; maxima for slots in dmax), and
 // the results land in out_d[slot] / out_i[slot] for every thread.  dmask /
 // imask select double / int64 slots (bit = slot).
-__device__ __forceinline__ void collect_partials(const double *pd, const long long *pi, int nb,
+template <typename V>
+__device__ __forceinline__ void collect_partials(const V *pd, const long long *pi, int nb,
                                                  unsigned dmask, unsigned dmax, unsigned imask,
-                                                 double *out_d, long long *out_i) {
+                                                 V *out_d, long long *out_i) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int w = 0;
     for (int slot = 0; slot < D_NSLOTS; ++slot) {
         if (!(dmask >> slot & 1u)) continue;
         if (warp == w) {
-            const double *p = pd + slot * nb;
+            const V *p = pd + slot * nb;
             const bool mx = dmax >> slot & 1u;
-            double s = 0.0;
+            V s = V(0);
 #pragma unroll 8
             for (int i = lane; i < nb; i += 32) {
-                const double v = __ldcg(p + i);
+                const V v = __ldcg(p + i);
                 s = mx ? max_nonneg(s, v) : s + v;
             }
             s = mx ? warp_max(s) : warp_sum(s);

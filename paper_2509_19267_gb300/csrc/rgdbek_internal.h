@@ -26,23 +26,34 @@ inline int auto_solve_block(long long m, long long n, int ctas) {
 // dynamic shared memory of a solve CTA: its chunk of the inner-solve block
 constexpr int kSolveDsmemBytes = 96 * 1024;
 
+// One system of a batch: its FP64 view and (for the FP32 form) its FP32 view.
+struct SysPair {
+    Params p;
+    ParamsF f;
+};
+
 // control block to its pre-launch state (status = kStatusRunning)
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
-// persistent solve (cooperative launch); returns the launch error
-cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s);
+// persistent solve (cooperative launch); returns the launch error.  FP64
+// solve, or (P.precision == RGDBEK_PRECISION_FP32_INNER) the FP64 refinement
+// loop around FP32 inner solves on the FP32 view F.
+cudaError_t launch_solve(const Params &P, const ParamsF &F, int grid, int block, cudaStream_t s);
 // batched solve: nteams * team CTAs (cooperative launch); sys_dev holds one
-// Params per system (team already set), plan_dev[t * stride + q] the q-th
+// SysPair per system (team already set), plan_dev[t * stride + q] the q-th
 // system of team t (-1 ends a team's list)
-cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int stride, int team,
+cudaError_t launch_solve_batched(const SysPair *sys_dev, const int *plan_dev, int stride, int team,
                                  int nteams, bool fp32, int block, cudaStream_t s);
-// the solve kernels of one shape (small: the 512-thread launch bound)
+// the solve kernels of one shape (small: the 512-thread launch bound); fp32:
+// the refinement kernel of the FP32 form
 const void *solve_kernel_fn(bool fp32, bool small);
 const void *batched_kernel_fn(bool fp32, bool small);
 const void *solve_kernel_fn_small(bool fp32);      // rgdbek_solve512.cu
 const void *batched_kernel_fn_small(bool fp32);
 // control blocks of a batch: reset before the launch, gathered after it
-cudaError_t launch_reset_ctrls(const Params *sys_dev, int nsys, cudaStream_t s);
-cudaError_t launch_gather_ctrls(const Params *sys_dev, int nsys, Ctrl *out, cudaStream_t s);
+cudaError_t launch_reset_ctrls(const SysPair *sys_dev, int nsys, cudaStream_t s);
+cudaError_t launch_gather_ctrls(const SysPair *sys_dev, int nsys, Ctrl *out, cudaStream_t s);
+// out[i] = (float)in[i], round to nearest
+cudaError_t launch_to_float(const double *in, long long len, float *out, cudaStream_t s);
 // standalone sampler on given weights (cooperative launch)
 cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
                           long long s, unsigned long long seed, unsigned long long sysid,

@@ -10,10 +10,10 @@
 namespace rgd {
 
 // Resets the control blocks of a batch (one thread each).
-__global__ void reset_ctrls_kernel(const Params *sys, int nsys) {
+__global__ void reset_ctrls_kernel(const SysPair *sys, int nsys) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nsys) return;
-    Ctrl *c = sys[i].ctrl;
+    Ctrl *c = sys[i].p.ctrl;
     c->bar_count = 0;
     c->abort = 0;
     c->status = kStatusRunning;
@@ -21,10 +21,10 @@ __global__ void reset_ctrls_kernel(const Params *sys, int nsys) {
 }
 
 // Copies the control blocks of a batch into one array (for one host copy).
-__global__ void gather_ctrls_kernel(const Params *sys, int nsys, Ctrl *out) {
+__global__ void gather_ctrls_kernel(const SysPair *sys, int nsys, Ctrl *out) {
     const int i = blockIdx.x;
     if (i >= nsys) return;
-    const int *src = reinterpret_cast<const int *>(sys[i].ctrl);
+    const int *src = reinterpret_cast<const int *>(sys[i].p.ctrl);
     int *dst = reinterpret_cast<int *>(out + i);
     for (int w = threadIdx.x; w < (int)(sizeof(Ctrl) / sizeof(int)); w += blockDim.x)
         dst[w] = src[w];
@@ -118,19 +118,23 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
         P.pd[D_EMAX_C * nct + trank(P)] = emax;
         P.pi[I_BAD_C * nct + trank(P)] = bad;
     }
-    RGD_SYNC(DS(D_EMAX_C), DS(D_EMAX_C), DS(I_BAD_C));
+#define SAMPLE_SYNC(dm, dx, im)                                         \
+    do {                                                                \
+        if (!sync_collect(P, S, (dm), (dx), (im), S.red_d)) return;     \
+    } while (0)
+    SAMPLE_SYNC(DS(D_EMAX_C), DS(D_EMAX_C), DS(I_BAD_C));
     emax = S.red_d[D_EMAX_C];
     bad = S.red_i[I_BAD_C];
     long long count = 0;
     if (bad == 0 && emax > 0.0) {
         phase_quantize(P, eps, len, emax, greedy, eta, bs);
-        RGD_SYNC(0, 0, 0);
+        SAMPLE_SYNC(0, 0, 0);
         if (!greedy) {
             phase_draw(P, len, s, seed, sysid, k, phase, S.tab, bs);
-            RGD_SYNC(0, 0, 0);
+            SAMPLE_SYNC(0, 0, 0);
         }
-        phase_compact_count(P, len, eps, eps, nullptr, bs);
-        RGD_SYNC(0, 0, 0);
+        phase_compact_count<double>(P, len, eps, eps, nullptr, bs);
+        SAMPLE_SYNC(0, 0, 0);
         count = phase_compact_write(P, len, P.rowpos, idx, S.tab, bs);
     }
     if (trank(P) == 0 && threadIdx.x == 0) {
@@ -140,8 +144,12 @@ __global__ void __launch_bounds__(kSolveMaxThreads, 1)
     }
 }
 
-#undef RGD_SYNC
+#undef SAMPLE_SYNC
 #undef DS
+
+__global__ void to_float_kernel(const double *in, long long len, float *out) {
+    for (long long i = gthread(); i < len; i += nthreads()) out[i] = __double2float_rn(in[i]);
+}
 
 __global__ void reset_ctrl_kernel(Ctrl *c) {
     c->bar_count = 0;
@@ -156,6 +164,7 @@ __global__ void reset_ctrl_kernel(Ctrl *c) {
     c->sample_count = 0;
     c->emax_out = 0.0;
     c->bad_out = 0;
+    c->refinements = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -170,8 +179,8 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
 // rgdbek_solve512.cu
 const void *solve_kernel_fn(bool fp32, bool small) {
     if (small) return solve_kernel_fn_small(fp32);
-    return fp32 ? (const void *)solve_kernel<true, kSolveMaxThreads>
-                : (const void *)solve_kernel<false, kSolveMaxThreads>;
+    return fp32 ? (const void *)refine_kernel<kSolveMaxThreads>
+                : (const void *)solve_kernel<kSolveMaxThreads>;
 }
 const void *batched_kernel_fn(bool fp32, bool small) {
     if (small) return batched_kernel_fn_small(fp32);
@@ -179,12 +188,17 @@ const void *batched_kernel_fn(bool fp32, bool small) {
                 : (const void *)batched_solve_kernel<false, kSolveMaxThreads>;
 }
 
-cudaError_t launch_solve(const Params &P, int grid, int block, cudaStream_t s) {
+cudaError_t launch_solve(const Params &P, const ParamsF &F, int grid, int block, cudaStream_t s) {
     Params p = P;
     p.team = grid;
-    void *args[] = {&p};
-    const void *fn = solve_kernel_fn(P.fp32_inner != 0, block <= kSolveSmallThreads);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, (size_t)P.dsmem_bytes, s);
+    ParamsF f = F;
+    f.team = grid;
+    const bool fp32 = P.precision == RGDBEK_PRECISION_FP32_INNER;
+    void *args1[] = {&p};
+    void *args2[] = {&p, &f};
+    const void *fn = solve_kernel_fn(fp32, block <= kSolveSmallThreads);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), fp32 ? args2 : args1,
+                                       (size_t)P.dsmem_bytes, s);
 }
 
 cudaError_t launch_sample(const Params &P, int grid, int block, const double *eps, long long len,
@@ -224,13 +238,21 @@ cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const doub
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_float(const double *in, long long len, float *out, cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    long long g = (len + 255) / 256;
+    if (g > 4096) g = 4096;
+    to_float_kernel<<<(int)g, 256, 0, s>>>(in, len, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_weights(const double *v, const double *norm2, long long len, double *eps,
                            Ctrl *ctrl, int grid, int block, cudaStream_t s) {
     weights_kernel<<<grid, block, 0, s>>>(v, norm2, len, eps, ctrl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int stride, int team,
+cudaError_t launch_solve_batched(const SysPair *sys_dev, const int *plan_dev, int stride, int team,
                                  int nteams, bool fp32, int block, cudaStream_t s) {
     void *args[] = {&sys_dev, &plan_dev, &stride, &team};
     const void *fn = batched_kernel_fn(fp32, block <= kSolveSmallThreads);
@@ -238,13 +260,13 @@ cudaError_t launch_solve_batched(const Params *sys_dev, const int *plan_dev, int
                                        (size_t)kSolveDsmemBytes, s);
 }
 
-cudaError_t launch_reset_ctrls(const Params *sys_dev, int nsys, cudaStream_t s) {
+cudaError_t launch_reset_ctrls(const SysPair *sys_dev, int nsys, cudaStream_t s) {
     if (nsys <= 0) return cudaSuccess;
     reset_ctrls_kernel<<<(nsys + 255) / 256, 256, 0, s>>>(sys_dev, nsys);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_ctrls(const Params *sys_dev, int nsys, Ctrl *out, cudaStream_t s) {
+cudaError_t launch_gather_ctrls(const SysPair *sys_dev, int nsys, Ctrl *out, cudaStream_t s) {
     if (nsys <= 0) return cudaSuccess;
     gather_ctrls_kernel<<<nsys, 128, 0, s>>>(sys_dev, nsys, out);
     return cudaGetLastError();

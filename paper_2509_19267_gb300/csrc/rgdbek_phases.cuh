@@ -23,39 +23,44 @@
 
 namespace rgd {
 
-struct Params {
+// Kernel parameters of one system, for values of type V: double for the FP64
+// solve (and the FP64 outer loop of the FP32 form), float for the FP32 inner
+// solve of RGDBEK_PRECISION_FP32_INNER.  Index arrays, selection scratch and
+// the control block are shared by both views of a system.
+template <typename V>
+struct ParamsT {
     long long m, n, nnz;
     // A in CSR and CSC form, squared row/column norms
     const long long *__restrict__ rp;
     const int *__restrict__ ci;
-    const double *__restrict__ av;
+    const V *__restrict__ av;
     const long long *__restrict__ cp;
     const int *__restrict__ ri;
-    const double *__restrict__ cv;
-    const double *__restrict__ rn2;
-    const double *__restrict__ cn2;
+    const V *__restrict__ cv;
+    const V *__restrict__ rn2;
+    const V *__restrict__ cn2;
     // right-hand side and solution
-    const double *b;
-    double *x;
+    const V *b;
+    V *x;
     // work vectors: z (m) and t = b - A x (m), stored as (z_i, t_i) pairs
     // (z_i at z[2 i], t_i at t[2 i] = z[2 i + 1]: the column pass gathers both
-    // with one 16-byte load), r (m), g = A^T z (n), weights, LSQR vectors u (m),
+    // with one load), r (m), g = A^T z (n), weights, LSQR vectors u (m),
     // v, w, y (n), the row-step solution dx (n) and the trial iterate
     // xt = x + dx (n) that the next column pass adopts
-    double *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx, *xt;
+    V *z, *t, *r, *g, *epsc, *epsr, *uu, *vv, *ww, *yy, *dx, *xt;
     unsigned long long *Q;  // chunk-local inclusive prefix of quantised weights
     unsigned char *flag;    // drawn / selected marks
     int *colpos, *rowpos;   // position of a column in U / of a row in J, or -1
     int *ulist, *jlist;     // U_k and J_k, ascending
     int *srn;               // A_U as CSR over all m rows: row i holds srn[i] entries
     int *sci;               // at sci/sav[rp[i] ..], columns renumbered 0..|U|-1
-    double *sav;
+    V *sav;
     int *scn;               // A^J as CSC over all n columns: column j holds scn[j]
     int *sri;               // entries at sri/scv[cp[j] ..], rows renumbered 0..|J|-1
-    double *scv;
-    double *dots, *dots2;   // per-line dot products of the inner solve when a CTA's
+    V *scv;
+    V *dots, *dots2;        // per-line dot products of the inner solve when a CTA's
                             // chunk does not fit in shared memory (max(m, n) each)
-    double *pd;             // double partials [D_NSLOTS][grid]
+    V *pd;                  // value partials [D_NSLOTS][grid]
     long long *pi;          // int64 partials [I_NSLOTS][grid]
     Ctrl *ctrl;
     long long *tr_counts;
@@ -69,19 +74,49 @@ struct Params {
     double inner_adapt;     // > 0: per-iteration inner tolerance tied to the outer residual
     double time_budget_ns;
     long long max_iter, s_col, s_row;
+    long long k0;           // number of the first outer iteration (the Philox counter)
     unsigned long long seed, sysid;
     int inner_max, stop_rule, selection;
-    int fp32_inner;         // inner LSQR products in FP32 (Kahan dots)
+    int precision;          // RGDBEK_PRECISION_* of the solve
     int team;               // CTAs that work on this system (rank = blockIdx.x % team)
     int warm;               // x holds x_0 on entry (else x_0 = 0)
-    float *vv32, *uu32;     // float copies of the LSQR vectors v~, u~ (fp32_inner)
-    double *vvs, *dsc;      // column step: D v~ and D = 1/||A_j|| per column of U
-    double *yh;             // column step: y^ of the scaled block (global fallback)
-    double *uus, *dsr;      // row step: D u~ and D = 1/||A^(i)|| per row of J
-    int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A, FP64 passes
+    V *vvs, *dsc;           // column step: D v~ and D = 1/||A_j|| per column of U
+    V *yh;                  // column step: y^ of the scaled block (global fallback)
+    V *uus, *dsr;           // row step: D u~ and D = 1/||A^(i)|| per row of J
+    int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A in the passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
 };
+using Params = ParamsT<double>;
+using ParamsF = ParamsT<float>;
+
+// Pairs of values loaded with one instruction.
+template <typename V>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+
+// Arithmetic of the two value types (the FP64 forms are the ones the FP64
+// solve has always used, so its results do not change).
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double vrsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float vrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+// residual weight v^2 / c, each operation correctly rounded (Section 2)
+__device__ __forceinline__ double weight_of(double v, double c) {
+    return __ddiv_rn(__dmul_rn(v, v), c);
+}
+__device__ __forceinline__ float weight_of(float v, float c) {
+    return __fdiv_rn(__fmul_rn(v, v), c);
+}
 
 // Lane geometry of a group of L lanes inside a warp.
 struct Grp {
@@ -121,26 +156,33 @@ __device__ __forceinline__ long long nthreads() {
 // The rank is computed once per kernel by enter_team (every kernel that runs
 // phase code calls it first) and kept in shared memory.
 __shared__ int s_team_rank;
-__device__ __forceinline__ void enter_team(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ void enter_team(const PT &P) {
     if (threadIdx.x == 0) s_team_rank = (int)(blockIdx.x % (unsigned)P.team);
     __syncthreads();
 }
-__device__ __forceinline__ int trank(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ int trank(const PT &P) {
     (void)P;
     // re-read at each use (like a special register) rather than held live
     return *reinterpret_cast<volatile int *>(&s_team_rank);
 }
-__device__ __forceinline__ int tsize(const Params &P) { return P.team; }
-__device__ __forceinline__ long long twarp(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ int tsize(const PT &P) { return P.team; }
+template <typename PT>
+__device__ __forceinline__ long long twarp(const PT &P) {
     return (long long)trank(P) * (blockDim.x >> 5) + (threadIdx.x >> 5);
 }
-__device__ __forceinline__ long long twarps(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ long long twarps(const PT &P) {
     return (long long)P.team * (blockDim.x >> 5);
 }
-__device__ __forceinline__ long long tthread(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ long long tthread(const PT &P) {
     return (long long)trank(P) * blockDim.x + threadIdx.x;
 }
-__device__ __forceinline__ long long tthreads(const Params &P) {
+template <typename PT>
+__device__ __forceinline__ long long tthreads(const PT &P) {
     return (long long)P.team * blockDim.x;
 }
 
@@ -152,79 +194,108 @@ __device__ __forceinline__ T ldx(const T *p) {
     else return *p;
 }
 
+// The right-hand side b of a solve.  The FP64 solve never writes it during a
+// kernel, so it goes through the read-only path; the FP32 inner solve's b is
+// rewritten by the refinement loop of the same kernel, so it is loaded from L2
+// (the non-coherent read-only cache could still hold the previous one).
+__device__ __forceinline__ double ld_rhs(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_rhs(const float *p) { return __ldcg(p); }
+
+// Kahan-compensated accumulation (Kahan 1965) of FP32 products: c carries the
+// rounding error of the running sum into the next term, and the sum is
+// returned as s - c.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float x) {
+        const float y = fmaf(a, x, -c);
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float sum() const { return s - c; }
+};
+
 // This lane's share of sum_e val[e] * f(idx[e]) over e = e, e + L, e + 2L, ...
-// below e1, accumulated in exactly that order.  Four entries are handled per
-// trip with all their loads issued before the multiply-adds, so four
+// below e1, accumulated in exactly that order (FP64: a chain of fused
+// multiply-adds; FP32: Kahan-compensated).  Four entries are handled per
+// trip with all their loads issued before the arithmetic, so four
 // independent index/value loads and four gathers are in flight per lane.
-template <bool RO, typename F>
-__device__ __forceinline__ double lane_dot(long long e, long long e1, long long L, const int *idx,
-                                           const double *val, F f) {
-    double s = 0.0;
+template <bool RO, typename V, typename F>
+__device__ __forceinline__ V lane_dot(long long e, long long e1, long long L, const int *idx,
+                                      const V *val, F f) {
+    V s = V(0);
+    KahanF k;
     for (; e < e1; e += 4 * L) {
         const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
         const int i0 = ldx<RO>(idx + e);
         const int i1 = v1 ? ldx<RO>(idx + e + L) : 0;
         const int i2 = v2 ? ldx<RO>(idx + e + 2 * L) : 0;
         const int i3 = v3 ? ldx<RO>(idx + e + 3 * L) : 0;
-        const double a0 = ldx<RO>(val + e);
-        const double a1 = v1 ? ldx<RO>(val + e + L) : 0.0;
-        const double a2 = v2 ? ldx<RO>(val + e + 2 * L) : 0.0;
-        const double a3 = v3 ? ldx<RO>(val + e + 3 * L) : 0.0;
-        const double x0 = f(i0);
-        const double x1 = v1 ? f(i1) : 0.0;
-        const double x2 = v2 ? f(i2) : 0.0;
-        const double x3 = v3 ? f(i3) : 0.0;
-        s = fma(a0, x0, s);
-        if (v1) s = fma(a1, x1, s);
-        if (v2) s = fma(a2, x2, s);
-        if (v3) s = fma(a3, x3, s);
+        const V a0 = ldx<RO>(val + e);
+        const V a1 = v1 ? ldx<RO>(val + e + L) : V(0);
+        const V a2 = v2 ? ldx<RO>(val + e + 2 * L) : V(0);
+        const V a3 = v3 ? ldx<RO>(val + e + 3 * L) : V(0);
+        const V x0 = f(i0);
+        const V x1 = v1 ? f(i1) : V(0);
+        const V x2 = v2 ? f(i2) : V(0);
+        const V x3 = v3 ? f(i3) : V(0);
+        if constexpr (sizeof(V) == 8) {
+            s = fma(a0, x0, s);
+            if (v1) s = fma(a1, x1, s);
+            if (v2) s = fma(a2, x2, s);
+            if (v3) s = fma(a3, x3, s);
+        } else {
+            k.add(a0, x0);
+            if (v1) k.add(a1, x1);
+            if (v2) k.add(a2, x2);
+            if (v3) k.add(a3, x3);
+        }
     }
-    return s;
+    if constexpr (sizeof(V) == 8) return s;
+    else return k.sum();
 }
 
 // Two dot products sharing the index/value loads (A^T z and A^T t): the two
-// vectors are stored as (z_i, t_i) pairs, so one 16-byte gather serves both.
+// vectors are stored as (z_i, t_i) pairs, so one gather serves both.
+template <typename V>
 __device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L, const int *idx,
-                                          const double *val, const double2 *zt, double &sf,
-                                          double &sg) {
+                                          const V *val, const typename Vec2<V>::type *zt, V &sf,
+                                          V &sg) {
+    using V2 = typename Vec2<V>::type;
+    KahanF kf, kg;
     for (; e < e1; e += 4 * L) {
         const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
         const int i0 = __ldg(idx + e);
         const int i1 = v1 ? __ldg(idx + e + L) : 0;
         const int i2 = v2 ? __ldg(idx + e + 2 * L) : 0;
         const int i3 = v3 ? __ldg(idx + e + 3 * L) : 0;
-        const double a0 = __ldg(val + e);
-        const double a1 = v1 ? __ldg(val + e + L) : 0.0;
-        const double a2 = v2 ? __ldg(val + e + 2 * L) : 0.0;
-        const double a3 = v3 ? __ldg(val + e + 3 * L) : 0.0;
-        const double2 p0 = zt[i0];
-        const double2 p1 = v1 ? zt[i1] : make_double2(0.0, 0.0);
-        const double2 p2 = v2 ? zt[i2] : make_double2(0.0, 0.0);
-        const double2 p3 = v3 ? zt[i3] : make_double2(0.0, 0.0);
-        sf = fma(a0, p0.x, sf);
-        sg = fma(a0, p0.y, sg);
-        if (v1) { sf = fma(a1, p1.x, sf); sg = fma(a1, p1.y, sg); }
-        if (v2) { sf = fma(a2, p2.x, sf); sg = fma(a2, p2.y, sg); }
-        if (v3) { sf = fma(a3, p3.x, sf); sg = fma(a3, p3.y, sg); }
+        const V a0 = __ldg(val + e);
+        const V a1 = v1 ? __ldg(val + e + L) : V(0);
+        const V a2 = v2 ? __ldg(val + e + 2 * L) : V(0);
+        const V a3 = v3 ? __ldg(val + e + 3 * L) : V(0);
+        const V2 zero{V(0), V(0)};
+        const V2 p0 = zt[i0];
+        const V2 p1 = v1 ? zt[i1] : zero;
+        const V2 p2 = v2 ? zt[i2] : zero;
+        const V2 p3 = v3 ? zt[i3] : zero;
+        if constexpr (sizeof(V) == 8) {
+            sf = fma(a0, p0.x, sf);
+            sg = fma(a0, p0.y, sg);
+            if (v1) { sf = fma(a1, p1.x, sf); sg = fma(a1, p1.y, sg); }
+            if (v2) { sf = fma(a2, p2.x, sf); sg = fma(a2, p2.y, sg); }
+            if (v3) { sf = fma(a3, p3.x, sf); sg = fma(a3, p3.y, sg); }
+        } else {
+            kf.add(a0, p0.x);
+            kg.add(a0, p0.y);
+            if (v1) { kf.add(a1, p1.x); kg.add(a1, p1.y); }
+            if (v2) { kf.add(a2, p2.x); kg.add(a2, p2.y); }
+            if (v3) { kf.add(a3, p3.x); kg.add(a3, p3.y); }
+        }
     }
-}
-
-// Number of entries e = e, e + L, ... below e1 with map[idx[e]] >= 0.
-__device__ __forceinline__ int lane_count(long long e, long long e1, long long L, const int *idx,
-                                          const int *map) {
-    int c = 0;
-    for (; e < e1; e += 4 * L) {
-        const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
-        const int i0 = __ldg(idx + e);
-        const int i1 = v1 ? __ldg(idx + e + L) : 0;
-        const int i2 = v2 ? __ldg(idx + e + 2 * L) : 0;
-        const int i3 = v3 ? __ldg(idx + e + 3 * L) : 0;
-        c += map[i0] >= 0;
-        if (v1) c += map[i1] >= 0;
-        if (v2) c += map[i2] >= 0;
-        if (v3) c += map[i3] >= 0;
+    if constexpr (sizeof(V) == 4) {
+        sf = kf.sum();
+        sg = kg.sum();
     }
-    return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -264,28 +335,30 @@ __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, 
 //   g = A^T z_k, h = A^T t_k with t_k = b - A x_k (for the stopping test),
 //   eps^z_j = g_j^2 / ||A_j||^2.
 // Partials: max eps^z, ||h||^2, ||g||^2, non-finite flag.
-__device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
+template <typename V>
+__device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs) {
+    using V2 = typename Vec2<V>::type;
     const Grp G(P.tpc);
-    double emax = 0.0, hh = 0.0, gg = 0.0;
+    V emax = V(0), hh = V(0), gg = V(0);
     long long bad = 0;
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
-        double sg = 0.0, sh = 0.0;
+        V sg = V(0), sh = V(0);
         if (j < P.n)
-            lane_dot2(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
-                      reinterpret_cast<const double2 *>(P.z), sg, sh);
+            lane_dot2<V>(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
+                         reinterpret_cast<const V2 *>(P.z), sg, sh);
         sg = group_sum(sg, G.L);
         sh = group_sum(sh, G.L);
         if (j < P.n && G.sl == 0) {
             P.x[j] = P.xt[j];
-            const double c = __ldg(P.cn2 + j);
-            const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(sg, sg), c) : 0.0;
+            const V c = __ldg(P.cn2 + j);
+            const V e = c > V(0) ? weight_of(sg, c) : V(0);
             P.g[j] = sg;
             P.epsc[j] = e;
             if (!isfinite(e)) bad = 1;
             else emax = max_nonneg(emax, e);
-            hh = fma(sh, sh, hh);
-            gg = fma(sg, sg, gg);
+            hh = vfma(sh, sh, hh);
+            gg = vfma(sg, sg, gg);
         }
     }
     emax = block_max(emax, bs);
@@ -301,20 +374,21 @@ __device__ __forceinline__ void phase_col(const Params &P, BlockScratch &bs) {
 }
 
 // t_{k+1} = b - A x_{k+1} over the CSR rows, x_{k+1} = xt.  Partial: ||t||^2.
-__device__ __forceinline__ void phase_residual(const Params &P, BlockScratch &bs) {
+template <typename V>
+__device__ __forceinline__ void phase_residual(const ParamsT<V> &P, BlockScratch &bs) {
     const Grp G(P.tpr);
-    double tt = 0.0;
+    V tt = V(0);
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
-        double s = 0.0;
+        V s = V(0);
         if (i < P.m)
             s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
                                [&](int j) { return P.xt[j]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
-            const double ti = __ldg(P.b + i) - s;
+            const V ti = ld_rhs(P.b + i) - s;
             P.t[2 * i] = ti;
-            tt = fma(ti, ti, tt);
+            tt = vfma(ti, ti, tt);
         }
     }
     tt = block_sum(tt, bs);
@@ -333,18 +407,41 @@ struct Chunk {
     }
 };
 
+// q = floor(2^K * fl(eps / eps_max)), the quantised weight of the random rule.
+// FP64: the correctly rounded FP64 ratio scaled by 2^K (exact) and floored.
+__device__ __forceinline__ unsigned long long quantize_weight(double e, double emax, int K) {
+    const double ratio = __ddiv_rn(e, emax);
+    return __double2ull_rz(floor(scalbn(ratio, K)));
+}
+// FP32: the correctly rounded FP32 ratio r in [0, 1] is m * 2^(x - 150) for
+// its 24-bit significand m and biased exponent x, so floor(2^K r) is m
+// shifted left by x - 150 + K, or right by its negative (bits shifted out
+// are the floor), computed exactly with integer operations.  Subnormal
+// ratios (below 2^-126) give 0, as 2^(K - 126) < 1 for K <= 62.
+__device__ __forceinline__ unsigned long long quantize_weight(float e, float emax, int K) {
+    const unsigned bits = __float_as_uint(__fdiv_rn(e, emax));
+    const int ex = (int)((bits >> 23) & 0xffu);
+    if (ex == 0) return 0ull;
+    const unsigned long long mant = (unsigned long long)((bits & 0x7fffffu) | 0x800000u);
+    const int sh = ex - 150 + K;
+    if (sh >= 0) return mant << sh;
+    if (sh <= -24) return 0ull;
+    return mant >> (-sh);
+}
+
 // Random rule: q_j = floor(2^K eps_j / eps_max), K = 62 - ceil(log2 len), and
 // the chunk-local inclusive prefix of q into Q; clears the marks.  Partial:
 // the chunk total.  Greedy rule: marks {j : eps_j >= eta eps_max, eps_j > 0}.
-__device__ __forceinline__ void phase_quantize(const Params &P, const double *eps, long long len,
-                                               double emax, bool greedy, double eta,
+template <typename V>
+__device__ __forceinline__ void phase_quantize(const ParamsT<V> &P, const V *eps, long long len,
+                                               V emax, bool greedy, double eta,
                                                BlockScratch &bs) {
     const Chunk C(len, trank(P), tsize(P));
     if (greedy) {
-        const double thr = __dmul_rn(eta, emax);
+        const V thr = (V)eta * emax;
         for (long long j = C.lo + threadIdx.x; j < C.hi; j += blockDim.x) {
-            const double e = eps[j];
-            P.flag[j] = (e >= thr && e > 0.0) ? 1 : 0;
+            const V e = eps[j];
+            P.flag[j] = (e >= thr && e > V(0)) ? 1 : 0;
         }
         return;
     }
@@ -354,8 +451,7 @@ __device__ __forceinline__ void phase_quantize(const Params &P, const double *ep
         const long long j = base + threadIdx.x;
         unsigned long long q = 0;
         if (j < C.hi) {
-            const double ratio = __ddiv_rn(eps[j], emax);
-            q = __double2ull_rz(floor(scalbn(ratio, K)));
+            q = quantize_weight(eps[j], emax, K);
             P.flag[j] = 0;
         }
         unsigned long long tot;
@@ -370,7 +466,8 @@ __device__ __forceinline__ void phase_quantize(const Params &P, const double *ep
 // (seed, sysid) and counter (k, phase, t div 4, 0); target = floor(R Q_tot /
 // 2^64); the drawn index is the first j whose global inclusive prefix of q
 // exceeds target (located through the per-CTA totals, then inside the chunk).
-__device__ __forceinline__ void phase_draw(const Params &P, long long len, long long s,
+template <typename PT>
+__device__ __forceinline__ void phase_draw(const PT &P, long long len, long long s,
                                            unsigned long long seed, unsigned long long sysid,
                                            unsigned long long k, unsigned long long phase,
                                            long long *tab, BlockScratch &bs) {
@@ -412,22 +509,23 @@ __device__ __forceinline__ void phase_draw(const Params &P, long long len, long 
 // side, or of B^T c in the column step), and with unit (the weights eps =
 // vec^2 / norm2) the same two sums for the block with its lines scaled to
 // unit norm: the line count and the sum of the weights.
-__device__ __forceinline__ void phase_compact_count(const Params &P, long long len,
-                                                    const double *norm2, const double *vec,
-                                                    const double *unit, BlockScratch &bs) {
+template <typename V>
+__device__ __forceinline__ void phase_compact_count(const ParamsT<V> &P, long long len,
+                                                    const V *norm2, const V *vec,
+                                                    const V *unit, BlockScratch &bs) {
     const Chunk C(len, trank(P), tsize(P));
     long long cnt = 0;
-    double fro = 0.0, ext = 0.0, frs = 0.0, exs = 0.0;
+    V fro = V(0), ext = V(0), frs = V(0), exs = V(0);
     for (long long base = C.lo; base < C.hi; base += blockDim.x) {
         const long long j = base + threadIdx.x;
         const bool f = j < C.hi && P.flag[j];
         cnt += __popc(__ballot_sync(kFull, f)) * ((threadIdx.x & 31) == 0);
         if (f) {
             fro += __ldg(norm2 + j);
-            const double v = vec[j];
-            ext = fma(v, v, ext);
+            const V v = vec[j];
+            ext = vfma(v, v, ext);
             if (unit) {
-                frs += 1.0;
+                frs += V(1);
                 exs += unit[j];
             }
         }
@@ -473,7 +571,8 @@ __device__ __forceinline__ long long block_rank_pred(bool f, BlockScratch &bs, l
 
 // Marked indices -> ascending list; pos[j] = position in the list or -1.
 // Returns the list length.
-__device__ __forceinline__ long long phase_compact_write(const Params &P, long long len, int *pos,
+template <typename PT>
+__device__ __forceinline__ long long phase_compact_write(const PT &P, long long len, int *pos,
                                                          int *list, long long *tab,
                                                          BlockScratch &bs) {
     const int nct = tsize(P);
@@ -508,16 +607,18 @@ __device__ __forceinline__ long long phase_compact_write(const Params &P, long l
 // rows and A^J all n columns, so both block products are gathers.
 // Partial: the number of extracted entries.
 // ---------------------------------------------------------------------------
+template <typename V>
 struct Lines {
     const long long *ptr;
     const int *idx;
-    const double *val;
+    const V *val;
     long long n;
     int L;
 };
 
-__device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, const int *map,
-                                              int *ocnt, int *oidx, double *oval,
+template <typename V>
+__device__ __forceinline__ void phase_extract(const ParamsT<V> &P, const Lines<V> &A,
+                                              const int *map, int *ocnt, int *oidx, V *oval,
                                               BlockScratch &bs) {
     const Grp G(A.L);
     const long long L = G.L;
@@ -534,13 +635,13 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
             // four entries per lane per trip: index and value loads, then map gathers
             const long long e = e0 + (long long)it * 4 * L + G.sl;
             int p[4];
-            double vq[4];
+            V vq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const long long f = e + q * L;
                 const bool in = valid && f < e1;
                 p[q] = in ? __ldg(A.idx + f) : -1;
-                vq[q] = in ? __ldg(A.val + f) : 0.0;   // with the index: one round trip less
+                vq[q] = in ? __ldg(A.val + f) : V(0);   // with the index: one round trip less
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) p[q] = p[q] >= 0 ? map[p[q]] : -1;
@@ -564,11 +665,12 @@ __device__ __forceinline__ void phase_extract(const Params &P, const Lines &A, c
     if (threadIdx.x == 0) P.pi[I_NNZ * tsize(P) + trank(P)] = total;
 }
 
-__device__ __forceinline__ bool stop_rule_holds(int rule, double tol, double rel, double nrm) {
+template <typename V>
+__device__ __forceinline__ bool stop_rule_holds(int rule, double tol, V rel, V nrm) {
     switch (rule) {
-    case RGDBEK_STOP_REL_RES: return rel <= tol;
-    case RGDBEK_STOP_RSE: return rel * rel <= tol;
-    default: return nrm <= tol;
+    case RGDBEK_STOP_REL_RES: return rel <= (V)tol;
+    case RGDBEK_STOP_RSE: return rel * rel <= (V)tol;
+    default: return nrm <= (V)tol;
     }
 }
 

@@ -1,8 +1,10 @@
 // Device code of the persistent solve: the inner LSQR, the phases of one
-// outer iteration (solve_body) and the single and batched solve kernels,
-// templated on the inner precision (F32) and the launch bound (NT threads).
-// Two translation units include it, each instantiating one launch bound, so
-// that the two shapes compile in parallel.
+// outer iteration (solve_body), the FP64 refinement loop of the FP32 form
+// (refine_body) and the single and batched solve kernels, templated on the
+// value type V of the iteration (double, or float for the inner solves of
+// RGDBEK_PRECISION_FP32_INNER) and the launch bound (NT threads).  Two
+// translation units include it, each instantiating one launch bound, so that
+// the two shapes compile in parallel.
 //
 // One outer iteration k of Algorithm 1, phase by phase (| = grid barrier):
 //   col:  x_k = x_{k-1} + dx; g = A^T z_k; h = A^T (b - A x_k); eps^z  |
@@ -23,6 +25,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 
 #include "rgdbek_internal.h"
 
@@ -31,24 +34,37 @@ namespace rgd {
 // Scalars of the LSQR recurrences.  GB300's FP64 rate is low, so they are
 // computed by thread 0 of each CTA only (every CTA gets bit-identical values
 // from the identically reduced partials) and broadcast through shared memory.
-struct LsqrState {
-    double alpha, beta, rhobar, phibar, beta1, fro;
-    double irho, cs, sn;         // plane rotation of the current step (1/rho, c, s)
-    double inv_a, ab, wcoef;     // coefficients of the next rows phase
-    double inv_b, ba, phi_rho;   // coefficients of the next cols phase
-    double itol;                 // inner tolerance of this solve
+template <typename V>
+struct LsqrStateT {
+    V alpha, beta, rhobar, phibar, beta1, fro;
+    V irho, cs, sn;         // plane rotation of the current step (1/rho, c, s)
+    V inv_a, ab, wcoef;     // coefficients of the next rows phase
+    V inv_b, ba, phi_rho;   // coefficients of the next cols phase
+    V itol;                 // inner tolerance of this solve
     int mv, done;
-    int fit;                     // at the end: 1 = the residual met the tolerance (a
-                                 // consistent block), 2 = step cap, 0 = otherwise
+    int fit;                // at the end: 1 = the residual met the tolerance (a
+                            // consistent block), 2 = step cap, 0 = otherwise
 };
 
 // Scalars of the outer iteration, also computed by thread 0 only.
-struct OuterState {
-    double bb, tt, zz, atb2, rel, nrm, emax_c, emax_r;
-    double beta1, alpha1, fro2, inv_beta1;
-    double beta1s, fro2s;        // row step: the same for the row-scaled block
-    double itol;                 // inner tolerance of this iteration
-    int verdict;                 // status to finish with, or kStatusRunning to go on
+template <typename V>
+struct OuterStateT {
+    V bb, tt, zz, atb2, rel, nrm, emax_c, emax_r;
+    V beta1, alpha1, fro2, inv_beta1;
+    V beta1s, fro2s;        // row step: the same for the row-scaled block
+    V itol;                 // inner tolerance of this iteration
+    V best;                 // smallest stopping measure so far (stall test)
+    long long kbest;        // iteration that reached it
+    int verdict;            // status to finish with, or kStatusRunning to go on
+};
+
+// Scalars of the FP64 refinement loop of the FP32 form (thread 0 only).
+struct RefineState {
+    double bb, atb2, tt, hh, rel, nrm, best;
+    double scale, inv_scale;  // ||t|| and its reciprocal: the inner rhs is t / ||t||
+    double itol;              // target of the next inner solve
+    long long refinements, kbest;
+    int verdict;
 };
 
 // per-solve counters, kept by thread 0 (only CTA 0's copy is reported)
@@ -57,25 +73,37 @@ struct Acc {
     long long lsqr_nnzu, lsqr_nnzj, lsqr_nu, lsqr_nj;
 };
 
-struct SolveSmem {
+template <typename V>
+struct SolveSmemT {
     BlockScratch bs;
     Acc acc;
     long long tab[kMaxGrid];
-    double red_d[D_NSLOTS];                          // reduced partials of the last barrier
+    V red_d[D_NSLOTS];                               // reduced partials of the last barrier
     long long red_i[I_NSLOTS];
-    LsqrState lsqr;                                  // LSQR scalars (written by thread 0)
-    OuterState o;                                    // outer-loop scalars (thread 0)
+    double red64[D_NSLOTS];                          // FP64 partials of the refinement loop
+    LsqrStateT<V> lsqr;                              // LSQR scalars (written by thread 0)
+    OuterStateT<V> o;                                // outer-loop scalars (thread 0)
+    RefineState ref;                                 // refinement scalars (thread 0)
     unsigned long long epoch;                        // grid barriers passed (thread 0 copy)
     int leader;                                      // this CTA has rank 0 in its team
     unsigned long long tlast;                        // phase timers (CTA 0, thread 0)
     unsigned long long tphase[RGDBEK_NUM_PHASES];
+    unsigned long long t_start;                      // globaltimer at the start of the solve
+    long long tr_off;                                // trace: list entries written so far
+    int tr_full;                                     // trace: lists full (or off)
 };
+using SolveSmem = SolveSmemT<double>;
 
 enum PhaseId { PH_SETUP = 0, PH_COL, PH_COL_SEL, PH_COL_EXT, PH_COL_LSQR, PH_ZUPD, PH_ROW_SEL,
-               PH_ROW_EXT, PH_ROW_LSQR, PH_RESID };
+               PH_ROW_EXT, PH_ROW_LSQR, PH_RESID, PH_REFINE };
+
+// Status value of a solve that left because a grid barrier was abandoned: the
+// barrier already recorded the error in the control block.
+constexpr int kAbandoned = kStatusRunning;
 
 // charges the time since the previous mark to phase `id` (team rank 0 only)
-__device__ __forceinline__ void mark(SolveSmem &S, int id) {
+template <typename V>
+__device__ __forceinline__ void mark(SolveSmemT<V> &S, int id) {
     if (S.leader && threadIdx.x == 0) {
         const unsigned long long now = globaltimer_ns();
         S.tphase[id] += now - S.tlast;
@@ -83,20 +111,40 @@ __device__ __forceinline__ void mark(SolveSmem &S, int id) {
     }
 }
 
+// Start-of-solve state of the shared block (every kernel calls it before
+// solve_body / refine_body; a batched team calls it for each system).
+template <typename V, typename PT>
+__device__ __forceinline__ void init_solve_smem(SolveSmemT<V> &S, const PT &P) {
+    if (threadIdx.x == 0) {
+        const unsigned long long now = globaltimer_ns();
+        S.epoch = 0;
+        S.leader = trank(P) == 0;
+        S.acc = Acc{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        S.tlast = now;
+        S.t_start = now;
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) S.tphase[i] = 0;
+        S.tr_off = 0;
+        S.tr_full = P.tr_lists == nullptr;
+    }
+    __syncthreads();
+}
+
 #define DS(x) (1u << (x))
 
 // Grid barrier, then the requested partial slots reduced into S.red_*.
 // Returns false if the barrier was abandoned.
-__device__ __forceinline__ bool sync_collect(const Params &P, SolveSmem &S, unsigned dmask,
-                                             unsigned dmax, unsigned imask) {
+template <typename V, typename SV>
+__device__ __forceinline__ bool sync_collect(const ParamsT<V> &P, SolveSmemT<SV> &S, unsigned dmask,
+                                             unsigned dmax, unsigned imask, V *out_d) {
     if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return false;
     if (dmask | imask)
-        collect_partials(P.pd, P.pi, tsize(P), dmask, dmax, imask, S.red_d, S.red_i);
+        collect_partials<V>(P.pd, P.pi, tsize(P), dmask, dmax, imask, out_d, S.red_i);
     return true;
 }
 
+template <typename SV>
 __device__ __forceinline__ void finish(const Params &P, int status, long long k, double rel,
-                                       double nrm, const SolveSmem &S) {
+                                       double nrm, long long refinements, const SolveSmemT<SV> &S) {
     if (trank(P) == 0 && threadIdx.x == 0) {
         const Acc &a = S.acc;
         Ctrl *C = P.ctrl;
@@ -115,6 +163,7 @@ __device__ __forceinline__ void finish(const Params &P, int status, long long k,
         C->rel_res = rel;
         C->normal_res = nrm;
         C->rse = rel * rel;
+        C->refinements = refinements;
         __threadfence();
         atomicCAS(&C->status, kStatusRunning, status);
     }
@@ -142,17 +191,20 @@ __device__ __forceinline__ void finish(const Params &P, int status, long long k,
 //   b = ptr[src], e = cnt ? b + cnt[src] : ptr[src + 1],  src = list ? list[l] : l
 // (an extracted block keeps its lines in place with counts; a block made of
 // selected rows/columns of A reads them through the selection list).
+template <typename V>
 struct SideC {
     const long long *ptr;
     const int *cnt;
     const int *list;
     const int *idx;        // indices into the other space
-    const double *val;
+    const V *val;
     long long n;           // lines
     int L;                 // lanes per line
 };
 
-__device__ __forceinline__ void line_span(const SideC &S, long long l, long long &b, long long &e) {
+template <typename V>
+__device__ __forceinline__ void line_span(const SideC<V> &S, long long l, long long &b,
+                                          long long &e) {
     const long long src = S.list ? S.list[l] : l;
     b = __ldg(S.ptr + src);
     e = S.cnt ? b + S.cnt[src] : __ldg(S.ptr + src + 1);
@@ -161,17 +213,17 @@ __device__ __forceinline__ void line_span(const SideC &S, long long l, long long
 // This CTA's chunk [lo, lo + nl) of a side.  Cached: local line li spans
 // idx/val[ptr[li], ptr[li+1]) in shared memory.  Otherwise the lines are read
 // from the global arrays through line_span.
+template <typename V>
 struct CtaSide {
     const long long *ptr;
     const int *idx;
-    const double *val;   // cached values (FP64 inner products)
-    const float *valf;   // cached values (FP32 inner products)
+    const V *val;        // cached values
     int nl;
     long long lo;
-    int L;               // lanes per line, FP64 products
-    int Lf;              // lanes per line, FP32 products
+    int L;               // lanes per line (FP64 products, and uncached lines)
+    int Lf;              // lanes per line of cached FP32 products
     bool cached;
-    SideC g;
+    SideC<V> g;
 };
 
 // bump allocation in dynamic shared memory (16-byte granules)
@@ -190,13 +242,12 @@ struct SmemArena {
 };
 
 // Copies this CTA's chunk of a side into shared memory (compacting the
-// lines), if it fits; with fp32 the values are stored as float.  All threads
-// of the CTA call it.
-template <bool fp32>
-__device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, BlockScratch &bs,
-                                              int rank, int nct) {
+// lines), if it fits.  All threads of the CTA call it.
+template <typename V>
+__device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A, BlockScratch &bs,
+                                                 int rank, int nct) {
     const Chunk C(S.n, rank, nct);
-    CtaSide out;
+    CtaSide<V> out;
     out.nl = (int)(C.hi - C.lo);
     out.lo = C.lo;
     out.L = S.L;
@@ -206,7 +257,6 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
     out.ptr = nullptr;
     out.idx = nullptr;
     out.val = nullptr;
-    out.valf = nullptr;
     const SmemArena save = A;
     long long *ps = A.take<long long>(out.nl + 1);
     long long *gs = ps ? A.take<long long>(out.nl) : nullptr;  // global start of each line
@@ -242,9 +292,8 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
         while (Lf > 1 && (long long)out.nl * Lf > lanes) Lf >>= 1;
     }
     int *is = A.take<int>(run);
-    double *vs = (is && !fp32) ? A.take<double>(run) : nullptr;
-    float *vf = (is && fp32) ? A.take<float>(run) : nullptr;
-    if (!vs && !vf) {
+    V *vs = is ? A.take<V>(run) : nullptr;
+    if (!vs) {
         A = save;
         __syncthreads();
         return out;
@@ -260,8 +309,7 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
                 const long long b = gs[li], o = ps[li], len = ps[li + 1] - o;
                 for (long long k = G.sl; k < len; k += G.L) {
                     is[o + k] = S.idx[b + k];
-                    if (fp32) vf[o + k] = (float)S.val[b + k];
-                    else vs[o + k] = S.val[b + k];
+                    vs[o + k] = S.val[b + k];
                 }
             }
         }
@@ -272,74 +320,24 @@ __device__ __forceinline__ CtaSide cache_side(const SideC &S, SmemArena &A, Bloc
     out.ptr = ps;
     out.idx = is;
     out.val = vs;
-    out.valf = vf;
     return out;
-}
-
-// This lane's share of an FP32 dot product over entries e, e + L, ... < e1,
-// Kahan-compensated (Kahan 1965): c carries the rounding error of the running
-// sum into the next term; the lane returns s - c.  Four entries per trip,
-// their gathers issued together.
-__device__ __forceinline__ float lane_dot_kahan(int e, int e1, int L, const int *idx,
-                                                const float *val, const float *vec) {
-    float s = 0.f, c = 0.f;
-    for (; e < e1; e += 4 * L) {
-        int ix[4];
-        float a[4], x[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool ok = e + q * L < e1;
-            ix[q] = ok ? idx[e + q * L] : -1;
-            a[q] = ok ? val[e + q * L] : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = ix[q] >= 0 ? vec[ix[q]] : 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (ix[q] >= 0) {
-                const float y = fmaf(a[q], x[q], -c);
-                const float t = s + y;
-                c = (t - s) - y;
-                s = t;
-            }
-        }
-    }
-    return s - c;
 }
 
 // Dot products of this CTA's lines with a gathered vector, into dots[li].
 // Warp 0 is left out: it reduces the partials of the previous barrier and
-// computes the LSQR scalars meanwhile.
-// FP32 form of cta_dots for a cached side.
-__device__ __forceinline__ void cta_dots_f32(const long long *ptr, const int *idx, const float *valf,
-                                          int nl, int Lf, const float *vec32, double *dots) {
-    const int warp = threadIdx.x >> 5;
-    const Grp G(Lf);
-    const int per = ((blockDim.x >> 5) - 1) * G.rpw;
-    for (int base = 0; base < nl; base += per) {
-        const int li = base + (warp - 1) * G.rpw + G.sub;
-        float s = 0.f;
-        if (li < nl) s = lane_dot_kahan((int)ptr[li] + G.sl, (int)ptr[li + 1], G.L, idx, valf, vec32);
-        s = group_sum(s, G.L);
-        if (li < nl && G.sl == 0) dots[li] = (double)s;
-    }
-}
-
-template <bool F32>
-__device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, const float *vec32,
-                                         double *dots) {
+// computes the LSQR scalars meanwhile.  FP32 lines accumulate with Kahan
+// compensation (lane_dot).
+template <typename V>
+__device__ __forceinline__ void cta_dots(const CtaSide<V> &C, const V *vec, V *dots) {
     const int warp = threadIdx.x >> 5;
     if (warp == 0) return;
-    if (F32 && C.cached) {
-        cta_dots_f32(C.ptr, C.idx, C.valf, C.nl, C.Lf, vec32, dots);
-        return;
-    }
-    const Grp G(C.L);
+    const int L = (sizeof(V) == 4 && C.cached) ? C.Lf : C.L;
+    const Grp G(L);
     const int per = ((blockDim.x >> 5) - 1) * G.rpw;
     const auto gat = [&](int j) { return vec[j]; };
     for (int base = 0; base < C.nl; base += per) {
         const int li = base + (warp - 1) * G.rpw + G.sub;
-        double s = 0.0;
+        V s = V(0);
         if (li < C.nl) {
             if (C.cached) {
                 s = lane_dot<false>(C.ptr[li] + G.sl, C.ptr[li + 1], G.L, C.idx, C.val, gat);
@@ -355,52 +353,52 @@ __device__ __forceinline__ void cta_dots(const CtaSide &C, const double *vec, co
 }
 
 // Warp 0: sum of the per-CTA partials of one slot (fixed order), for lane 0.
-__device__ __forceinline__ double warp0_collect(const double *pd, int slot, int nb) {
-    const double *p = pd + slot * nb;
-    double s = 0.0;
+template <typename V>
+__device__ __forceinline__ V warp0_collect(const V *pd, int slot, int nb) {
+    const V *p = pd + slot * nb;
+    V s = V(0);
 #pragma unroll 8
     for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
     return warp_sum(s);
 }
 
 // LSQR from y = 0 on the block (R, C) with right-hand side c0 (u-space,
-// global, element i at c0[i * c0s]; without v_given c0s must be 1), beta1 = ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in
-// P.vv and alpha1 is passed; otherwise it is computed first (one more
-// phase).  fro2 = ||B||_F^2.  y_g (v-space) receives the solution; with xt
-// given (the row step, v-space = x-space) also xt = x + y, so the residual
-// pass gathers x_{k+1} without an addition per nonzero.  With csc (the column
-// step; requires v_given) the solve runs on B D, D = diag(csc) over the
-// v-space (unit columns): the rows phase gathers D v~, the cols phase scales
-// B^T u~ by D, and y_g receives y = D y^, so B y_g is the projection of c0
-// whatever the scaling.  Returns the number of steps (0 if alpha1 == 0), or
-// -1 if a grid barrier was abandoned.
+// global, element i at c0[i * c0s]; without v_given c0s must be 1), beta1 =
+// ||c0||.  With v_given, v~_1 = B^T c0 / beta1 is already in P.vv and alpha1
+// is passed; otherwise it is computed first (one more phase).  fro2 =
+// ||B||_F^2.  y_g (v-space) receives the solution; with xt given (the row
+// step, v-space = x-space) also xt = x + y, so the residual pass gathers
+// x_{k+1} without an addition per nonzero.  With csc (the column step;
+// requires v_given) the solve runs on B D, D = diag(csc) over the v-space
+// (unit columns): the rows phase gathers D v~, the cols phase scales B^T u~
+// by D, and y_g receives y = D y^, so B y_g is the projection of c0 whatever
+// the scaling.  Returns the number of steps (0 if alpha1 == 0), or -1 if a
+// grid barrier was abandoned.
 //
 // Per phase: grid barrier | warp 0 reduces the partials and updates the
 // scalars while warps 1.. compute the dot products of the CTA's lines |
 // __syncthreads | all threads combine element-wise and form the partial.
-template <bool f32>
-__device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const SideC &Cs,
-                                        const double *c0, int c0s, const float *c0_32, double *y_g,
-                                        double *xt, const double *csc, const double *rsc,
-                                        bool v_given,
-                                        double alpha1, double beta1, double fro2,
-                                        unsigned char *dsmem, long long dsmem_bytes,
-                                        SolveSmem &S) {
-    LsqrState &L = S.lsqr;
+template <typename V>
+__device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
+                                        const SideC<V> &Cs, const V *c0, int c0s, V *y_g, V *xt,
+                                        const V *csc, const V *rsc, bool v_given, V alpha1,
+                                        V beta1, V fro2, unsigned char *dsmem,
+                                        long long dsmem_bytes, SolveSmemT<V> &S) {
+    LsqrStateT<V> &L = S.lsqr;
     SmemArena A{dsmem, dsmem_bytes, 0};
     const Chunk RC(Rs.n, trank(P), tsize(P)), CC(Cs.n, trank(P), tsize(P));
     const int nrl = (int)(RC.hi - RC.lo), ncl = (int)(CC.hi - CC.lo);
     // per-CTA vector slices and dot buffers
-    double *uold = A.take<double>(nrl);
-    double *dr = uold ? A.take<double>(nrl) : nullptr;
-    double *vown = dr ? A.take<double>(ncl) : nullptr;
-    double *wown = vown ? A.take<double>(ncl) : nullptr;
-    double *yown = wown ? A.take<double>(ncl) : nullptr;
-    double *dc = yown ? A.take<double>(ncl) : nullptr;
+    V *uold = A.take<V>(nrl);
+    V *dr = uold ? A.take<V>(nrl) : nullptr;
+    V *vown = dr ? A.take<V>(ncl) : nullptr;
+    V *wown = vown ? A.take<V>(ncl) : nullptr;
+    V *yown = wown ? A.take<V>(ncl) : nullptr;
+    V *dc = yown ? A.take<V>(ncl) : nullptr;
     // column scaling D of the v-space (column step), row scaling of the
     // u-space (row step): their slices
-    double *sown = (dc && csc) ? A.take<double>(ncl) : nullptr;
-    double *rown = (dc && rsc) ? A.take<double>(nrl) : nullptr;
+    V *sown = (dc && csc) ? A.take<V>(ncl) : nullptr;
+    V *rown = (dc && rsc) ? A.take<V>(nrl) : nullptr;
     const bool st_smem = dc != nullptr && (sown != nullptr || csc == nullptr) &&
                          (rown != nullptr || rsc == nullptr);
     if (!st_smem) {
@@ -411,28 +409,28 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         wown = P.ww + CC.lo;
         yown = (csc ? P.yh : y_g) + CC.lo;  // scaled: y^ apart from y = D y^
         dc = P.dots2 + CC.lo;
-        for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = 0.0;
+        for (int i = threadIdx.x; i < ncl; i += blockDim.x) yown[i] = V(0);
     } else {
         for (int i = threadIdx.x; i < nrl; i += blockDim.x) {
             uold[i] = c0[(RC.lo + i) * c0s];
             if (rown) rown[i] = rsc[RC.lo + i];
         }
         for (int i = threadIdx.x; i < ncl; i += blockDim.x) {
-            vown[i] = v_given ? P.vv[CC.lo + i] : 0.0;
-            yown[i] = 0.0;
+            vown[i] = v_given ? P.vv[CC.lo + i] : V(0);
+            yown[i] = V(0);
             if (sown) sown[i] = csc[CC.lo + i];
         }
     }
-    const double *dloc = csc ? (sown ? sown : csc + CC.lo) : nullptr;
-    const double *rloc = rsc ? (rown ? rown : rsc + RC.lo) : nullptr;
+    const V *dloc = csc ? (sown ? sown : csc + CC.lo) : nullptr;
+    const V *rloc = rsc ? (rown ? rown : rsc + RC.lo) : nullptr;
     // the cols phase gathers D u~ when the u-space is scaled
-    const double *usrc = rsc ? P.uus : P.uu;
+    const V *usrc = rsc ? P.uus : P.uu;
     // the rows phase gathers D v~ when the v-space is scaled
-    const double *vsrc = csc ? P.vvs : P.vv;
-    const CtaSide R = cache_side<f32>(Rs, A, S.bs, trank(P), tsize(P));
-    const CtaSide C = cache_side<f32>(Cs, A, S.bs, trank(P), tsize(P));
+    const V *vsrc = csc ? P.vvs : P.vv;
+    const CtaSide<V> R = cache_side<V>(Rs, A, S.bs, trank(P), tsize(P));
+    const CtaSide<V> C = cache_side<V>(Cs, A, S.bs, trank(P), tsize(P));
     if (threadIdx.x == 0) {
-        L.inv_b = 1.0 / beta1;
+        L.inv_b = V(1) / beta1;
         L.done = 0;
         L.fit = 0;
         L.itol = S.o.itol;
@@ -441,26 +439,25 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
 
     if (!v_given) {
         // v~_1 = B^T c0 / beta1 (warp 0 has no scalars to update in this phase)
-        cta_dots<f32>(C, rsc ? P.uus : c0, c0_32, dc);
+        cta_dots<V>(C, rsc ? P.uus : c0, dc);
         __syncthreads();
-        double acc = 0.0;
+        V acc = V(0);
         for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
-            const double v = dc[li] * L.inv_b;
+            const V v = dc[li] * L.inv_b;
             vown[li] = v;
             P.vv[CC.lo + li] = v;
-            if (f32) P.vv32[CC.lo + li] = (float)v;
-            acc = fma(v, v, acc);
+            acc = vfma(v, v, acc);
         }
         acc = block_sum(acc, S.bs);
         if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
         if (threadIdx.x < 32) {
-            const double vv = warp0_collect(P.pd, D_VV, tsize(P));
-            if (threadIdx.x == 0) L.alpha = sqrt(vv);
+            const V vv = warp0_collect(P.pd, D_VV, tsize(P));
+            if (threadIdx.x == 0) L.alpha = vsqrt(vv);
         }
         __syncthreads();
         alpha1 = L.alpha;
-        if (!(alpha1 > 0.0)) return 0;
+        if (!(alpha1 > V(0))) return 0;
     }
     if (threadIdx.x == 0) {
         L.alpha = alpha1;
@@ -468,32 +465,32 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         L.rhobar = alpha1;
         L.phibar = beta1;
         L.beta1 = beta1;
-        L.fro = sqrt(fro2);
-        L.inv_a = 1.0 / alpha1;
+        L.fro = vsqrt(fro2);
+        L.inv_a = V(1) / alpha1;
         L.ab = alpha1 / beta1;
-        L.wcoef = 0.0;
+        L.wcoef = V(0);
     }
     __syncthreads();
     for (int it = 1;; ++it) {
         const bool first = it == 1;
         // ---- rows phase: u~_new = B v~ / alpha - (alpha/beta) u~, w update
-        cta_dots<f32>(R, vsrc, P.vv32, dr);
+        cta_dots<V>(R, vsrc, dr);
         if (threadIdx.x < 32 && !first) {
             // scalars from ||v~||^2 of the previous cols phase
-            const double vv = warp0_collect(P.pd, D_VV, tsize(P));
+            const V vv = warp0_collect(P.pd, D_VV, tsize(P));
             if (threadIdx.x == 0) {
                 // alpha_{i+1} = ||v~||; the divisions of the recurrence are
                 // multiplications by reciprocals formed with rsqrt, which keeps
-                // the dependent FP64 chain of this single thread short
-                const double cs = L.cs, sn = L.sn, bn = L.beta;
-                const double an = bn > 0.0 ? sqrt(vv) : 0.0;
-                const double ian = an > 0.0 ? rsqrt(vv) : 0.0;
+                // the dependent chain of this single thread short
+                const V cs = L.cs, sn = L.sn, bn = L.beta;
+                const V an = bn > V(0) ? vsqrt(vv) : V(0);
+                const V ian = an > V(0) ? vrsqrt(vv) : V(0);
                 L.rhobar = -cs * an;
                 L.wcoef = sn * an * L.irho;   // theta / rho
-                const double rnorm = L.phibar;
-                const double arnorm = L.phibar * an * fabs(cs);
-                const bool resid = rnorm <= L.itol * L.beta1 || bn == 0.0;
-                const bool other = arnorm <= L.itol * L.fro * rnorm || an == 0.0;
+                const V rnorm = L.phibar;
+                const V arnorm = L.phibar * an * fabs(cs);
+                const bool resid = rnorm <= L.itol * L.beta1 || bn == V(0);
+                const bool other = arnorm <= L.itol * L.fro * rnorm || an == V(0);
                 const bool cap = it - 1 >= P.inner_max;
                 L.done = resid || other || cap;
                 L.fit = resid ? 1 : (other ? 0 : (cap ? 2 : 0));
@@ -505,22 +502,21 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         __syncthreads();
         if (L.done) return it - 1;
         {
-            const double inv_a = L.inv_a, ab = L.ab, wcoef = L.wcoef;
+            const V inv_a = L.inv_a, ab = L.ab, wcoef = L.wcoef;
             for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
-                const double vn = vown[li] * inv_a;
+                const V vn = vown[li] * inv_a;
                 wown[li] = first ? vn : vn - wcoef * wown[li];
             }
-            double acc = 0.0;
+            V acc = V(0);
             for (int li = threadIdx.x; li < nrl; li += blockDim.x) {
-                const double rl = rloc ? rloc[li] : 1.0;
-                const double uo = st_smem ? uold[li]
-                                          : (first ? c0[(RC.lo + li) * c0s] : P.uu[RC.lo + li]);
-                const double u = (rloc ? dr[li] * rl : dr[li]) * inv_a - ab * uo;
+                const V rl = rloc ? rloc[li] : V(1);
+                const V uo = st_smem ? uold[li]
+                                     : (first ? c0[(RC.lo + li) * c0s] : P.uu[RC.lo + li]);
+                const V u = (rloc ? dr[li] * rl : dr[li]) * inv_a - ab * uo;
                 P.uu[RC.lo + li] = u;
                 if (rloc) P.uus[RC.lo + li] = u * rl;
-                if (f32) P.uu32[RC.lo + li] = (float)(rloc ? u * rl : u);
                 if (st_smem) uold[li] = u;
-                acc = fma(u, u, acc);
+                acc = vfma(u, u, acc);
             }
             acc = block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_UU * tsize(P) + trank(P)] = acc;
@@ -528,19 +524,19 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
 
         // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
-        cta_dots<f32>(C, usrc, P.uu32, dc);
+        cta_dots<V>(C, usrc, dc);
         if (threadIdx.x < 32) {
-            const double uu = warp0_collect(P.pd, D_UU, tsize(P));
+            const V uu = warp0_collect(P.pd, D_UU, tsize(P));
             if (threadIdx.x == 0) {
                 // beta_{i+1} = ||u~||, rho = sqrt(rhobar^2 + beta^2); 1/rho from
                 // rsqrt of rho^2 directly, in parallel with sqrt(||u~||^2)
-                const double bn = sqrt(uu);
-                const double irho = rsqrt(fma(L.rhobar, L.rhobar, uu));
-                const double cs = L.rhobar * irho, sn = bn * irho;
-                const double phi = cs * L.phibar;
+                const V bn = vsqrt(uu);
+                const V irho = vrsqrt(vfma(L.rhobar, L.rhobar, uu));
+                const V cs = L.rhobar * irho, sn = bn * irho;
+                const V phi = cs * L.phibar;
                 L.phibar = sn * L.phibar;
-                L.mv = bn > 0.0;
-                L.inv_b = bn > 0.0 ? rsqrt(uu) : 0.0;
+                L.mv = bn > V(0);
+                L.inv_b = bn > V(0) ? vrsqrt(uu) : V(0);
                 L.ba = bn * L.inv_a;           // beta / alpha
                 L.phi_rho = phi * irho;
                 L.beta = bn;
@@ -551,20 +547,19 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
         }
         __syncthreads();
         {
-            const double inv_b = L.inv_b, ba = L.ba, phi_rho = L.phi_rho;
+            const V inv_b = L.inv_b, ba = L.ba, phi_rho = L.phi_rho;
             const bool mv = L.mv != 0;
-            double acc = 0.0;
+            V acc = V(0);
             for (int li = threadIdx.x; li < ncl; li += blockDim.x) {
-                const double dl = dloc ? dloc[li] : 1.0;
+                const V dl = dloc ? dloc[li] : V(1);
                 if (mv) {
-                    const double v = (dloc ? dc[li] * dl : dc[li]) * inv_b - ba * vown[li];
+                    const V v = (dloc ? dc[li] * dl : dc[li]) * inv_b - ba * vown[li];
                     vown[li] = v;
                     P.vv[CC.lo + li] = v;
                     if (dloc) P.vvs[CC.lo + li] = v * dl;
-                    if (f32) P.vv32[CC.lo + li] = (float)(dloc ? v * dl : v);
-                    acc = fma(v, v, acc);
+                    acc = vfma(v, v, acc);
                 }
-                const double y = fma(phi_rho, wown[li], yown[li]);
+                const V y = vfma(phi_rho, wown[li], yown[li]);
                 yown[li] = y;
                 y_g[CC.lo + li] = dloc ? y * dl : y;   // y = D y^ when scaled
                 if (xt) xt[CC.lo + li] = P.x[CC.lo + li] + y;
@@ -578,29 +573,30 @@ __device__ __forceinline__ int run_lsqr(const Params &P, const SideC &Rs, const 
 
 // z_{k+1} = z_k - A_U y (A_U as extracted CSR), r = t_k - z_{k+1},
 // eps^x_i = r_i^2 / ||A^(i)||^2.  Partials: max eps^x, ||z_{k+1}||^2, bad.
-__device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Lsub,
+template <typename V>
+__device__ __forceinline__ void phase_zupdate(const ParamsT<V> &P, bool hasU, int Lsub,
                                               BlockScratch &bs) {
     const Grp G(hasU ? Lsub : 1);
-    double emax = 0.0, zz = 0.0;
+    V emax = V(0), zz = V(0);
     long long bad = 0;
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
-        double s = 0.0;
+        V s = V(0);
         if (hasU && i < P.m)
             s = lane_dot<false>(P.rp[i] + G.sl, P.rp[i] + P.srn[i], G.L, P.sci, P.sav,
                                 [&](int p) { return P.yy[p]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
-            const double zi = P.z[2 * i] - s;
+            const V zi = P.z[2 * i] - s;
             P.z[2 * i] = zi;
-            const double ri = P.t[2 * i] - zi;
+            const V ri = P.t[2 * i] - zi;
             P.r[i] = ri;
-            const double c = __ldg(P.rn2 + i);
-            const double e = c > 0.0 ? __ddiv_rn(__dmul_rn(ri, ri), c) : 0.0;
+            const V c = __ldg(P.rn2 + i);
+            const V e = c > V(0) ? weight_of(ri, c) : V(0);
             P.epsr[i] = e;
             if (!isfinite(e)) bad = 1;
             else emax = max_nonneg(emax, e);
-            zz = fma(zi, zi, zz);
+            zz = vfma(zi, zi, zz);
         }
     }
     emax = block_max(emax, bs);
@@ -613,43 +609,53 @@ __device__ __forceinline__ void phase_zupdate(const Params &P, bool hasU, int Ls
     }
 }
 
-#define RGD_SYNC(dm, dx, im)                                 \
-    do {                                                     \
-        if (!sync_collect(P, S, (dm), (dx), (im))) return;   \
+// Result of one solve_body: the status to finish with (kAbandoned when a
+// barrier was abandoned), the iteration reached and the measures of x_k.
+template <typename V>
+struct SolveOut {
+    int status;
+    long long k;
+    V rel, nrm;
+};
+
+// Iterations without a new smallest stopping measure after which the FP32
+// inner solve of the refinement loop stops (it has reached its rounding floor).
+constexpr long long kInnerStallIters = 40;
+
+#define RGD_SYNC(dm, dx, im)                                                     \
+    do {                                                                         \
+        if (!sync_collect(P, S, (dm), (dx), (im), S.red_d))                      \
+            return SolveOut<V>{kAbandoned, 0, V(0), V(0)};                       \
     } while (0)
 
-// One whole solve of Algorithm 1 by the CTAs of a team (after enter_team).
-// F32: inner LSQR products in FP32 (RGDBEK_PRECISION_FP32_INNER); a separate
-// instantiation, so the FP64 code's registers are unaffected.
-template <bool F32>
-__device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsigned char *dsmem) {
+// One whole solve of Algorithm 1 by the CTAs of a team (after enter_team and
+// init_solve_smem), from iteration P.k0.  V = double: the FP64 solve.  V =
+// float: the inner solve of the refinement loop (x_0 = 0, its own right-hand
+// side P.b and stopping test; it also stops when its measure has not reached a
+// new minimum for kInnerStallIters iterations, reported as NOT_CONVERGED).
+template <typename V>
+__device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmemT<V> &S,
+                                                  unsigned char *dsmem) {
+    constexpr bool kF32 = sizeof(V) == 4;
     BlockScratch &bs = S.bs;
-    OuterState &O = S.o;
+    OuterStateT<V> &O = S.o;
     const int nct = tsize(P);
     const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
-    const unsigned long long t_start = globaltimer_ns();
-    if (threadIdx.x == 0) {
-        S.epoch = 0;
-        S.leader = trank(P) == 0;
-        S.acc = Acc{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        S.tlast = t_start;
-        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) S.tphase[i] = 0;
-    }
 
     // ---- x_0 = 0, z_0 = b, t_0 = b - A x_0 = b, dx = 0
     {
-        double bb = 0.0;
+        V bb = V(0);
         long long bad = 0;
         for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
-            const double bi = __ldg(P.b + i);
+            const V bi = ld_rhs(P.b + i);
             P.z[2 * i] = bi;
             P.t[2 * i] = bi;
-            bb = fma(bi, bi, bb);
+            bb = vfma(bi, bi, bb);
             if (!isfinite(bi)) bad = 1;
         }
         // x_0 = 0, or the caller's x (warm start)
         for (long long j = tthread(P); j < P.n; j += tthreads(P)) {
-            const double x0 = P.warm ? P.x[j] : 0.0;
+            const V x0 = P.warm ? P.x[j] : V(0);
             if (!isfinite(x0)) bad = 1;
             P.x[j] = x0;
             P.xt[j] = x0;
@@ -672,62 +678,62 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
         O.bb = S.red_d[D_BB];
         O.tt = P.warm ? S.red_d[D_TT] : O.bb;  // t_0 = b - A x_0 (= b from x_0 = 0)
         O.zz = O.bb;
-        O.atb2 = 0.0;
+        O.atb2 = V(0);
+        O.best = V(0);
+        O.kbest = P.k0;
         O.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(O.bb)) ? RGDBEK_ERR_NONFINITE
                                                                 : kStatusRunning;
     }
     __syncthreads();
-    if (O.verdict != kStatusRunning) {
-        finish(P, O.verdict, 0, NAN, NAN, S);
-        return;
-    }
-    long long tr_off = 0;
-    bool tr_full = P.tr_lists == nullptr;
+    if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, P.k0, V(NAN), V(NAN)};
 
-    for (long long k = 0;; ++k) {
+    for (long long k = P.k0;; ++k) {
         // ---- column pass and stopping test on x_k
         if (trank(P) == 0 && threadIdx.x == 0 && P.time_budget_ns > 0.0 &&
-            (double)(globaltimer_ns() - t_start) > P.time_budget_ns)
+            (double)(globaltimer_ns() - S.t_start) > P.time_budget_ns)
             P.ctrl->stop_req = 1;
         phase_col(P, bs);
         RGD_SYNC(DS(D_EMAX_C) | DS(D_HH) | DS(D_GG), DS(D_EMAX_C), DS(I_BAD_C));
         mark(S, PH_COL);
         if (P.tr_g && k < P.tr_vec_cap)  // trace: g = A^T z_k, complete after the barrier
-            for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.tr_g[k * P.n + j] = P.g[j];
+            for (long long j = tthread(P); j < P.n; j += tthreads(P))
+                P.tr_g[k * P.n + j] = (double)P.g[j];
         if (threadIdx.x == 0) {
-            const double hh = S.red_d[D_HH];
+            const V hh = S.red_d[D_HH];
             O.emax_c = S.red_d[D_EMAX_C];
-            if (k == 0) O.atb2 = S.red_d[D_GG];  // g = A^T z_0 = A^T b
-            O.rel = O.bb > 0.0 ? sqrt(O.tt / O.bb) : 0.0;
-            O.nrm = O.atb2 > 0.0 ? sqrt(hh / O.atb2) : 0.0;
+            if (k == P.k0) O.atb2 = S.red_d[D_GG];  // g = A^T z_0 = A^T b
+            O.rel = O.bb > V(0) ? vsqrt(O.tt / O.bb) : V(0);
+            O.nrm = O.atb2 > V(0) ? vsqrt(hh / O.atb2) : V(0);
+            const V meas = P.stop_rule == RGDBEK_STOP_REL_RES
+                               ? O.rel
+                               : (P.stop_rule == RGDBEK_STOP_RSE ? O.rel * O.rel : O.nrm);
             // inner tolerance of this iteration: fixed, or tied to how far x_k
             // is from the stopping rule (looser block solves while far away)
-            O.itol = P.inner_tol;
+            O.itol = (V)P.inner_tol;
             if (P.inner_adapt > 0.0) {
-                const double rk = P.stop_rule == RGDBEK_STOP_REL_RES
-                                      ? O.rel
-                                      : (P.stop_rule == RGDBEK_STOP_RSE ? O.rel * O.rel : O.nrm);
-                const double a = fmin(0.1, P.inner_adapt * rk);
+                const V a = fmin(V(0.1), (V)P.inner_adapt * meas);
                 if (a > O.itol) O.itol = a;
+            }
+            if (k == P.k0 || meas < O.best) {
+                O.best = meas;
+                O.kbest = k;
             }
             int v = kStatusRunning;
             if (S.red_i[I_BAD_C] != 0 || !isfinite(hh) || !isfinite(O.tt)) v = RGDBEK_ERR_NONFINITE;
             else if (stop_rule_holds(P.stop_rule, P.tol, O.rel, O.nrm)) v = RGDBEK_OK;
             else if (k >= P.max_iter) v = RGDBEK_NOT_CONVERGED;
             else if (ld_volatile_i32(&P.ctrl->stop_req)) v = RGDBEK_ERR_TIMEOUT;
+            else if (kF32 && k - O.kbest >= kInnerStallIters) v = RGDBEK_NOT_CONVERGED;
             O.verdict = v;
         }
         __syncthreads();
-        if (O.verdict != kStatusRunning) {
-            finish(P, O.verdict, k, O.rel, O.nrm, S);
-            return;
-        }
+        if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, k, O.rel, O.nrm};
 
         // ---- column block U_k and z_{k+1} = z_k - A_U A_U^+ z_k
         long long nU = 0, nnzU = 0;
         int stepsU = 0, Lsub_u = 1;
-        bool rec_u = !tr_full;
-        if (O.emax_c > 0.0) {
+        bool rec_u = !S.tr_full;
+        if (O.emax_c > V(0)) {
             phase_quantize(P, P.epsc, P.n, O.emax_c, greedy, P.eta_col, bs);
             RGD_SYNC(0, 0, 0);
             if (!greedy) {
@@ -742,41 +748,40 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 // ||B^T z_k|| / beta1 = sqrt(sum of the selected eps^z) / beta1,
                 // ||B||_F^2 = |U|
                 O.fro2 = S.red_d[D_FRO_S];
-                O.beta1 = sqrt(O.zz);
-                O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
-                O.alpha1 = sqrt(S.red_d[D_EXTRA_S]) * O.inv_beta1;
+                O.beta1 = vsqrt(O.zz);
+                O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
+                O.alpha1 = vsqrt(S.red_d[D_EXTRA_S]) * O.inv_beta1;
             }
             nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_COL_SEL);
-            rec_u = !tr_full && tr_off + nU <= P.tr_list_cap;
-            const double inv_beta1 = O.inv_beta1;
+            rec_u = !S.tr_full && S.tr_off + nU <= P.tr_list_cap;
+            const V inv_beta1 = O.inv_beta1;
             for (long long p = tthread(P); p < nU; p += tthreads(P)) {
                 const int j = P.ulist[p];
-                const double d = rsqrt(P.cn2[j]);       // selected: ||A_j|| > 0
-                const double v1 = P.g[j] * d * inv_beta1;  // v~_1 = B^T z_k / beta1
+                const V d = vrsqrt(P.cn2[j]);           // selected: ||A_j|| > 0
+                const V v1 = P.g[j] * d * inv_beta1;    // v~_1 = B^T z_k / beta1
                 P.dsc[p] = d;
                 P.vv[p] = v1;
                 P.vvs[p] = v1 * d;
-                if (F32) P.vv32[p] = (float)(v1 * d);
-                P.yy[p] = 0.0;
-                if (rec_u) P.tr_lists[tr_off + p] = j;
+                P.yy[p] = V(0);
+                if (rec_u) P.tr_lists[S.tr_off + p] = j;
             }
             // A_U: the entries of every row of A that lie in U's columns
             // about ten entries per lane, as in the FP64 passes (measured: fewer
             // lanes per line keep more lines, and so more loads, in flight)
-            const Lines Arows{P.rp, P.ci, P.av, P.m, P.tpr};
+            const Lines<V> Arows{P.rp, P.ci, P.av, P.m, P.tpr};
             phase_extract(P, Arows, P.colpos, P.srn, P.sci, P.sav, bs);
             RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_COL_EXT);
             nnzU = S.red_i[I_NNZ];
             Lsub_u = pick_lanes_fp64(nnzU, P.m);
-            if (O.beta1 > 0.0 && O.alpha1 > 0.0) {
-                const SideC rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
-                const SideC cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr<F32>(P, rows, cols, P.z, 2, nullptr, P.yy, nullptr, P.dsc, nullptr, true, O.alpha1, O.beta1,
-                                  O.fro2, dsmem, P.dsmem_bytes, S);
-                if (stepsU < 0) return;
+            if (O.beta1 > V(0) && O.alpha1 > V(0)) {
+                const SideC<V> rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
+                const SideC<V> cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
+                stepsU = run_lsqr<V>(P, rows, cols, P.z, 2, P.yy, nullptr, P.dsc, nullptr, true,
+                                     O.alpha1, O.beta1, O.fro2, dsmem, P.dsmem_bytes, S);
+                if (stepsU < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
                 mark(S, PH_COL_LSQR);
             }
         }
@@ -786,23 +791,21 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
         RGD_SYNC(DS(D_EMAX_R) | DS(D_ZZ), DS(D_EMAX_R), DS(I_BAD_R));
         mark(S, PH_ZUPD);
         if (P.tr_r && k < P.tr_vec_cap)  // trace: the row residual r = b - z_{k+1} - A x_k
-            for (long long i = tthread(P); i < P.m; i += tthreads(P)) P.tr_r[k * P.m + i] = P.r[i];
+            for (long long i = tthread(P); i < P.m; i += tthreads(P))
+                P.tr_r[k * P.m + i] = (double)P.r[i];
         if (threadIdx.x == 0) {
             O.emax_r = S.red_d[D_EMAX_R];
             O.zz = S.red_d[D_ZZ];
             O.verdict = S.red_i[I_BAD_R] != 0 ? RGDBEK_ERR_NONFINITE : kStatusRunning;
         }
         __syncthreads();
-        if (O.verdict != kStatusRunning) {
-            finish(P, O.verdict, k, O.rel, O.nrm, S);
-            return;
-        }
+        if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, k, O.rel, O.nrm};
 
         // ---- row block J_k and dx = (A^J)^+ r_J
         long long nJ = 0, nnzJ = 0;
         int stepsJ = 0;
         bool rec_j = false;
-        if (O.emax_r > 0.0) {
+        if (O.emax_r > V(0)) {
             phase_quantize(P, P.epsr, P.m, O.emax_r, greedy, P.eta_row, bs);
             RGD_SYNC(0, 0, 0);
             if (!greedy) {
@@ -815,69 +818,67 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
                 // LSQR start on A^J with c = r_J: beta1 = ||r_J||; on D A^J
                 // (unit rows) with c = D r_J: beta1 = sqrt(sum of the weights)
                 O.fro2 = S.red_d[D_FRO];
-                O.beta1 = sqrt(S.red_d[D_EXTRA]);
-                O.inv_beta1 = O.beta1 > 0.0 ? 1.0 / O.beta1 : 0.0;
+                O.beta1 = vsqrt(S.red_d[D_EXTRA]);
+                O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
                 O.fro2s = S.red_d[D_FRO_S];
-                O.beta1s = sqrt(S.red_d[D_EXTRA_S]);
+                O.beta1s = vsqrt(S.red_d[D_EXTRA_S]);
             }
             nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
             mark(S, PH_ROW_SEL);
-            rec_j = rec_u && tr_off + nU + nJ <= P.tr_list_cap;
+            rec_j = rec_u && S.tr_off + nU + nJ <= P.tr_list_cap;
             // |J| <= n: first on D A^J (rows scaled to unit norm, D =
             // diag(1/||A^(i)||)) with c = D r_J, which has the same minimum-norm
             // solution whenever the block system is consistent
             const bool rscale = nJ <= P.n;
             for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
                 const int i = P.jlist[p];
-                const double ri = P.r[i];
+                const V ri = P.r[i];
                 if (rscale) {
-                    const double d = rsqrt(P.rn2[i]);  // selected: ||A^(i)|| > 0
-                    const double u1 = ri * d;          // u~_1 = D r_J
+                    const V d = vrsqrt(P.rn2[i]);      // selected: ||A^(i)|| > 0
+                    const V u1 = ri * d;               // u~_1 = D r_J
                     P.dsr[p] = d;
                     P.uu[p] = u1;
                     P.uus[p] = u1 * d;
-                    if (F32) P.uu32[p] = (float)(u1 * d);
                 } else {
                     P.uu[p] = ri;  // u~_1 = r_J
-                    if (F32) P.uu32[p] = (float)ri;
                 }
-                if (rec_j) P.tr_lists[tr_off + nU + p] = i;
+                if (rec_j) P.tr_lists[S.tr_off + nU + p] = i;
             }
             // A^J: the entries of every column of A that lie in J's rows
-            const Lines Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
+            const Lines<V> Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
             phase_extract(P, Acols, P.rowpos, P.scn, P.sri, P.scv, bs);
             RGD_SYNC(0, 0, DS(I_NNZ));
             mark(S, PH_ROW_EXT);
             nnzJ = S.red_i[I_NNZ];
-            if (O.beta1 > 0.0) {
-                const SideC rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
-                const SideC cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
-                                 pick_lanes_fp64(nnzJ, P.n)};
+            if (O.beta1 > V(0)) {
+                const SideC<V> rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
+                const SideC<V> cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
+                                    pick_lanes_fp64(nnzJ, P.n)};
                 int fit = 0;
                 if (rscale) {
-                    stepsJ = run_lsqr<F32>(P, rows, cols, P.uu, 1, P.uu32, P.dx, P.xt, nullptr,
-                                           P.dsr, false, 0.0, O.beta1s, O.fro2s, dsmem,
-                                           P.dsmem_bytes, S);
-                    if (stepsJ < 0) return;
+                    stepsJ = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr, P.dsr,
+                                         false, V(0), O.beta1s, O.fro2s, dsmem, P.dsmem_bytes, S);
+                    if (stepsJ < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
                     fit = S.lsqr.fit;
                 }
-                if (!rscale || fit == 0) {
+                // The FP32 inner solve keeps the row-scaled step even when LSQR
+                // finds the block inconsistent at FP32 rounding level: the step
+                // still lies in range(A^T), and the FP64 refinement removes the
+                // difference.  The FP64 solve takes (A^J)^+ r_J exactly.
+                if (!rscale || (!kF32 && fit == 0)) {
                     if (rscale) {
                         // found inconsistent: (A^J)^+ r_J needs the unscaled block;
                         // the scaled attempt's x + y is undone first
-                        for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
-                            const double ri = P.r[P.jlist[p]];
-                            P.uu[p] = ri;
-                            if (F32) P.uu32[p] = (float)ri;
-                        }
+                        for (long long p = tthread(P); p < nJ; p += tthreads(P))
+                            P.uu[p] = P.r[P.jlist[p]];
                         for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.xt[j] = P.x[j];
                         RGD_SYNC(0, 0, 0);
                     }
-                    const int s2 = run_lsqr<F32>(P, rows, cols, P.uu, 1, P.uu32, P.dx, P.xt,
-                                                 nullptr, nullptr, false, 0.0, O.beta1, O.fro2,
-                                                 dsmem, P.dsmem_bytes, S);
-                    if (s2 < 0) return;
+                    const int s2 = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr,
+                                               nullptr, false, V(0), O.beta1, O.fro2, dsmem,
+                                               P.dsmem_bytes, S);
+                    if (s2 < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
                     stepsJ += s2;
                 }
                 mark(S, PH_ROW_LSQR);
@@ -903,15 +904,19 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
             P.tr_counts[4 * k + 2] = stepsU;
             P.tr_counts[4 * k + 3] = stepsJ;
         }
-        if (!tr_full) {
-            const bool ok = rec_u && (nJ == 0 || rec_j) && tr_off + nU + nJ <= P.tr_list_cap;
-            if (ok) tr_off += nU + nJ;
-            else tr_full = true;
+        if (!S.tr_full) {
+            // every thread evaluates the same condition; thread 0 stores it
+            const bool ok = rec_u && (nJ == 0 || rec_j) && S.tr_off + nU + nJ <= P.tr_list_cap;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (ok) S.tr_off += nU + nJ;
+                else S.tr_full = 1;
+            }
+            __syncthreads();
         }
         if (nU == 0 && nJ == 0) {
             // both blocks empty: x can no longer change
-            finish(P, RGDBEK_OK, k, O.rel, O.nrm, S);
-            return;
+            return SolveOut<V>{RGDBEK_OK, k, O.rel, O.nrm};
         }
 
         // ---- t_{k+1} = b - A x_{k+1}
@@ -922,39 +927,272 @@ __device__ __forceinline__ void solve_body(const Params &P, SolveSmem &S, unsign
     }
 }
 
+#undef RGD_SYNC
+
+// ---------------------------------------------------------------------------
+// RGDBEK_PRECISION_FP32_INNER: FP32 inner RGDBEK wrapped in FP64 iterative
+// refinement.  Every update of x lies in range(A^T), so A^+ (b - A x) = x* - x
+// for x* = A^+ b (Theorem 2.3's limit): solving A d = t, t = b - A x, for its
+// minimum-norm least-squares solution and adding d to x is one exact step to
+// x*.  The refinement loop does that with an approximate d from Algorithm 1
+// run in FP32 on A's values rounded to float, with t scaled to unit norm:
+//   t = b - A x (FP64 CSR pass), ||A^T t|| (FP64 CSC pass), stopping test
+//   d = FP32 RGDBEK(A_f32, t / ||t||) to relative measure tau_j
+//   x += ||t|| d (FP64)
+// tau_j = clamp(0.5 tol / measure_j, kRefineTolMin, 0.5), so the last inner
+// solve does no more than the outer tolerance needs; an inner solve also
+// stops at its FP32 rounding floor (kInnerStallIters without progress).  The
+// outer measures, the stopping test and x are FP64 throughout.
+// ---------------------------------------------------------------------------
+constexpr double kRefineTolMin = 1e-5;
+constexpr double kRefineTolMax = 0.5;
+// refinement steps in a row without halving the outer measure after which the
+// solve stops with NOT_CONVERGED (the FP32 inner solves make no more progress)
+constexpr int kRefineStallSteps = 3;
+
+// t_i = b_i - (A x)_i over the CSR rows in FP64, into t (m).  Partial: ||t||^2.
+__device__ __forceinline__ void phase_outer_residual(const Params &P, double *t, BlockScratch &bs) {
+    const Grp G(P.tpr);
+    double tt = 0.0;
+    for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
+        const long long i = base + G.sub;
+        double s = 0.0;
+        if (i < P.m)
+            s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
+                               [&](int j) { return P.x[j]; });
+        s = group_sum(s, G.L);
+        if (i < P.m && G.sl == 0) {
+            const double ti = __ldg(P.b + i) - s;
+            t[i] = ti;
+            tt = fma(ti, ti, tt);
+        }
+    }
+    tt = block_sum(tt, bs);
+    if (threadIdx.x == 0) P.pd[D_TT * tsize(P) + trank(P)] = tt;
+}
+
+// ||A^T v||^2 over the CSC columns in FP64 (the vector itself is not kept),
+// into partial slot `slot`.
+__device__ __forceinline__ void phase_outer_normal(const Params &P, const double *v, int slot,
+                                                   BlockScratch &bs) {
+    const Grp G(P.tpc);
+    double hh = 0.0;
+    for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
+        const long long j = base + G.sub;
+        double s = 0.0;
+        if (j < P.n)
+            s = lane_dot<true>(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
+                               [&](int i) { return v[i]; });
+        s = group_sum(s, G.L);
+        if (j < P.n && G.sl == 0) hh = fma(s, s, hh);
+    }
+    hh = block_sum(hh, bs);
+    if (threadIdx.x == 0) P.pd[slot * tsize(P) + trank(P)] = hh;
+}
+
+// The refinement loop by the CTAs of a team (after enter_team and
+// init_solve_smem).  P: the FP64 view (A in FP64, b, x, the FP64 residual in
+// P.r); F: the FP32 view of the same system (A_f32, float work vectors, its
+// own right-hand side F.b written here, solution F.x).
+__device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
+                                            SolveSmemT<float> &S, unsigned char *dsmem) {
+    BlockScratch &bs = S.bs;
+    RefineState &R = S.ref;
+    double *t64 = P.r;  // the FP64 residual b - A x
+#define RGD_SYNC64(dm, im)                                                         \
+    do {                                                                           \
+        if (!sync_collect(P, S, (dm), 0u, (im), S.red64)) return;                  \
+    } while (0)
+
+    // ---- x_0 (0 or the caller's), ||b||^2, non-finite inputs
+    {
+        double bb = 0.0;
+        long long bad = 0;
+        for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
+            const double bi = __ldg(P.b + i);
+            bb = fma(bi, bi, bb);
+            if (!isfinite(bi)) bad = 1;
+        }
+        for (long long j = tthread(P); j < P.n; j += tthreads(P)) {
+            const double x0 = P.warm ? P.x[j] : 0.0;
+            if (!isfinite(x0)) bad = 1;
+            P.x[j] = x0;
+        }
+        bb = block_sum(bb, bs);
+        bad = block_sum(bad, bs);
+        if (threadIdx.x == 0) {
+            P.pd[D_BB * tsize(P) + trank(P)] = bb;
+            P.pi[I_BAD_R * tsize(P) + trank(P)] = bad;
+        }
+    }
+    RGD_SYNC64(DS(D_BB), DS(I_BAD_R));
+    if (threadIdx.x == 0) {
+        R.bb = S.red64[D_BB];
+        R.refinements = 0;
+        R.best = 0.0;
+        R.kbest = 0;
+        R.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(R.bb)) ? RGDBEK_ERR_NONFINITE
+                                                               : kStatusRunning;
+    }
+    __syncthreads();
+    if (R.verdict != kStatusRunning) {
+        finish(P, R.verdict, 0, NAN, NAN, 0, S);
+        return;
+    }
+    // ||A^T b||^2 (the reference of the normal-equation measure) and t_0 = b - A x_0
+    phase_outer_normal(P, P.b, D_GG, bs);
+    phase_outer_residual(P, t64, bs);
+    RGD_SYNC64(DS(D_GG) | DS(D_TT), 0);
+    if (threadIdx.x == 0) {
+        R.atb2 = S.red64[D_GG];
+        R.tt = S.red64[D_TT];
+    }
+    // the time budget is checked by rank 0 before the barrier that ends each
+    // refinement step, so that every CTA reads the same stop request after it
+    const auto check_budget = [&]() {
+        if (trank(P) == 0 && threadIdx.x == 0 && P.time_budget_ns > 0.0 &&
+            (double)(globaltimer_ns() - S.t_start) > P.time_budget_ns)
+            P.ctrl->stop_req = 1;
+    };
+    phase_outer_normal(P, t64, D_HH, bs);
+    check_budget();
+    RGD_SYNC64(DS(D_HH), 0);
+    if (threadIdx.x == 0) R.hh = S.red64[D_HH];
+    mark(S, PH_REFINE);
+
+    long long k = 0;  // outer iterations of all inner solves so far
+    for (;;) {
+        if (threadIdx.x == 0) {
+            R.rel = R.bb > 0.0 ? sqrt(R.tt / R.bb) : 0.0;
+            R.nrm = R.atb2 > 0.0 ? sqrt(R.hh / R.atb2) : 0.0;
+            const double meas = P.stop_rule == RGDBEK_STOP_REL_RES
+                                    ? R.rel
+                                    : (P.stop_rule == RGDBEK_STOP_RSE ? R.rel * R.rel : R.nrm);
+            if (R.refinements == 0 || meas <= 0.5 * R.best) {
+                R.best = meas;
+                R.kbest = R.refinements;
+            }
+            int v = kStatusRunning;
+            if (!isfinite(R.tt) || !isfinite(R.hh)) v = RGDBEK_ERR_NONFINITE;
+            else if (stop_rule_holds(P.stop_rule, P.tol, R.rel, R.nrm)) v = RGDBEK_OK;
+            else if (k >= P.max_iter) v = RGDBEK_NOT_CONVERGED;
+            else if (ld_volatile_i32(&P.ctrl->stop_req)) v = RGDBEK_ERR_TIMEOUT;
+            else if (R.refinements - R.kbest >= kRefineStallSteps) v = RGDBEK_NOT_CONVERGED;
+            R.verdict = v;
+            // the target of the next inner solve, and the scaling of its rhs
+            double tau = meas > 0.0 ? 0.5 * P.tol / meas : kRefineTolMax;
+            R.itol = fmin(kRefineTolMax, fmax(kRefineTolMin, tau));
+            R.scale = sqrt(R.tt);
+            R.inv_scale = R.scale > 0.0 ? 1.0 / R.scale : 0.0;
+        }
+        __syncthreads();
+        if (R.verdict != kStatusRunning) {
+            finish(P, R.verdict, k, R.rel, R.nrm, R.refinements, S);
+            return;
+        }
+        // ---- the inner right-hand side t / ||t|| in FP32
+        {
+            const double is = R.inv_scale;
+            float *bf = const_cast<float *>(F.b);
+            for (long long i = tthread(P); i < P.m; i += tthreads(P))
+                bf[i] = (float)(t64[i] * is);
+        }
+        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return;
+        mark(S, PH_REFINE);
+        // ---- d = FP32 RGDBEK(A_f32, t / ||t||)
+        ParamsF Fj = F;
+        Fj.tol = R.itol;
+        Fj.k0 = k;
+        const SolveOut<float> o = solve_body<float>(Fj, S, dsmem);
+        if (o.status == kAbandoned) return;
+        if (o.status < 0) {
+            // NONFINITE inside the inner solve, or TIMEOUT between its iterations
+            finish(P, o.status, o.k, R.rel, R.nrm, R.refinements, S);
+            return;
+        }
+        k = o.k;
+        // ---- x += ||t|| d (FP64), then t = b - A x and ||A^T t||
+        {
+            const double sc = R.scale;
+            for (long long j = tthread(P); j < P.n; j += tthreads(P))
+                P.x[j] = fma(sc, (double)F.x[j], P.x[j]);
+        }
+        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return;
+        phase_outer_residual(P, t64, bs);
+        RGD_SYNC64(DS(D_TT), 0);
+        if (threadIdx.x == 0) R.tt = S.red64[D_TT];
+        phase_outer_normal(P, t64, D_HH, bs);
+        check_budget();
+        RGD_SYNC64(DS(D_HH), 0);
+        if (threadIdx.x == 0) {
+            R.hh = S.red64[D_HH];
+            ++R.refinements;
+        }
+        mark(S, PH_REFINE);
+    }
+#undef RGD_SYNC64
+}
+
 // A single solve: the whole grid is one team.  NT: launch bound (threads).
-template <bool F32, int NT>
+template <int NT>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(const Params P) {
     __shared__ SolveSmem S;
     extern __shared__ __align__(16) unsigned char dsmem[];
     enter_team(P);
-    solve_body<F32>(P, S, dsmem);
+    init_solve_smem(S, P);
+    const SolveOut<double> o = solve_body<double>(P, S, dsmem);
+    if (o.status != kAbandoned) finish(P, o.status, o.k, o.rel, o.nrm, 0, S);
+}
+
+// The FP32 form: FP64 refinement around FP32 inner solves, the whole grid one team.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) refine_kernel(const Params P, const ParamsF F) {
+    __shared__ SolveSmemT<float> S;
+    extern __shared__ __align__(16) unsigned char dsmem[];
+    enter_team(P);
+    init_solve_smem(S, P);
+    refine_body(P, F, S, dsmem);
 }
 
 // Many independent systems in one cooperative launch: the grid is cut into
 // teams of `team` consecutive CTAs; team t solves the systems
 // plan[t * stride], plan[t * stride + 1], ... (ending at -1) one after
-// another, each to its own stopping rule (its Params and control block in
+// another, each to its own stopping rule (its parameters and control block in
 // sys[]), with barriers among the team's CTAs only.
 template <bool F32, int NT>
 __global__ void __launch_bounds__(NT, 1)
-    batched_solve_kernel(const Params *sys, const int *plan, int stride, int team) {
-    __shared__ SolveSmem S;
+    batched_solve_kernel(const SysPair *sys, const int *plan, int stride, int team) {
+    using SV = typename std::conditional<F32, float, double>::type;
+    __shared__ SolveSmemT<SV> S;
     __shared__ Params SP;
+    __shared__ ParamsF SF;
     extern __shared__ __align__(16) unsigned char dsmem[];
     const int t = (int)(blockIdx.x / (unsigned)team);
     for (int q = 0; q < stride; ++q) {
         const int i = plan[(long long)t * stride + q];
         if (i < 0) break;
         {
-            const int *src = reinterpret_cast<const int *>(sys + i);
+            const int *src = reinterpret_cast<const int *>(&sys[i].p);
             int *dst = reinterpret_cast<int *>(&SP);
             for (int w = threadIdx.x; w < (int)(sizeof(Params) / sizeof(int)); w += blockDim.x)
                 dst[w] = src[w];
+            if (F32) {
+                const int *sf = reinterpret_cast<const int *>(&sys[i].f);
+                int *df = reinterpret_cast<int *>(&SF);
+                for (int w = threadIdx.x; w < (int)(sizeof(ParamsF) / sizeof(int));
+                     w += blockDim.x)
+                    df[w] = sf[w];
+            }
         }
         __syncthreads();
         enter_team(SP);
-        solve_body<F32>(SP, S, dsmem);
+        init_solve_smem(S, SP);
+        if constexpr (F32) {
+            refine_body(SP, SF, S, dsmem);
+        } else {
+            const SolveOut<double> o = solve_body<double>(SP, S, dsmem);
+            if (o.status != kAbandoned) finish(SP, o.status, o.k, o.rel, o.nrm, 0, S);
+        }
         __syncthreads();
     }
 }

@@ -6,8 +6,8 @@
 namespace rgd {
 
 const void *solve_kernel_fn_small(bool fp32) {
-    return fp32 ? (const void *)solve_kernel<true, kSolveSmallThreads>
-                : (const void *)solve_kernel<false, kSolveSmallThreads>;
+    return fp32 ? (const void *)refine_kernel<kSolveSmallThreads>
+                : (const void *)solve_kernel<kSolveSmallThreads>;
 }
 
 const void *batched_kernel_fn_small(bool fp32) {
