@@ -67,12 +67,17 @@ extern "C" {
  * products) on A d = t / ||t|| from d = 0, to the stopping rule's relative
  * measure tau = min(0.5, max(RGDBEK_FP32_REFINE_TOL_MIN, 0.5 tol / measure))
  * or until that inner solve stops making progress, and adds ||t|| d to x in
- * FP64.  The returned x, the stopping rule and its tolerance are FP64; the
- * limit is A^+ b up to FP64 rounding when A has full column rank.  With a
- * nontrivial null space, FP32 rounding leaves components in it that no
- * refinement removes (relative size about 1e-7).  The inner LSQR tolerance
- * is raised to at least RGDBEK_FP32_INNER_TOL.  stats.iters counts the outer
- * iterations of all inner solves, stats.refinements the FP64 steps. */
+ * FP64.  Rounding t / ||t|| to float bounds what an FP32 step resolves (for
+ * least squares, near kappa(A) u_32 ||b - A x*|| / ||b|| in the
+ * normal-equation measure), so once an FP32 step fails to halve the FP64
+ * measure the remaining steps solve the same refinement system with the FP64
+ * iteration (short solves: their z starts near the final residual).  The
+ * returned x, the stopping rule and its tolerance are FP64; the limit is
+ * A^+ b up to FP64 rounding when A has full column rank.  With a nontrivial
+ * null space, FP32 rounding leaves components in it that no refinement
+ * removes (relative size about 1e-7).  The inner LSQR tolerance of FP32
+ * steps is raised to at least RGDBEK_FP32_INNER_TOL.  stats.iters counts the
+ * outer iterations of all inner solves, stats.refinements the FP64 steps. */
 #define RGDBEK_PRECISION_FP32_INNER 1
 #define RGDBEK_FP32_INNER_TOL 1e-6
 #define RGDBEK_FP32_REFINE_TOL_MIN 1e-5

@@ -56,6 +56,9 @@ struct rgdbek_s {
     // FP64 arrays sav / scv, which the FP32 form does not otherwise use
     float *f_z, *f_r, *f_g, *f_epsc, *f_epsr, *f_uu, *f_vv, *f_ww, *f_yy, *f_dx, *f_xt, *f_x, *f_b;
     float *f_dots, *f_dots2, *f_vvs, *f_dsc, *f_yh, *f_uus, *f_dsr, *f_pd;
+    // the FP32 form's refinement loop: FP64 residual, and the right-hand side and
+    // solution of its FP64 inner solves
+    double *ref_t, *ref_b, *ref_x;
     Ctrl *ctrl;
     double *b_stage, *x_stage;
     // implicit adjoint scratch, allocated by the first rgdbek_backward call:
@@ -149,6 +152,9 @@ void carve(rgdbek_s *h, Layout &L) {
                     &h->f_dsr};
     for (float **p : fv) *p = L.take<float>(mx);
     h->f_pd = L.take<float>((long long)D_NSLOTS * kMaxGrid);
+    h->ref_t = L.take<double>(mx);
+    h->ref_b = L.take<double>(mx);
+    h->ref_x = L.take<double>(mx);
     h->ctrl = L.take<Ctrl>(1);
     h->b_stage = L.take<double>(m);
     h->x_stage = L.take<double>(n);
@@ -258,6 +264,9 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.yh = h->yh;
     P.uus = h->uus;
     P.dsr = h->dsr;
+    P.ref_t = h->ref_t;
+    P.ref_b = h->ref_b;
+    P.ref_x = h->ref_x;
     P.inner_max = h->opt.inner_max;
     P.stop_rule = h->opt.stop_rule;
     P.selection = h->opt.selection;

@@ -83,6 +83,10 @@ struct ParamsT {
     V *vvs, *dsc;           // column step: D v~ and D = 1/||A_j|| per column of U
     V *yh;                  // column step: y^ of the scaled block (global fallback)
     V *uus, *dsr;           // row step: D u~ and D = 1/||A^(i)|| per row of J
+    // refinement loop of the FP32 form (FP64 view only): the FP64 residual
+    // b - A x (m), the scaled right-hand side (m) and solution (n) of an FP64
+    // inner solve
+    V *ref_t, *ref_b, *ref_x;
     int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A in the passes
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel

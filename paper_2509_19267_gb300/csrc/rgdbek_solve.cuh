@@ -64,6 +64,7 @@ struct RefineState {
     double scale, inv_scale;  // ||t|| and its reciprocal: the inner rhs is t / ||t||
     double itol;              // target of the next inner solve
     long long refinements, kbest;
+    int fp64;                 // the inner solves now run in FP64 (FP32 reached its floor)
     int verdict;
 };
 
@@ -73,16 +74,20 @@ struct Acc {
     long long lsqr_nnzu, lsqr_nnzj, lsqr_nu, lsqr_nj;
 };
 
-template <typename V>
-struct SolveSmemT {
+// Shared state of a solve.  It holds the scalars of both value types, so that
+// one kernel can run FP64 and FP32 solves (the refinement loop of the FP32
+// form does) with one barrier epoch and one set of counters.
+struct SolveSmem {
     BlockScratch bs;
     Acc acc;
     long long tab[kMaxGrid];
-    V red_d[D_NSLOTS];                               // reduced partials of the last barrier
+    double red_d[D_NSLOTS];                          // reduced partials of the last barrier
+    float red_f[D_NSLOTS];                           // (FP64 and FP32 slots)
     long long red_i[I_NSLOTS];
-    double red64[D_NSLOTS];                          // FP64 partials of the refinement loop
-    LsqrStateT<V> lsqr;                              // LSQR scalars (written by thread 0)
-    OuterStateT<V> o;                                // outer-loop scalars (thread 0)
+    LsqrStateT<double> lsqr_d;                       // LSQR scalars (written by thread 0)
+    LsqrStateT<float> lsqr_f;
+    OuterStateT<double> o_d;                         // outer-loop scalars (thread 0)
+    OuterStateT<float> o_f;
     RefineState ref;                                 // refinement scalars (thread 0)
     unsigned long long epoch;                        // grid barriers passed (thread 0 copy)
     int leader;                                      // this CTA has rank 0 in its team
@@ -91,8 +96,23 @@ struct SolveSmemT {
     unsigned long long t_start;                      // globaltimer at the start of the solve
     long long tr_off;                                // trace: list entries written so far
     int tr_full;                                     // trace: lists full (or off)
+
+    template <typename V>
+    __device__ __forceinline__ V *red() {
+        if constexpr (sizeof(V) == 8) return red_d;
+        else return red_f;
+    }
+    template <typename V>
+    __device__ __forceinline__ LsqrStateT<V> &lsqr() {
+        if constexpr (sizeof(V) == 8) return lsqr_d;
+        else return lsqr_f;
+    }
+    template <typename V>
+    __device__ __forceinline__ OuterStateT<V> &o() {
+        if constexpr (sizeof(V) == 8) return o_d;
+        else return o_f;
+    }
 };
-using SolveSmem = SolveSmemT<double>;
 
 enum PhaseId { PH_SETUP = 0, PH_COL, PH_COL_SEL, PH_COL_EXT, PH_COL_LSQR, PH_ZUPD, PH_ROW_SEL,
                PH_ROW_EXT, PH_ROW_LSQR, PH_RESID, PH_REFINE };
@@ -102,8 +122,7 @@ enum PhaseId { PH_SETUP = 0, PH_COL, PH_COL_SEL, PH_COL_EXT, PH_COL_LSQR, PH_ZUP
 constexpr int kAbandoned = kStatusRunning;
 
 // charges the time since the previous mark to phase `id` (team rank 0 only)
-template <typename V>
-__device__ __forceinline__ void mark(SolveSmemT<V> &S, int id) {
+__device__ __forceinline__ void mark(SolveSmem &S, int id) {
     if (S.leader && threadIdx.x == 0) {
         const unsigned long long now = globaltimer_ns();
         S.tphase[id] += now - S.tlast;
@@ -113,8 +132,8 @@ __device__ __forceinline__ void mark(SolveSmemT<V> &S, int id) {
 
 // Start-of-solve state of the shared block (every kernel calls it before
 // solve_body / refine_body; a batched team calls it for each system).
-template <typename V, typename PT>
-__device__ __forceinline__ void init_solve_smem(SolveSmemT<V> &S, const PT &P) {
+template <typename PT>
+__device__ __forceinline__ void init_solve_smem(SolveSmem &S, const PT &P) {
     if (threadIdx.x == 0) {
         const unsigned long long now = globaltimer_ns();
         S.epoch = 0;
@@ -133,8 +152,8 @@ __device__ __forceinline__ void init_solve_smem(SolveSmemT<V> &S, const PT &P) {
 
 // Grid barrier, then the requested partial slots reduced into S.red_*.
 // Returns false if the barrier was abandoned.
-template <typename V, typename SV>
-__device__ __forceinline__ bool sync_collect(const ParamsT<V> &P, SolveSmemT<SV> &S, unsigned dmask,
+template <typename V>
+__device__ __forceinline__ bool sync_collect(const ParamsT<V> &P, SolveSmem &S, unsigned dmask,
                                              unsigned dmax, unsigned imask, V *out_d) {
     if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return false;
     if (dmask | imask)
@@ -142,9 +161,8 @@ __device__ __forceinline__ bool sync_collect(const ParamsT<V> &P, SolveSmemT<SV>
     return true;
 }
 
-template <typename SV>
 __device__ __forceinline__ void finish(const Params &P, int status, long long k, double rel,
-                                       double nrm, long long refinements, const SolveSmemT<SV> &S) {
+                                       double nrm, long long refinements, const SolveSmem &S) {
     if (trank(P) == 0 && threadIdx.x == 0) {
         const Acc &a = S.acc;
         Ctrl *C = P.ctrl;
@@ -383,8 +401,8 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
                                         const SideC<V> &Cs, const V *c0, int c0s, V *y_g, V *xt,
                                         const V *csc, const V *rsc, bool v_given, V alpha1,
                                         V beta1, V fro2, unsigned char *dsmem,
-                                        long long dsmem_bytes, SolveSmemT<V> &S) {
-    LsqrStateT<V> &L = S.lsqr;
+                                        long long dsmem_bytes, SolveSmem &S) {
+    LsqrStateT<V> &L = S.lsqr<V>();
     SmemArena A{dsmem, dsmem_bytes, 0};
     const Chunk RC(Rs.n, trank(P), tsize(P)), CC(Cs.n, trank(P), tsize(P));
     const int nrl = (int)(RC.hi - RC.lo), ncl = (int)(CC.hi - CC.lo);
@@ -433,7 +451,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
         L.inv_b = V(1) / beta1;
         L.done = 0;
         L.fit = 0;
-        L.itol = S.o.itol;
+        L.itol = S.o<V>().itol;
     }
     __syncthreads();
 
@@ -624,7 +642,7 @@ constexpr long long kInnerStallIters = 40;
 
 #define RGD_SYNC(dm, dx, im)                                                     \
     do {                                                                         \
-        if (!sync_collect(P, S, (dm), (dx), (im), S.red_d))                      \
+        if (!sync_collect(P, S, (dm), (dx), (im), red))                          \
             return SolveOut<V>{kAbandoned, 0, V(0), V(0)};                       \
     } while (0)
 
@@ -634,11 +652,12 @@ constexpr long long kInnerStallIters = 40;
 // side P.b and stopping test; it also stops when its measure has not reached a
 // new minimum for kInnerStallIters iterations, reported as NOT_CONVERGED).
 template <typename V>
-__device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmemT<V> &S,
+__device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem &S,
                                                   unsigned char *dsmem) {
     constexpr bool kF32 = sizeof(V) == 4;
     BlockScratch &bs = S.bs;
-    OuterStateT<V> &O = S.o;
+    OuterStateT<V> &O = S.o<V>();
+    V *const red = S.red<V>();
     const int nct = tsize(P);
     const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
 
@@ -675,8 +694,8 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
         RGD_SYNC(DS(D_TT), 0, 0);
     }
     if (threadIdx.x == 0) {
-        O.bb = S.red_d[D_BB];
-        O.tt = P.warm ? S.red_d[D_TT] : O.bb;  // t_0 = b - A x_0 (= b from x_0 = 0)
+        O.bb = red[D_BB];
+        O.tt = P.warm ? red[D_TT] : O.bb;  // t_0 = b - A x_0 (= b from x_0 = 0)
         O.zz = O.bb;
         O.atb2 = V(0);
         O.best = V(0);
@@ -699,9 +718,9 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
             for (long long j = tthread(P); j < P.n; j += tthreads(P))
                 P.tr_g[k * P.n + j] = (double)P.g[j];
         if (threadIdx.x == 0) {
-            const V hh = S.red_d[D_HH];
-            O.emax_c = S.red_d[D_EMAX_C];
-            if (k == P.k0) O.atb2 = S.red_d[D_GG];  // g = A^T z_0 = A^T b
+            const V hh = red[D_HH];
+            O.emax_c = red[D_EMAX_C];
+            if (k == P.k0) O.atb2 = red[D_GG];  // g = A^T z_0 = A^T b
             O.rel = O.bb > V(0) ? vsqrt(O.tt / O.bb) : V(0);
             O.nrm = O.atb2 > V(0) ? vsqrt(hh / O.atb2) : V(0);
             const V meas = P.stop_rule == RGDBEK_STOP_REL_RES
@@ -747,10 +766,10 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
                 // diag(1/||A_j||)) with c = z_k: beta1 = ||z_k||, alpha1 =
                 // ||B^T z_k|| / beta1 = sqrt(sum of the selected eps^z) / beta1,
                 // ||B||_F^2 = |U|
-                O.fro2 = S.red_d[D_FRO_S];
+                O.fro2 = red[D_FRO_S];
                 O.beta1 = vsqrt(O.zz);
                 O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
-                O.alpha1 = vsqrt(S.red_d[D_EXTRA_S]) * O.inv_beta1;
+                O.alpha1 = vsqrt(red[D_EXTRA_S]) * O.inv_beta1;
             }
             nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
@@ -794,8 +813,8 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
             for (long long i = tthread(P); i < P.m; i += tthreads(P))
                 P.tr_r[k * P.m + i] = (double)P.r[i];
         if (threadIdx.x == 0) {
-            O.emax_r = S.red_d[D_EMAX_R];
-            O.zz = S.red_d[D_ZZ];
+            O.emax_r = red[D_EMAX_R];
+            O.zz = red[D_ZZ];
             O.verdict = S.red_i[I_BAD_R] != 0 ? RGDBEK_ERR_NONFINITE : kStatusRunning;
         }
         __syncthreads();
@@ -817,11 +836,11 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
             if (threadIdx.x == 0) {
                 // LSQR start on A^J with c = r_J: beta1 = ||r_J||; on D A^J
                 // (unit rows) with c = D r_J: beta1 = sqrt(sum of the weights)
-                O.fro2 = S.red_d[D_FRO];
-                O.beta1 = vsqrt(S.red_d[D_EXTRA]);
+                O.fro2 = red[D_FRO];
+                O.beta1 = vsqrt(red[D_EXTRA]);
                 O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
-                O.fro2s = S.red_d[D_FRO_S];
-                O.beta1s = vsqrt(S.red_d[D_EXTRA_S]);
+                O.fro2s = red[D_FRO_S];
+                O.beta1s = vsqrt(red[D_EXTRA_S]);
             }
             nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
             RGD_SYNC(0, 0, 0);
@@ -860,7 +879,7 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
                     stepsJ = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr, P.dsr,
                                          false, V(0), O.beta1s, O.fro2s, dsmem, P.dsmem_bytes, S);
                     if (stepsJ < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
-                    fit = S.lsqr.fit;
+                    fit = S.lsqr<V>().fit;
                 }
                 // The FP32 inner solve keeps the row-scaled step even when LSQR
                 // finds the block inconsistent at FP32 rounding level: the step
@@ -923,7 +942,7 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
         phase_residual(P, bs);
         RGD_SYNC(DS(D_TT), 0, 0);
         mark(S, PH_RESID);
-        if (threadIdx.x == 0) O.tt = S.red_d[D_TT];
+        if (threadIdx.x == 0) O.tt = red[D_TT];
     }
 }
 
@@ -941,13 +960,20 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
 //   x += ||t|| d (FP64)
 // tau_j = clamp(0.5 tol / measure_j, kRefineTolMin, 0.5), so the last inner
 // solve does no more than the outer tolerance needs; an inner solve also
-// stops at its FP32 rounding floor (kInnerStallIters without progress).  The
-// outer measures, the stopping test and x are FP64 throughout.
+// stops at its FP32 rounding floor (kInnerStallIters without progress).
+// The rounding of t / ||t|| to float limits what an FP32 step can resolve:
+// for a least-squares problem t is dominated by the residual r* = b - A x*,
+// and the normal-equation measure of its FP32 image cannot fall much below
+// about kappa(A) u_32 ||r*|| / ||b||.  When an FP32 step no longer halves the
+// FP64 measure, the remaining steps solve the same system A d = t / ||t||
+// with the FP64 iteration: its z starts at t, within a small multiple of the
+// final r*, so those solves are short.  The outer measures, the stopping test
+// and x are FP64 throughout.
 // ---------------------------------------------------------------------------
-constexpr double kRefineTolMin = 1e-5;
+constexpr double kRefineTolMin = RGDBEK_FP32_REFINE_TOL_MIN;
 constexpr double kRefineTolMax = 0.5;
 // refinement steps in a row without halving the outer measure after which the
-// solve stops with NOT_CONVERGED (the FP32 inner solves make no more progress)
+// solve stops with NOT_CONVERGED (with FP64 inner solves: no more progress)
 constexpr int kRefineStallSteps = 3;
 
 // t_i = b_i - (A x)_i over the CSR rows in FP64, into t (m).  Partial: ||t||^2.
@@ -991,17 +1017,19 @@ __device__ __forceinline__ void phase_outer_normal(const Params &P, const double
 }
 
 // The refinement loop by the CTAs of a team (after enter_team and
-// init_solve_smem).  P: the FP64 view (A in FP64, b, x, the FP64 residual in
-// P.r); F: the FP32 view of the same system (A_f32, float work vectors, its
+// init_solve_smem).  P: the FP64 view (A in FP64, b, x, the refinement
+// buffers ref_t / ref_b / ref_x and the FP64 work vectors for FP64 inner
+// solves); F: the FP32 view of the same system (A_f32, float work vectors, its
 // own right-hand side F.b written here, solution F.x).
-__device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
-                                            SolveSmemT<float> &S, unsigned char *dsmem) {
+__device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F, SolveSmem &S,
+                                            unsigned char *dsmem) {
     BlockScratch &bs = S.bs;
     RefineState &R = S.ref;
-    double *t64 = P.r;  // the FP64 residual b - A x
+    double *const t64 = P.ref_t;  // the FP64 residual b - A x
+    double *const red = S.red_d;
 #define RGD_SYNC64(dm, im)                                                         \
     do {                                                                           \
-        if (!sync_collect(P, S, (dm), 0u, (im), S.red64)) return;                  \
+        if (!sync_collect(P, S, (dm), 0u, (im), red)) return;                      \
     } while (0)
 
     // ---- x_0 (0 or the caller's), ||b||^2, non-finite inputs
@@ -1027,10 +1055,11 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
     }
     RGD_SYNC64(DS(D_BB), DS(I_BAD_R));
     if (threadIdx.x == 0) {
-        R.bb = S.red64[D_BB];
+        R.bb = red[D_BB];
         R.refinements = 0;
         R.best = 0.0;
         R.kbest = 0;
+        R.fp64 = 0;
         R.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(R.bb)) ? RGDBEK_ERR_NONFINITE
                                                                : kStatusRunning;
     }
@@ -1044,8 +1073,8 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
     phase_outer_residual(P, t64, bs);
     RGD_SYNC64(DS(D_GG) | DS(D_TT), 0);
     if (threadIdx.x == 0) {
-        R.atb2 = S.red64[D_GG];
-        R.tt = S.red64[D_TT];
+        R.atb2 = red[D_GG];
+        R.tt = red[D_TT];
     }
     // the time budget is checked by rank 0 before the barrier that ends each
     // refinement step, so that every CTA reads the same stop request after it
@@ -1057,7 +1086,7 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
     phase_outer_normal(P, t64, D_HH, bs);
     check_budget();
     RGD_SYNC64(DS(D_HH), 0);
-    if (threadIdx.x == 0) R.hh = S.red64[D_HH];
+    if (threadIdx.x == 0) R.hh = red[D_HH];
     mark(S, PH_REFINE);
 
     long long k = 0;  // outer iterations of all inner solves so far
@@ -1071,6 +1100,11 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
             if (R.refinements == 0 || meas <= 0.5 * R.best) {
                 R.best = meas;
                 R.kbest = R.refinements;
+            } else if (!R.fp64) {
+                // an FP32 step that did not halve the measure: FP32 has reached
+                // its floor, the next steps run in FP64
+                R.fp64 = 1;
+                R.kbest = R.refinements;
             }
             int v = kStatusRunning;
             if (!isfinite(R.tt) || !isfinite(R.hh)) v = RGDBEK_ERR_NONFINITE;
@@ -1081,7 +1115,7 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
             R.verdict = v;
             // the target of the next inner solve, and the scaling of its rhs
             double tau = meas > 0.0 ? 0.5 * P.tol / meas : kRefineTolMax;
-            R.itol = fmin(kRefineTolMax, fmax(kRefineTolMin, tau));
+            R.itol = fmin(kRefineTolMax, fmax(R.fp64 ? 0.0 : kRefineTolMin, tau));
             R.scale = sqrt(R.tt);
             R.inv_scale = R.scale > 0.0 ? 1.0 / R.scale : 0.0;
         }
@@ -1090,42 +1124,61 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F,
             finish(P, R.verdict, k, R.rel, R.nrm, R.refinements, S);
             return;
         }
-        // ---- the inner right-hand side t / ||t|| in FP32
+        const bool fp64 = R.fp64 != 0;
+        // ---- the inner right-hand side t / ||t|| (FP32, or FP64 for FP64 steps)
         {
             const double is = R.inv_scale;
             float *bf = const_cast<float *>(F.b);
-            for (long long i = tthread(P); i < P.m; i += tthreads(P))
-                bf[i] = (float)(t64[i] * is);
+            for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
+                const double v = t64[i] * is;
+                if (fp64) P.ref_b[i] = v;
+                else bf[i] = (float)v;
+            }
         }
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return;
         mark(S, PH_REFINE);
-        // ---- d = FP32 RGDBEK(A_f32, t / ||t||)
-        ParamsF Fj = F;
-        Fj.tol = R.itol;
-        Fj.k0 = k;
-        const SolveOut<float> o = solve_body<float>(Fj, S, dsmem);
-        if (o.status == kAbandoned) return;
-        if (o.status < 0) {
+        int ist;
+        if (!fp64) {
+            // ---- d = FP32 RGDBEK(A_f32, t / ||t||)
+            ParamsF Fj = F;
+            Fj.tol = R.itol;
+            Fj.k0 = k;
+            const SolveOut<float> o = solve_body<float>(Fj, S, dsmem);
+            ist = o.status;
+            k = o.k;
+        } else {
+            // ---- d = FP64 RGDBEK(A, t / ||t||)
+            Params Pj = P;
+            Pj.b = P.ref_b;
+            Pj.x = P.ref_x;
+            Pj.warm = 0;
+            Pj.tol = R.itol;
+            Pj.k0 = k;
+            const SolveOut<double> o = solve_body<double>(Pj, S, dsmem);
+            ist = o.status;
+            k = o.k;
+        }
+        if (ist == kAbandoned) return;
+        if (ist < 0) {
             // NONFINITE inside the inner solve, or TIMEOUT between its iterations
-            finish(P, o.status, o.k, R.rel, R.nrm, R.refinements, S);
+            finish(P, ist, k, R.rel, R.nrm, R.refinements, S);
             return;
         }
-        k = o.k;
         // ---- x += ||t|| d (FP64), then t = b - A x and ||A^T t||
         {
             const double sc = R.scale;
             for (long long j = tthread(P); j < P.n; j += tthreads(P))
-                P.x[j] = fma(sc, (double)F.x[j], P.x[j]);
+                P.x[j] = fma(sc, fp64 ? P.ref_x[j] : (double)F.x[j], P.x[j]);
         }
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return;
         phase_outer_residual(P, t64, bs);
         RGD_SYNC64(DS(D_TT), 0);
-        if (threadIdx.x == 0) R.tt = S.red64[D_TT];
+        if (threadIdx.x == 0) R.tt = red[D_TT];
         phase_outer_normal(P, t64, D_HH, bs);
         check_budget();
         RGD_SYNC64(DS(D_HH), 0);
         if (threadIdx.x == 0) {
-            R.hh = S.red64[D_HH];
+            R.hh = red[D_HH];
             ++R.refinements;
         }
         mark(S, PH_REFINE);
@@ -1147,7 +1200,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const Params P) {
 // The FP32 form: FP64 refinement around FP32 inner solves, the whole grid one team.
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) refine_kernel(const Params P, const ParamsF F) {
-    __shared__ SolveSmemT<float> S;
+    __shared__ SolveSmem S;
     extern __shared__ __align__(16) unsigned char dsmem[];
     enter_team(P);
     init_solve_smem(S, P);
@@ -1162,8 +1215,7 @@ __global__ void __launch_bounds__(NT, 1) refine_kernel(const Params P, const Par
 template <bool F32, int NT>
 __global__ void __launch_bounds__(NT, 1)
     batched_solve_kernel(const SysPair *sys, const int *plan, int stride, int team) {
-    using SV = typename std::conditional<F32, float, double>::type;
-    __shared__ SolveSmemT<SV> S;
+    __shared__ SolveSmem S;
     __shared__ Params SP;
     __shared__ ParamsF SF;
     extern __shared__ __align__(16) unsigned char dsmem[];
