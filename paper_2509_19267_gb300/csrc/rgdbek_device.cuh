@@ -283,6 +283,118 @@ __device__ __forceinline__ float block_max(float v, BlockScratch &bs) {
     return __int_as_float((int)bs.i[32]);
 }
 
+// ---------------------------------------------------------------------------
+// Sums of nonnegative doubles in fixed point (order-independent, no FP64 adds)
+//
+// On GB300 a dependent FP64 add costs 64 cycles, and several hundred while
+// other warps of the SM issue FP64 work, so a tree of FP64 adds on the
+// critical path of every inner-solver phase is slow.  These sums instead align
+// every term to the largest exponent of the set and add the significands as
+// 64-bit integers: exact integer arithmetic, so the result does not depend on
+// the order of the terms, and each term is truncated to a multiple of
+// 2^(e_max - 52 - h), h = the headroom bits left for the count of terms.  The
+// relative error is below count * 2^-(52 + h) of the largest term, about 1e-14
+// for a thousand terms, against about count * 2^-53 for an FP64 add tree.
+// Inputs must be nonnegative (sums of squares); a NaN or infinite term gives
+// a NaN result.  One integer-to-double conversion and one power-of-two
+// multiply remain in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fx_headroom(int count) {
+    // 63 bits hold count terms below 2^(53 + shift) when count <= 2^(10 - shift)
+    int h = 0;
+    while ((1 << h) < count) ++h;
+    return h;
+}
+// significand of a nonnegative finite double aligned to exponent emax, with
+// `shift` extra low bits (shift = 63 - 53 - headroom >= 0)
+__device__ __forceinline__ unsigned long long fx_term(unsigned long long bits, int emax, int shift) {
+    const int e = (int)(bits >> 52);
+    if (e == 0) return 0ull;  // zero (subnormal terms are far below any nonzero sum here)
+    const unsigned long long m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int d = emax - e;
+    return d < 64 ? (m << shift) >> d : 0ull;
+}
+// the fixed-point sum back to a double: acc * 2^(emax - 1075 - shift)
+__device__ __forceinline__ double fx_value(unsigned long long acc, int emax, int shift) {
+    if (emax == 0x7ff) return __longlong_as_double(0x7ff8000000000000ll);  // NaN or Inf term
+    if (emax == 0) return 0.0;
+    const int e2 = emax - 52 - shift;  // biased exponent of the unit 2^(emax - 1075 - shift)
+    if (e2 <= 0) return __ull2double_rn(acc) * 0.0;  // below the normal range: zero
+    return __ull2double_rn(acc) * __longlong_as_double((long long)e2 << 52);
+}
+
+// Sum of the per-CTA partials p[0..nb) (nonnegative) by one warp, nb <=
+// kMaxGrid; every lane returns it.  Up to 256 partials are held in registers
+// (one load each); more are loaded twice.
+__device__ __forceinline__ double warp_sum_fixed(const double *p, int nb) {
+    const int lane = threadIdx.x & 31;
+    const int shift = 10 - fx_headroom(nb);
+    long long mx = 0;
+    unsigned long long acc = 0;
+    if (nb <= 256) {
+        unsigned long long b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = lane + 32 * q;
+            b[q] = i < nb ? (unsigned long long)__double_as_longlong(__ldcg(p + i)) : 0ull;
+            mx = max(mx, (long long)b[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        const int emax = (int)((unsigned long long)mx >> 52);
+        if (emax < 0x7ff) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc += fx_term(b[q], emax, shift);
+        }
+    } else {
+        for (int i = lane; i < nb; i += 32) mx = max(mx, __double_as_longlong(__ldcg(p + i)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        const int emax = (int)((unsigned long long)mx >> 52);
+        if (emax < 0x7ff)
+            for (int i = lane; i < nb; i += 32)
+                acc += fx_term((unsigned long long)__double_as_longlong(__ldcg(p + i)), emax, shift);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    return fx_value(acc, (int)((unsigned long long)mx >> 52), shift);
+}
+
+// Sum over the CTA of one nonnegative double per thread (blockDim <= 1024);
+// every thread returns it.
+__device__ __forceinline__ double block_sum_fixed(double v, BlockScratch &bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    long long mx = (long long)bits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    __syncthreads();
+    if (lane == 0) bs.i[warp] = mx;
+    __syncthreads();
+    if (warp == 0) {
+        long long r = lane < nw ? bs.i[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(kFull, r, o));
+        if (lane == 0) bs.i[33] = r;
+    }
+    __syncthreads();
+    const int emax = (int)((unsigned long long)bs.i[33] >> 52);
+    const int shift = 10 - fx_headroom((int)blockDim.x);
+    unsigned long long q = emax < 0x7ff ? fx_term(bits, emax, shift) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+    if (lane == 0) bs.u[warp] = q;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long r = lane < nw ? bs.u[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+        if (lane == 0) bs.d[33] = fx_value(r, emax, shift);
+    }
+    __syncthreads();
+    return bs.d[33];
+}
+
 // Exclusive scan of one value per thread in thread order; *total gets the sum.
 template <typename T>
 __device__ __forceinline__ T block_excl_scan(T v, BlockScratch &bs, T *total) {

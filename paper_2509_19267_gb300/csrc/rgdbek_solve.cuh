@@ -370,14 +370,27 @@ __device__ __forceinline__ void cta_dots(const CtaSide<V> &C, const V *vec, V *d
     }
 }
 
-// Warp 0: sum of the per-CTA partials of one slot (fixed order), for lane 0.
+// Warp 0: sum of the per-CTA partials of one slot, for lane 0.  FP64: the
+// order-independent fixed-point sum (no FP64 adds on the critical path of the
+// phase); FP32: float adds in a fixed order.
 template <typename V>
 __device__ __forceinline__ V warp0_collect(const V *pd, int slot, int nb) {
-    const V *p = pd + slot * nb;
-    V s = V(0);
+    if constexpr (sizeof(V) == 8) {
+        return warp_sum_fixed(pd + slot * nb, nb);
+    } else {
+        const V *p = pd + slot * nb;
+        V s = V(0);
 #pragma unroll 8
-    for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
-    return warp_sum(s);
+        for (int i = threadIdx.x; i < nb; i += 32) s += __ldcg(p + i);
+        return warp_sum(s);
+    }
+}
+
+// CTA sum of the squares the LSQR combine forms (FP64: fixed point, as above).
+template <typename V>
+__device__ __forceinline__ V lsqr_block_sum(V v, BlockScratch &bs) {
+    if constexpr (sizeof(V) == 8) return block_sum_fixed(v, bs);
+    else return block_sum(v, bs);
 }
 
 // LSQR from y = 0 on the block (R, C) with right-hand side c0 (u-space,
@@ -466,7 +479,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
             P.vv[CC.lo + li] = v;
             acc = vfma(v, v, acc);
         }
-        acc = block_sum(acc, S.bs);
+        acc = lsqr_block_sum(acc, S.bs);
         if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
         if (threadIdx.x < 32) {
@@ -500,9 +513,11 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
                 // alpha_{i+1} = ||v~||; the divisions of the recurrence are
                 // multiplications by reciprocals formed with rsqrt, which keeps
                 // the dependent chain of this single thread short
+                // alpha = vv * rsqrt(vv): one reciprocal square root serves both
                 const V cs = L.cs, sn = L.sn, bn = L.beta;
-                const V an = bn > V(0) ? vsqrt(vv) : V(0);
-                const V ian = an > V(0) ? vrsqrt(vv) : V(0);
+                const V ivv = vv > V(0) ? vrsqrt(vv) : V(0);
+                const V an = bn > V(0) ? vv * ivv : V(0);
+                const V ian = an > V(0) ? ivv : V(0);
                 L.rhobar = -cs * an;
                 L.wcoef = sn * an * L.irho;   // theta / rho
                 const V rnorm = L.phibar;
@@ -536,7 +551,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
                 if (st_smem) uold[li] = u;
                 acc = vfma(u, u, acc);
             }
-            acc = block_sum(acc, S.bs);
+            acc = lsqr_block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_UU * tsize(P) + trank(P)] = acc;
         }
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
@@ -546,15 +561,16 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
         if (threadIdx.x < 32) {
             const V uu = warp0_collect(P.pd, D_UU, tsize(P));
             if (threadIdx.x == 0) {
-                // beta_{i+1} = ||u~||, rho = sqrt(rhobar^2 + beta^2); 1/rho from
-                // rsqrt of rho^2 directly, in parallel with sqrt(||u~||^2)
-                const V bn = vsqrt(uu);
+                // beta_{i+1} = ||u~|| = uu * rsqrt(uu), rho = sqrt(rhobar^2 +
+                // beta^2); 1/rho from rsqrt of rho^2 directly, in parallel
+                const V iuu = uu > V(0) ? vrsqrt(uu) : V(0);
+                const V bn = uu * iuu;
                 const V irho = vrsqrt(vfma(L.rhobar, L.rhobar, uu));
                 const V cs = L.rhobar * irho, sn = bn * irho;
                 const V phi = cs * L.phibar;
                 L.phibar = sn * L.phibar;
                 L.mv = bn > V(0);
-                L.inv_b = bn > V(0) ? vrsqrt(uu) : V(0);
+                L.inv_b = bn > V(0) ? iuu : V(0);
                 L.ba = bn * L.inv_a;           // beta / alpha
                 L.phi_rho = phi * irho;
                 L.beta = bn;
@@ -582,7 +598,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
                 y_g[CC.lo + li] = dloc ? y * dl : y;   // y = D y^ when scaled
                 if (xt) xt[CC.lo + li] = P.x[CC.lo + li] + y;
             }
-            acc = block_sum(acc, S.bs);
+            acc = lsqr_block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
         }
         if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
