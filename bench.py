@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--cpu-repeats", type=int, default=1,
                     help="full oracle solves timed for cpu_baseline (the median is reported)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-spmv-large", action="store_true",
+                    help="skip the 2000000 x 500000 SpMV bandwidth measurement")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the secondary solve with the adaptive inner tolerance")
     ap.add_argument("--workload", default="sparse_ls",
@@ -75,6 +77,10 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--budget", type=int, default=None,
                     help="outer iterations per system (batched_deblur, poisson_mixed)")
+    ap.add_argument("--inner-max", type=int, default=None,
+                    help="LSQR step cap per block solve (batched_deblur)")
+    ap.add_argument("--fp32", action="store_true",
+                    help="batched_deblur: the FP32 form (FP64 refinement) instead of FP64")
     return ap.parse_args()
 
 
@@ -372,6 +378,9 @@ def run_ours(args):
 
     # standalone SpMV kernels (the a1 / a5 products), L2 flushed before each launch
     spmv = spmv_rooflines(rg, solver, S, dev, flush, peak)
+    spmv_big = None
+    if not args.no_spmv_large and rank == 0:
+        spmv_big = spmv_large(rg, dev, flush, peak)
 
     # secondary figure: the same solve with the inner tolerance tied to the
     # outer residual (inner_adapt = 0.1); the headline keeps the fixed one
@@ -440,6 +449,7 @@ def run_ours(args):
                 "us_per_phase": 1e6 * statistics.median(ms) / 1e3 / max(
                     1, 14 * st0.iters + 2 * (st0.inner_u + st0.inner_j))},
             "spmv": spmv,
+            "spmv_large": spmv_big,
             "adaptive_inner": adaptive,
             "eta_tuning": eta,
             "fp32_inner": fp32,
@@ -530,6 +540,58 @@ def spmv_rooflines(rg, solver, S, dev, flush, peak):
                              "frac": 16 * half / t / 1e9 / peak}
     for name in ("csr_Ax", "csc_ATz"):
         out[name]["frac_of_same_size_copy"] = out[name]["GB/s"] / out["same_size_copy"]["GB/s"]
+    return out
+
+
+SPMV_LARGE = dict(m=2000000, n=500000, k=20, seed=7)
+
+
+def spmv_large(rg, dev, flush, peak):
+    """The full-matrix products (a1 A^T z over the CSC copy, a5 A x over the
+    CSR form) on the benchmark's recipe at 2000000 x 500000 (40M nonzeros,
+    480 MB per copy of A: far larger than L2), after rgdbek_tune_spmv chose
+    the lane split of each; L2 flushed before every timed launch."""
+    import torch
+    w = SPMV_LARGE
+    t0 = time.perf_counter()
+    S = workloads.sparse_ls(w["m"], w["n"], w["k"], sigma=1e-2, seed=w["seed"])
+    gen_s = time.perf_counter() - t0
+    s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals)
+    default = (s.info().lanes_per_row, s.info().lanes_per_col)
+    lr, lc, us_r, us_c = rg.rgdbek_tune_spmv(s.handle, reps=10)
+    xv = torch.randn(S.n, dtype=torch.float64, device=dev)
+    zv = torch.randn(S.m, dtype=torch.float64, device=dev)
+    y = torch.empty(S.m, dtype=torch.float64, device=dev)
+    g = torch.empty(S.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"sparse_ls_{S.m}x{S.n}_k{w['k']} (seed {w['seed']})", "nnz": S.nnz,
+           "generate_s": gen_s, "default_lanes": {"row": default[0], "col": default[1]},
+           "tuned_lanes": {"row": lr, "col": lc},
+           "tuner_us": {"csr": {str(k): round(v, 2) for k, v in us_r.items()},
+                        "csc": {str(k): round(v, 2) for k, v in us_c.items()}}}
+    cases = {"csr_Ax": (lambda: rg.rgdbek_spmv(s.handle, xv, y),
+                        12 * S.nnz + 8 * (S.m + 1) + 8 * S.n + 8 * S.m),
+             "csc_ATz": (lambda: rg.rgdbek_spmv_t(s.handle, zv, g),
+                         12 * S.nnz + 8 * (S.n + 1) + 8 * S.m + 8 * S.n)}
+    for name, (fn, nbytes) in cases.items():
+        fn()
+        ts = []
+        for i in range(10):
+            a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(float(i))
+            torch.cuda._sleep(400000)
+            a.record(stream)
+            fn()
+            bb.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(bb) / 1e3)
+        t = statistics.median(ts)
+        gbs = nbytes / t / 1e9
+        out[name] = {"us": t * 1e6, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / peak,
+                     "fp64_tflops": 2 * S.nnz / t / 1e12,
+                     "fp64_frac_of_nominal": 2 * S.nnz / t / 1e12 / FP64_PEAK_TFLOPS}
+    s.close()
+    del S
     return out
 
 
@@ -698,6 +760,10 @@ def run_batched_deblur(args):
     S = workloads.blur_batch(args.batch_count, 64, 512, seed=3)
     gen_s = time.perf_counter() - t0
     opts = dict(eta_col=0.1, eta_row=0.1, stop_rule=rg.STOP_REL_RES)
+    if args.inner_max:
+        opts["inner_max"] = args.inner_max
+    if args.fp32:
+        opts["precision"] = rg.PRECISION_FP32_INNER
     hs = [rg.Solver(s.m, s.n, s.row_ptr, s.col_idx, s.vals, **opts) for s in S]
     H = [h.handle for h in hs]
     bs = [torch.from_numpy(s.b).cuda() for s in S]
@@ -724,6 +790,14 @@ def run_batched_deblur(args):
     ms_seq, outs_seq = _timed(torch, sequential, 1)
     seq_value = outs_seq[0] / (ms_seq[0] / 1e3)
     rel = [st.rel_res for st in outs[0][1]]
+    # roofline of the batched launch: the algorithmic bytes of every system's
+    # solve (from its own counters) over the launch's CUDA-event time
+    peak, peak_kind = measured_peaks()
+    sts = outs[0][1]
+    alg = sum(algorithmic_bytes(st, s.m, s.n, s.nnz) for st, s in zip(sts, S))
+    t_launch = statistics.median(ms) / 1e3
+    inner_max = opts.get("inner_max", 200)
+    row_steps = [st.inner_j / max(st.iters, 1) for st in sts]
     line = {"metric": f"batched RGDBEK system-iterations/s ({len(S)} deblur systems, "
                       f"{budget}-iteration budget each)",
             "value": value, "unit": "system-iters/s", "n_gpus": 1, "steps": args.steps,
@@ -743,6 +817,17 @@ def run_batched_deblur(args):
             "speedup_vs_sequential": value / seq_value,
             "rel_res_after_budget": {"min": min(rel), "median": statistics.median(rel),
                                      "max": max(rel)},
+            "roofline": {"bound": "hbm", "achieved": alg / t_launch / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": alg / t_launch / 1e9 / peak, "traffic": None,
+                         "kernel": "batched_solve_kernel (one launch per step)",
+                         "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg},
+            "inner_max": inner_max,
+            "row_lsqr_steps_per_iteration": {"min": min(row_steps),
+                                             "median": statistics.median(row_steps),
+                                             "max": max(row_steps)},
+            "col_lsqr_steps_per_iteration": statistics.median(
+                [st.inner_u / max(st.iters, 1) for st in sts]),
+            "precision": "fp32 inner / fp64 refinement" if args.fp32 else "fp64",
             "generate_s": gen_s, "gpu_launches": args.steps * 4, "clocks": clk}
     print(json.dumps(line), flush=True)
     for h in hs:

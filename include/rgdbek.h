@@ -145,8 +145,8 @@ typedef struct {
     int64_t m, n, nnz;
     int grid;              /* CTAs of the persistent solve kernel                */
     int threads_per_block;
-    int lanes_per_row;     /* lanes that share one CSR row in the A x products   */
-    int lanes_per_col;     /* lanes that share one CSC column in A^T z products  */
+    int lanes_per_row;     /* lanes that share one CSR row in the A x passes     */
+    int lanes_per_col;     /* lanes that share one CSC column in the A^T z passes */
     int num_sms;
     int64_t device_bytes;  /* device memory the handle uses (with its matrix)    */
 } rgdbek_info_t;
@@ -281,6 +281,26 @@ int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candid
  * first error (the options are then left as they were). */
 int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uint64_t seed,
                 int *block_out, double *ms_out);
+
+/* Autotuner of the work split of the full-matrix passes (A^T z and b - A x
+ * of every outer iteration, the FP64 passes of the refinement loop and the
+ * component SpMVs): for each candidate of RGDBEK_SPMV_LANE_CANDIDATES lanes
+ * per CSR row (1, 2, 4, 8, 16, 32) it times reps launches of the CSR product
+ * (after one warm-up launch), and likewise per CSC column for the CSC
+ * product, with CUDA events on the handle's stream, and keeps the fastest of
+ * each for the handle (rgdbek_get_info reports them as lanes_per_row /
+ * lanes_per_col).  The sums of each pass are taken in a different order per
+ * lane count, so a solve's rounding (not its limit) depends on the choice.
+ * us_out: host double[2 * RGDBEK_SPMV_LANE_CANDIDATES] (may be NULL), the
+ * median time in microseconds of each candidate, CSR first.  The handle's
+ * workspace serves as input and output vectors (zeros).  Returns OK,
+ * INVALID_ARG (reps < 1), CUDA. */
+#define RGDBEK_SPMV_LANE_CANDIDATES 6
+int rgdbek_tune_spmv(rgdbek_t h, int reps, int *lanes_row, int *lanes_col, double *us_out);
+
+/* Sets the lanes per row / column of the full-matrix passes by hand (powers
+ * of two in [1, 32]; the default is about sixteen entries per lane). */
+int rgdbek_set_pass_lanes(rgdbek_t h, int lanes_row, int lanes_col);
 
 /* Implicit adjoint of the solve (reverse-mode gradient).  The method
  * converges to x = A^+ b, the minimum-norm least-squares solution (the

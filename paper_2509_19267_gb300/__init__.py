@@ -118,6 +118,9 @@ SIGNATURES = [
                            ctypes.POINTER(_dbl)]),
     ("rgdbek_tune_eta", _int, [_ptr, _ptr, _ptr, _ptr, _int, _i64, _u64,
                                ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
+    ("rgdbek_tune_spmv", _int, [_ptr, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                ctypes.POINTER(_dbl)]),
+    ("rgdbek_set_pass_lanes", _int, [_ptr, _int, _int]),
     ("rgdbek_backward", _int, [_ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _i64, _u64, _int,
                                ctypes.POINTER(rgdbek_stats)]),
     ("rgdbek_set_trace", _int, [_ptr, _ptr, _i64, _ptr, _i64]),
@@ -325,6 +328,25 @@ def rgdbek_tune_eta(h: int, b, x, candidates=None, probe_iters: int = 20, seed: 
                                 0 if candidates is None else len(cands), probe_iters, seed,
                                 ctypes.byref(best), rate), "rgdbek_tune_eta")
     return best.value, {c: rate[i] for i, c in enumerate(cands)}
+
+
+SPMV_LANE_CANDIDATES = (1, 2, 4, 8, 16, 32)
+
+
+def rgdbek_tune_spmv(h: int, reps: int = 10):
+    """Times each lane split of the full-matrix passes and keeps the fastest.
+    Returns (lanes_row, lanes_col, {lanes: us} for CSR, {lanes: us} for CSC)."""
+    lr, lc = _int(0), _int(0)
+    nc = len(SPMV_LANE_CANDIDATES)
+    us = (_dbl * (2 * nc))()
+    _check(_lib.rgdbek_tune_spmv(h, reps, ctypes.byref(lr), ctypes.byref(lc), us),
+           "rgdbek_tune_spmv")
+    return (lr.value, lc.value, dict(zip(SPMV_LANE_CANDIDATES, list(us)[:nc])),
+            dict(zip(SPMV_LANE_CANDIDATES, list(us)[nc:])))
+
+
+def rgdbek_set_pass_lanes(h: int, lanes_row: int, lanes_col: int) -> None:
+    _check(_lib.rgdbek_set_pass_lanes(h, lanes_row, lanes_col), "rgdbek_set_pass_lanes")
 
 
 ADJ_RANK_TERM = 1

@@ -68,6 +68,7 @@ struct rgdbek_s {
     double *adj_ax, *adj_w, *adj_v, *adj_u, *adj_ag, *adj_q;
     // launch shape
     int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
+    int lpr = 1, lpc = 1;  // lanes of the full-matrix passes (rgdbek_tune_spmv)
     int tuned_team = 0;   // team size found by rgdbek_tune_batched (0 = none yet)
     int tuned_block = 0;  // block of the batched solve found by it (0 = automatic)
     // trace
@@ -274,6 +275,8 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.time_budget_ns = h->opt.time_budget_s * 1e9;
     P.tpr = h->tpr;
     P.tpc = h->tpc;
+    P.lpr = h->lpr;
+    P.lpc = h->lpc;
     P.ipr = h->ipr;
     P.ipc = h->ipc;
     P.dsmem_bytes = kSolveDsmemBytes;
@@ -291,6 +294,8 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
         P.cn2 = h->rn2;
         P.tpr = h->tpc;
         P.tpc = h->tpr;
+        P.lpr = h->lpc;
+        P.lpc = h->lpr;
         P.ipr = h->ipc;
         P.ipc = h->ipr;
         P.tr_counts = nullptr;
@@ -388,6 +393,8 @@ ParamsF make_params_f(const rgdbek_s *h, const Params &P, bool transposed) {
     F.dsr = h->f_dsr;
     F.tpr = P.tpr;
     F.tpc = P.tpc;
+    F.lpr = P.lpr;
+    F.lpc = P.lpc;
     F.ipr = P.ipr;
     F.ipc = P.ipc;
     F.dsmem_bytes = P.dsmem_bytes;
@@ -722,6 +729,8 @@ int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_
     }
     h->tpr = pick_lanes_fp64(nnz, m);
     h->tpc = pick_lanes_fp64(nnz, n);
+    h->lpr = h->tpr;
+    h->lpc = h->tpc;
     h->ipr = pick_lanes_int(nnz, m);
     h->ipc = pick_lanes_int(nnz, n);
 
@@ -827,6 +836,8 @@ int rgdbek_create_like(rgdbek_t base, const rgdbek_options *opt, void *stream, r
     h->stream = (cudaStream_t)stream;
     h->tpr = base->tpr;
     h->tpc = base->tpc;
+    h->lpr = base->lpr;
+    h->lpc = base->lpc;
     h->ipr = base->ipr;
     h->ipc = base->ipc;
     int dev = -1;
@@ -903,8 +914,8 @@ int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
     info->nnz = h->nnz;
     info->grid = h->grid;
     info->threads_per_block = h->block;
-    info->lanes_per_row = h->tpr;
-    info->lanes_per_col = h->tpc;
+    info->lanes_per_row = h->lpr;
+    info->lanes_per_col = h->lpc;
     info->num_sms = h->num_sms;
     info->device_bytes = (int64_t)(h->arena_bytes + (h->mat ? h->mat->bytes : 0));
     return RGDBEK_OK;
@@ -1212,6 +1223,65 @@ int rgdbek_backward(rgdbek_t h, const double *b, const double *x, const double *
                                 rank_term ? h->adj_q : nullptr, grad_vals, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? worst : cuda_status(e);
+}
+
+int rgdbek_tune_spmv(rgdbek_t h, int reps, int *lanes_row, int *lanes_col, double *us_out) {
+    if (!h || reps < 1) return RGDBEK_ERR_INVALID_ARG;
+    static const int kCand[RGDBEK_SPMV_LANE_CANDIDATES] = {1, 2, 4, 8, 16, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // input and output vectors from the handle's workspace (zeros: the time of
+    // a pass does not depend on the values)
+    double *xin = h->ref_x, *zin = h->ref_b, *out = h->ref_t;
+    const long long mx = h->m > h->n ? h->m : h->n;
+    if (e == cudaSuccess) e = cudaMemsetAsync(xin, 0, (size_t)mx * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zin, 0, (size_t)mx * sizeof(double), h->stream);
+    int best[2] = {h->lpr, h->lpc};
+    for (int side = 0; side < 2 && e == cudaSuccess; ++side) {
+        float best_us = 0.f;
+        for (int c = 0; c < RGDBEK_SPMV_LANE_CANDIDATES && e == cudaSuccess; ++c) {
+            Params P = make_params(h);
+            if (side == 0) P.lpr = kCand[c];
+            else P.lpc = kCand[c];
+            std::vector<float> ts;
+            for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, h->stream);
+                if (e == cudaSuccess)
+                    e = side == 0 ? launch_spmv(P, h->num_sms, kSolveMaxThreads, xin, out, h->stream)
+                                  : launch_spmv_t(P, h->num_sms, kSolveMaxThreads, zin, out, h->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) ts.push_back(1e3f * ms);  // the first launch warms up
+            }
+            if (e != cudaSuccess) break;
+            std::sort(ts.begin(), ts.end());
+            const float us = ts[ts.size() / 2];
+            if (us_out) us_out[side * RGDBEK_SPMV_LANE_CANDIDATES + c] = us;
+            if (c == 0 || us < best_us) {
+                best_us = us;
+                best[side] = kCand[c];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->lpr = best[0];
+    h->lpc = best[1];
+    if (lanes_row) *lanes_row = best[0];
+    if (lanes_col) *lanes_col = best[1];
+    return RGDBEK_OK;
+}
+
+int rgdbek_set_pass_lanes(rgdbek_t h, int lanes_row, int lanes_col) {
+    auto ok = [](int L) { return L >= 1 && L <= 32 && (L & (L - 1)) == 0; };
+    if (!h || !ok(lanes_row) || !ok(lanes_col)) return RGDBEK_ERR_INVALID_ARG;
+    h->lpr = lanes_row;
+    h->lpc = lanes_col;
+    return RGDBEK_OK;
 }
 
 int rgdbek_spmv(rgdbek_t h, const double *x, double *y) {

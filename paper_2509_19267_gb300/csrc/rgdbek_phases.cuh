@@ -87,7 +87,10 @@ struct ParamsT {
     // b - A x (m), the scaled right-hand side (m) and solution (n) of an FP64
     // inner solve
     V *ref_t, *ref_b, *ref_x;
-    int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A in the passes
+    int tpr, tpc;           // lanes per row (CSR) / column (CSC) of A: block extraction
+                            // and the selected lines of the inner solves
+    int lpr, lpc;           // lanes per row / column of A in the full-matrix passes
+                            // (A^T z, b - A x, the component SpMVs; tunable)
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
 };
@@ -308,7 +311,7 @@ __device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L
 
 // y = A x (rows of the CSR form, L lanes per row).  Component entry point.
 __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, double *y) {
-    const Grp G(P.tpr);
+    const Grp G(P.lpr);
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         double s = 0.0;
@@ -322,7 +325,7 @@ __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, 
 
 // g = A^T z (columns of the CSC form, L lanes per column).  Component entry point.
 __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, double *gout) {
-    const Grp G(P.tpc);
+    const Grp G(P.lpc);
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
         double s = 0.0;
@@ -342,7 +345,7 @@ __device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, 
 template <typename V>
 __device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs) {
     using V2 = typename Vec2<V>::type;
-    const Grp G(P.tpc);
+    const Grp G(P.lpc);
     V emax = V(0), hh = V(0), gg = V(0);
     long long bad = 0;
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
@@ -380,7 +383,7 @@ __device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs)
 // t_{k+1} = b - A x_{k+1} over the CSR rows, x_{k+1} = xt.  Partial: ||t||^2.
 template <typename V>
 __device__ __forceinline__ void phase_residual(const ParamsT<V> &P, BlockScratch &bs) {
-    const Grp G(P.tpr);
+    const Grp G(P.lpr);
     V tt = V(0);
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;

@@ -994,7 +994,7 @@ constexpr int kRefineStallSteps = 3;
 
 // t_i = b_i - (A x)_i over the CSR rows in FP64, into t (m).  Partial: ||t||^2.
 __device__ __forceinline__ void phase_outer_residual(const Params &P, double *t, BlockScratch &bs) {
-    const Grp G(P.tpr);
+    const Grp G(P.lpr);
     double tt = 0.0;
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
@@ -1017,7 +1017,7 @@ __device__ __forceinline__ void phase_outer_residual(const Params &P, double *t,
 // into partial slot `slot`.
 __device__ __forceinline__ void phase_outer_normal(const Params &P, const double *v, int slot,
                                                    BlockScratch &bs) {
-    const Grp G(P.tpc);
+    const Grp G(P.lpc);
     double hh = 0.0;
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;

@@ -620,3 +620,44 @@ def test_selection_replay_over_a_whole_run(rg, selection):
     assert st.iters == 20 and len(blocks) == 20
     assert np.all(np.isfinite(g)) and np.all(np.isfinite(r))
     _replay(rg, blocks, g, r, rn2, cn2, eta, eta, seed=17, greedy=selection == 1)
+
+
+def test_pass_lane_tuner_and_every_lane_split(rg):
+    """rgdbek_tune_spmv times each lane split of the full-matrix passes and
+    keeps the fastest; every split (set by hand) gives the products within
+    1e-13 of the oracle's (relative to the sum of |terms|), and a solve with
+    the tuned split still meets the 1e-8 bar against the oracle."""
+    import ctypes
+    import torch
+    S = workloads.sparse_ls(20000, 5000, 20, sigma=1e-2, seed=4)
+    rng = np.random.default_rng(2)
+    x, z = rng.standard_normal(S.n), rng.standard_normal(S.m)
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=0.2, eta_row=0.2, stop_rule=rg.STOP_NORMAL)
+    Aabs = (S.A[0], S.A[1], np.abs(S.A[2]))
+    scale_y = oracle.spmv(Aabs, np.abs(x)) + 1e-300
+    scale_g = oracle.spmv_t(Aabs, np.abs(z), S.n) + 1e-300
+    y = torch.empty(S.m, dtype=torch.float64, device="cuda")
+    g = torch.empty(S.n, dtype=torch.float64, device="cuda")
+    for L in rg.SPMV_LANE_CANDIDATES:
+        rg.rgdbek_set_pass_lanes(s.handle, L, L)
+        info = s.info()
+        assert (info.lanes_per_row, info.lanes_per_col) == (L, L)
+        rg.rgdbek_spmv(s.handle, G.dev(x), y)
+        rg.rgdbek_spmv_t(s.handle, G.dev(z), g)
+        torch.cuda.synchronize()
+        assert np.all(np.abs(G.host(y) - oracle.spmv(S.A, x)) <= 1e-13 * scale_y), L
+        assert np.all(np.abs(G.host(g) - oracle.spmv_t(S.A, z, S.n)) <= 1e-13 * scale_g), L
+    for bad in (0, 3, 64):
+        assert rg._lib.rgdbek_set_pass_lanes(ctypes.c_void_p(s.handle), bad, 1) == rg.ERR_INVALID_ARG
+    assert rg._lib.rgdbek_tune_spmv(ctypes.c_void_p(s.handle), 0, None, None, None) \
+        == rg.ERR_INVALID_ARG
+    lr, lc, us_r, us_c = rg.rgdbek_tune_spmv(s.handle, reps=5)
+    assert lr in rg.SPMV_LANE_CANDIDATES and lc in rg.SPMV_LANE_CANDIDATES
+    assert us_r[lr] == min(us_r.values()) and us_c[lc] == min(us_c.values())
+    assert (s.info().lanes_per_row, s.info().lanes_per_col) == (lr, lc)
+    res = s.solve(G.dev(S.b), tol=1e-11, max_iter=100000, seed=3)
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.2, eta_row=0.2, stop_rule=2,
+                                                tol=1e-11, max_iter=100000, seed=3), n=S.n)
+    assert res.stats.status == rg.OK
+    assert G.rel(G.host(res.x), ref.x) <= X_TOL
+    s.close()
