@@ -68,6 +68,11 @@ def parse():
     ap.add_argument("--cpu-repeats", type=int, default=1,
                     help="full oracle solves timed for cpu_baseline (the median is reported)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="the timed solve: FP64 (headline) or the FP32 form (FP32 inner "
+                         "iterations in FP64 refinement) to the same FP64 tolerance")
+    ap.add_argument("--only-spmv-large", action="store_true",
+                    help="print only the 2000000 x 500000 SpMV measurement (profiling)")
     ap.add_argument("--no-spmv-large", action="store_true",
                     help="skip the 2000000 x 500000 SpMV bandwidth measurement")
     ap.add_argument("--no-adaptive", action="store_true",
@@ -318,6 +323,13 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     opts = dict(eta_col=w["eta"], eta_row=w["eta"], stop_rule=rg.STOP_NORMAL)
+    if args.precision == "fp32":
+        opts["precision"] = rg.PRECISION_FP32_INNER
+    if args.only_spmv_large:
+        peak, _ = measured_peaks()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"spmv_large": spmv_large(rg, dev, flush, peak)}), flush=True)
+        return
     solver = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, **opts)
     info = solver.info()
     b = torch.from_numpy(S.b).to(dev)
@@ -414,7 +426,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32 inner / f64 refinement",
             "data": "synthetic",
             "config": {"workload": w["name"], "m": S.m, "n": S.n, "nnz": S.nnz, "eta": w["eta"],
                        "tol": w["tol"], "stop_rule": w["stop_rule"],
