@@ -425,7 +425,8 @@ __device__ __forceinline__ T block_excl_scan(T v, BlockScratch &bs, T *total) {
 }
 
 // All requested partial slots reduced at once: warp w of the CTA reduces the
-// w-th requested slot (sums in a fixed order; maxima for slots in dmax), and
+// w-th requested slot (FP64 sums in fixed point, FP32 sums in a fixed order;
+// maxima for slots in dmax), and
 // the results land in out_d[slot] / out_i[slot] for every thread.  dmask /
 // imask select double / int64 slots (bit = slot).
 template <typename V>
@@ -440,12 +441,17 @@ __device__ __forceinline__ void collect_partials(const V *pd, const long long *p
             const V *p = pd + slot * nb;
             const bool mx = dmax >> slot & 1u;
             V s = V(0);
+            if (sizeof(V) == 8 && !mx) {
+                // FP64 sums (all of nonnegative terms) in fixed point
+                s = (V)warp_sum_fixed(reinterpret_cast<const double *>(p), nb);
+            } else {
 #pragma unroll 8
-            for (int i = lane; i < nb; i += 32) {
-                const V v = __ldcg(p + i);
-                s = mx ? max_nonneg(s, v) : s + v;
+                for (int i = lane; i < nb; i += 32) {
+                    const V v = __ldcg(p + i);
+                    s = mx ? max_nonneg(s, v) : s + v;
+                }
+                s = mx ? warp_max(s) : warp_sum(s);
             }
-            s = mx ? warp_max(s) : warp_sum(s);
             if (lane == 0) out_d[slot] = s;
         }
         ++w;
