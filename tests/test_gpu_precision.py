@@ -189,3 +189,37 @@ def test_fp32_inner_adjoint_matches_oracle(rg):
     assert np.abs(gb - gb_d).max() <= 1e-6 * np.abs(gb_d).max()
     Ge = Gd[rows, S.col_idx]
     assert np.abs(gv - Ge).max() <= 1e-6 * np.abs(Ge).max()
+
+
+def test_fp32_form_selections_replay_bit_exact(rg):
+    """The FP32 form's blocks are drawn from FP32 weights: eps = fl32(fl32(g^2) /
+    fl32(||A_j||^2)), quantised as floor(2^K fl32(eps / eps_max)).  The oracle's
+    sampler replays them exactly when it is given the FP32 ratios
+    fl32(eps / eps_max) (computed here with IEEE float32 operations on the GPU's
+    own recorded residuals and its float norms) as weights with eps_max = 1:
+    its FP64 division by 1 is exact and its quantisation then takes the same
+    integers.  Every block of 20 inner iterations matches byte for byte."""
+    S = workloads.sparse_ls(6000, 1500, 20, sigma=1e-2, seed=32)
+    eta = 0.1
+    s = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=eta, eta_row=eta,
+                  stop_rule=rg.STOP_NORMAL, precision=rg.PRECISION_FP32_INNER)
+    rn2, cn2 = G.gpu_norms(rg, s, S)
+    st, _, blocks, g, r, _ = G.traced_solve(rg, s, S, 20, seed=23)
+    s.close()
+    assert st.iters == 20 and len(blocks) == 20 and st.refinements == 1
+    f32 = np.float32
+    rn2f, cn2f = rn2.astype(f32), cn2.astype(f32)
+
+    def ratios(v, c):
+        v = v.astype(f32)
+        assert np.array_equal(v.astype(np.float64), v.astype(np.float64))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e = np.where(c > 0, (v * v) / np.where(c > 0, c, f32(1)), f32(0)).astype(f32)
+        return (e / e.max()).astype(f32).astype(np.float64)
+
+    for k, (U, J) in enumerate(blocks):
+        rc, rr = ratios(g[k], cn2f), ratios(r[k], rn2f)
+        Ur = oracle.sample(rc, oracle.num_draws(eta, S.n), 23, 0, k, 0, 1.0)
+        Jr = oracle.sample(rr, oracle.num_draws(eta, S.m), 23, 0, k, 1, 1.0)
+        assert Ur.tobytes() == U.tobytes(), f"U_{k} differs"
+        assert Jr.tobytes() == J.tobytes(), f"J_{k} differs"
