@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -21,7 +22,9 @@ struct MatrixStore {
     size_t bytes = 0;
     std::atomic<int> refs{1};
     // A's values and squared norms rounded to float, for the FP32 form: made
-    // by the first FP32 solve on any handle that shares this matrix
+    // by the first FP32 solve on any handle that shares this matrix, complete
+    // (its stream synchronised) before mem32 is published under the mutex
+    std::mutex mu32;
     void *mem32 = nullptr;
     float *av32 = nullptr, *cv32 = nullptr, *rn2f = nullptr, *cn2f = nullptr;
 };
@@ -402,33 +405,42 @@ ParamsF make_params_f(const rgdbek_s *h, const Params &P, bool transposed) {
 }
 
 // The float copies of A's values and squared norms for the FP32 form, made
-// once per matrix (and shared by the handles that share it).
+// once per matrix (and shared by the handles that share it).  The copies are
+// complete before they are published: another handle on another stream may
+// use them as soon as it sees them.
 int ensure_f32_matrix(rgdbek_s *h) {
     MatrixStore *M = h->mat;
+    std::lock_guard<std::mutex> lock(M->mu32);
     if (M->mem32) return RGDBEK_OK;
     Layout L;
+    void *p = nullptr;
+    float *av32 = nullptr, *cv32 = nullptr, *rn2f = nullptr, *cn2f = nullptr;
     for (int pass = 0; pass < 2; ++pass) {
-        M->av32 = L.take<float>(h->nnz);
-        M->cv32 = L.take<float>(h->nnz);
-        M->rn2f = L.take<float>(h->m);
-        M->cn2f = L.take<float>(h->n);
+        av32 = L.take<float>(h->nnz);
+        cv32 = L.take<float>(h->nnz);
+        rn2f = L.take<float>(h->m);
+        cn2f = L.take<float>(h->n);
         if (pass == 0) {
-            void *p = nullptr;
             const cudaError_t e = cudaMalloc(&p, L.off);
-            if (e != cudaSuccess) {
-                M->av32 = M->cv32 = M->rn2f = M->cn2f = nullptr;
-                return e == cudaErrorMemoryAllocation ? RGDBEK_ERR_OOM : RGDBEK_ERR_CUDA;
-            }
-            M->mem32 = p;
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RGDBEK_ERR_OOM : RGDBEK_ERR_CUDA;
             L = Layout();
             L.base = static_cast<char *>(p);
         }
     }
-    cudaError_t e = launch_to_float(h->av, h->nnz, M->av32, h->stream);
-    if (e == cudaSuccess) e = launch_to_float(h->cv, h->nnz, M->cv32, h->stream);
-    if (e == cudaSuccess) e = launch_to_float(h->rn2, h->m, M->rn2f, h->stream);
-    if (e == cudaSuccess) e = launch_to_float(h->cn2, h->n, M->cn2f, h->stream);
-    if (e != cudaSuccess) return RGDBEK_ERR_CUDA;
+    cudaError_t e = launch_to_float(h->av, h->nnz, av32, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->cv, h->nnz, cv32, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->rn2, h->m, rn2f, h->stream);
+    if (e == cudaSuccess) e = launch_to_float(h->cn2, h->n, cn2f, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return RGDBEK_ERR_CUDA;
+    }
+    M->av32 = av32;
+    M->cv32 = cv32;
+    M->rn2f = rn2f;
+    M->cn2f = cn2f;
+    M->mem32 = p;
     return RGDBEK_OK;
 }
 

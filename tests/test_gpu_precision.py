@@ -223,3 +223,29 @@ def test_fp32_form_selections_replay_bit_exact(rg):
         Jr = oracle.sample(rr, oracle.num_draws(eta, S.m), 23, 0, k, 1, 1.0)
         assert Ur.tobytes() == U.tobytes(), f"U_{k} differs"
         assert Jr.tobytes() == J.tobytes(), f"J_{k} differs"
+
+
+def test_fp32_form_on_handles_sharing_a_matrix(rg):
+    """Handles made with rgdbek_create_like share A, and with it the float copy
+    of A the FP32 form makes on first use: a derived handle on its own stream
+    may be the first to need it, and the base then reuses it; both solve to the
+    FP64 bar against the oracle."""
+    import torch
+    S = workloads.sparse_ls(3000, 700, 20, sigma=1e-2, seed=14)
+    base = rg.Solver(S.m, S.n, S.row_ptr, S.col_idx, S.vals, eta_col=0.1, eta_row=0.1,
+                     stop_rule=rg.STOP_NORMAL)
+    side = torch.cuda.Stream()
+    derived = rg.Solver.like(base, stream=side, precision=rg.PRECISION_FP32_INNER)
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.1, eta_row=0.1, stop_rule=2,
+                                                tol=1e-12, max_iter=100000), n=S.n)
+    with torch.cuda.stream(side):
+        bd = G.dev(S.b)
+        rd = derived.solve(bd, tol=1e-11, max_iter=100000, seed=2)
+    side.synchronize()
+    base.set_options(precision=rg.PRECISION_FP32_INNER)
+    rb = base.solve(G.dev(S.b), tol=1e-11, max_iter=100000, seed=2)
+    assert rd.stats.status == rg.OK and rb.stats.status == rg.OK
+    assert G.rel(G.host(rd.x), ref.x) <= 1e-8
+    assert G.rel(G.host(rb.x), ref.x) <= 1e-8
+    derived.close()
+    base.close()
