@@ -362,6 +362,14 @@ int rgdbek_set_trace_vectors(rgdbek_t h, double *g, double *r, int64_t iters_cap
 /* y = A x: x device double[n], y device double[m]  (CSR product). */
 int rgdbek_spmv(rgdbek_t h, const double *x, double *y);
 
+/* The FP32 form's products with the float copy of A (values rounded to float,
+ * made on first use and kept with the matrix): transposed = 0 gives y = A x
+ * (x device float[n], y device float[m], CSR), transposed = 1 gives
+ * y = A^T x (x device float[m], y device float[n], CSC); each lane's share of a
+ * line is summed with Kahan compensation, the lanes then in float.  Errors:
+ * INVALID_ARG, OOM (the float copy), CUDA. */
+int rgdbek_spmv_f32(rgdbek_t h, int transposed, const float *x, float *y);
+
 /* g = A^T z: z device double[m], g device double[n]  (CSC product). */
 int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g);
 

@@ -127,6 +127,7 @@ SIGNATURES = [
     ("rgdbek_set_trace_vectors", _int, [_ptr, _ptr, _ptr, _i64]),
     ("rgdbek_spmv", _int, [_ptr, _ptr, _ptr]),
     ("rgdbek_spmv_t", _int, [_ptr, _ptr, _ptr]),
+    ("rgdbek_spmv_f32", _int, [_ptr, _int, _ptr, _ptr]),
     ("rgdbek_weights", _int, [_ptr, _int, _ptr, _ptr, ctypes.POINTER(_dbl)]),
     ("rgdbek_sample", _int, [_ptr, _ptr, _i64, _i64, _u64, _u64, _i64, _int, _ptr,
                              ctypes.POINTER(_i64)]),
@@ -389,6 +390,11 @@ def rgdbek_set_trace_vectors(h: int, g=None, r=None) -> None:
 
 def rgdbek_spmv(h: int, x, y) -> None:
     _check(_lib.rgdbek_spmv(h, _dptr(x), _dptr(y)), "rgdbek_spmv")
+
+
+def rgdbek_spmv_f32(h: int, transposed: int, x, y) -> None:
+    """FP32 products with the float copy of A: y = A x, or y = A^T x."""
+    _check(_lib.rgdbek_spmv_f32(h, int(transposed), _dptr(x), _dptr(y)), "rgdbek_spmv_f32")
 
 
 def rgdbek_spmv_t(h: int, z, g) -> None:

@@ -1301,6 +1301,16 @@ int rgdbek_spmv(rgdbek_t h, const double *x, double *y) {
     return cuda_status(launch_spmv(make_params(h), h->num_sms, kSolveMaxThreads, x, y, h->stream));
 }
 
+int rgdbek_spmv_f32(rgdbek_t h, int transposed, const float *x, float *y) {
+    if (!h || !x || !y || (transposed != 0 && transposed != 1)) return RGDBEK_ERR_INVALID_ARG;
+    const int st = ensure_f32_matrix(h);
+    if (st != RGDBEK_OK) return st;
+    const Params P = make_params(h);
+    const ParamsF F = make_params_f(h, P, false);
+    return cuda_status(launch_spmv_f32(F, h->num_sms, kSolveMaxThreads, x, y, transposed != 0,
+                                       h->stream));
+}
+
 int rgdbek_spmv_t(rgdbek_t h, const double *z, double *g) {
     if (!h || !z || !g) return RGDBEK_ERR_INVALID_ARG;
     return cuda_status(launch_spmv_t(make_params(h), h->num_sms, kSolveMaxThreads, z, g, h->stream));

@@ -63,6 +63,10 @@ cudaError_t launch_spmv(const Params &P, int grid, int block, const double *x, d
                         cudaStream_t s);
 cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z, double *g,
                           cudaStream_t s);
+// FP32 products with the float copy of A (the FP32 form's passes): y = A x,
+// or with transposed g = A^T z
+cudaError_t launch_spmv_f32(const ParamsF &F, int grid, int block, const float *x, float *y,
+                            bool transposed, cudaStream_t s);
 // gv[e] = (b_i - ax_i) v_j - w_i x_j [+ u_i (g_j - q_j) when u != nullptr]
 // over the stored entries e = (i, j) of P's CSR form
 cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const double *b,

@@ -43,6 +43,16 @@ __global__ void __launch_bounds__(kSolveMaxThreads) spmv_t_kernel(const Params P
     enter_team(P);
     cols_matvec(P, z, g);
 }
+__global__ void __launch_bounds__(kSolveMaxThreads) spmv_f32_kernel(const ParamsF F, const float *x,
+                                                                    float *y) {
+    enter_team(F);
+    rows_matvec(F, x, y);
+}
+__global__ void __launch_bounds__(kSolveMaxThreads) spmv_t_f32_kernel(const ParamsF F,
+                                                                      const float *z, float *g) {
+    enter_team(F);
+    cols_matvec(F, z, g);
+}
 
 // Gradient of a loss with respect to the stored entries of A (the implicit
 // adjoint of x = A^+ b; Golub-Pereyra derivative of the pseudo-inverse):
@@ -225,6 +235,15 @@ cudaError_t launch_spmv_t(const Params &P, int grid, int block, const double *z,
     Params p = P;
     p.team = grid;
     spmv_t_kernel<<<grid, block, 0, s>>>(p, z, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_f32(const ParamsF &F, int grid, int block, const float *x, float *y,
+                            bool transposed, cudaStream_t s) {
+    ParamsF f = F;
+    f.team = grid;
+    if (transposed) spmv_t_f32_kernel<<<grid, block, 0, s>>>(f, x, y);
+    else spmv_f32_kernel<<<grid, block, 0, s>>>(f, x, y);
     return cudaGetLastError();
 }
 

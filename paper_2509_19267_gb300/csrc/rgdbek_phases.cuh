@@ -309,12 +309,14 @@ __device__ __forceinline__ void lane_dot2(long long e, long long e1, long long L
 // Full-matrix products
 // ---------------------------------------------------------------------------
 
-// y = A x (rows of the CSR form, L lanes per row).  Component entry point.
-__device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, double *y) {
+// y = A x (rows of the CSR form, L lanes per row).  Component entry point;
+// FP32: A's float values, Kahan-compensated lane sums (the FP32 form's passes).
+template <typename V>
+__device__ __forceinline__ void rows_matvec(const ParamsT<V> &P, const V *xin, V *y) {
     const Grp G(P.lpr);
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
-        double s = 0.0;
+        V s = V(0);
         if (i < P.m)
             s = lane_dot<true>(__ldg(P.rp + i) + G.sl, __ldg(P.rp + i + 1), G.L, P.ci, P.av,
                                [&](int j) { return xin[j]; });
@@ -324,11 +326,12 @@ __device__ __forceinline__ void rows_matvec(const Params &P, const double *xin, 
 }
 
 // g = A^T z (columns of the CSC form, L lanes per column).  Component entry point.
-__device__ __forceinline__ void cols_matvec(const Params &P, const double *zin, double *gout) {
+template <typename V>
+__device__ __forceinline__ void cols_matvec(const ParamsT<V> &P, const V *zin, V *gout) {
     const Grp G(P.lpc);
     for (long long base = twarp(P) * G.rpw; base < P.n; base += twarps(P) * G.rpw) {
         const long long j = base + G.sub;
-        double s = 0.0;
+        V s = V(0);
         if (j < P.n)
             s = lane_dot<true>(__ldg(P.cp + j) + G.sl, __ldg(P.cp + j + 1), G.L, P.ri, P.cv,
                                [&](int i) { return zin[i]; });

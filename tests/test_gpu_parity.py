@@ -97,6 +97,44 @@ def test_spmv_and_transpose(rg, case):
     s.close()
 
 
+@pytest.mark.parametrize("case", ["sparse_ragged", "sparse_ls_20000x5000"])
+def test_spmv_f32(rg, case):
+    """The FP32 form's products on the float copy of A, against the oracle's
+    FP64 products of the same float-rounded values and vectors.  Bound: each
+    product a*x rounds once, each lane's Kahan sum adds O(2u), and the tree over
+    at most 32 lanes adds 5 roundings, so |error| <= 8 u32 sum|a x|, u32 = 2^-24;
+    the test takes 1e-6 (about 17 u32)."""
+    import torch
+    if case == "sparse_ragged":
+        D = random_sparse(777, 1234, 0.01, seed=3, empty_rows=(5, 6), empty_cols=(0, 9))
+        A, (m, n) = workloads.csr_from_dense(D), D.shape
+    else:
+        S = workloads.sparse_ls(20000, 5000, 20, seed=4)
+        A, m, n = S.A, S.m, S.n
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(n).astype(np.float32)
+    z = rng.standard_normal(m).astype(np.float32)
+    A32 = (A[0], A[1], A[2].astype(np.float32).astype(np.float64))
+    s = rg.Solver(m, n, *A)
+    y = torch.empty(m, dtype=torch.float32, device="cuda")
+    g = torch.empty(n, dtype=torch.float32, device="cuda")
+    rg.rgdbek_spmv_f32(s.handle, 0, torch.from_numpy(x).cuda(), y)
+    rg.rgdbek_spmv_f32(s.handle, 1, torch.from_numpy(z).cuda(), g)
+    torch.cuda.synchronize()
+    Aabs = (A32[0], A32[1], np.abs(A32[2]))
+    xd, zd = x.astype(np.float64), z.astype(np.float64)
+    scale_y = oracle.spmv(Aabs, np.abs(xd)) + 1e-300
+    scale_g = oracle.spmv_t(Aabs, np.abs(zd), n) + 1e-300
+    assert np.all(np.abs(y.cpu().numpy() - oracle.spmv(A32, xd)) <= 1e-6 * scale_y)
+    assert np.all(np.abs(g.cpu().numpy() - oracle.spmv_t(A32, zd, n)) <= 1e-6 * scale_g)
+    # an empty row and an empty column give exact zeros
+    if case == "sparse_ragged":
+        assert y.cpu().numpy()[5] == 0.0 and g.cpu().numpy()[0] == 0.0
+    with pytest.raises(RuntimeError):
+        rg.rgdbek_spmv_f32(s.handle, 2, torch.from_numpy(x).cuda(), y)
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # Weights and block selection: bit-exact
 # ---------------------------------------------------------------------------
