@@ -84,6 +84,9 @@ def parse():
                     help="outer iterations per system (batched_deblur, poisson_mixed)")
     ap.add_argument("--inner-max", type=int, default=None,
                     help="LSQR step cap per block solve (batched_deblur)")
+    ap.add_argument("--col-team", type=int, default=None,
+                    help="CTAs of the column team of the two-team schedule (0 automatic, -1 one "
+                         "team); default: the library's automatic choice")
     ap.add_argument("--fp32", action="store_true",
                     help="batched_deblur: the FP32 form (FP64 refinement) instead of FP64")
     return ap.parse_args()
@@ -323,6 +326,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     opts = dict(eta_col=w["eta"], eta_row=w["eta"], stop_rule=rg.STOP_NORMAL)
+    if args.col_team is not None:
+        opts["col_team"] = args.col_team
     if args.precision == "fp32":
         opts["precision"] = rg.PRECISION_FP32_INNER
     if args.only_spmv_large:

@@ -110,6 +110,19 @@ typedef struct {
                               stopping rule's measure of x_k (looser block solves
                               while x_k is far from the target; the outer test and
                               its tolerance are unchanged).  0 (default): inner_tol */
+    int col_team;          /* two-team schedule of rgdbek_solve (and of the solves of
+                              rgdbek_backward and the FP32 form): the column steps of
+                              Algorithm 1 (the z recurrence, which does not depend on
+                              x) run one outer iteration ahead of the row steps, on
+                              col_team CTAs of the grid with barriers of their own,
+                              while the other CTAs run the row steps.  0 = automatic
+                              (3/16 of the grid; one team when inner_adapt > 0, whose
+                              inner tolerance ties the column step to x, or when the
+                              grid is below 8 CTAs), -1 = one team runs every phase
+                              in turn, k > 0 = k CTAs (at most half the grid).  The
+                              iterates are the same either way up to the rounding of
+                              the reductions; rgdbek_solve_batched always runs one
+                              team per system */
 } rgdbek_options;
 
 typedef struct {
@@ -131,7 +144,11 @@ typedef struct {
     /* device time (ms, globaltimer of CTA 0) spent per phase kind, in the order
      * of RGDBEK_PHASE_NAMES: set-up, column pass, column selection, A_U
      * extraction, LSQR on A_U, z update, row selection, A^J extraction, LSQR on
-     * A^J, residual pass, and the FP64 refinement steps of the FP32 form */
+     * A^J, residual pass, and the FP64 refinement steps of the FP32 form.  With
+     * two teams (option col_team) each team's rank 0 times its own phases and
+     * the two are added: the column team's run beside the row team's, so the
+     * sum exceeds the solve's time; the row team's waits for the column team
+     * count as column pass */
     double phase_ms[11];
     int64_t refinements; /* FP64 refinement steps (RGDBEK_PRECISION_FP32_INNER)   */
 } rgdbek_stats;
@@ -149,6 +166,8 @@ typedef struct {
     int lanes_per_col;     /* lanes that share one CSC column in the A^T z passes */
     int num_sms;
     int64_t device_bytes;  /* device memory the handle uses (with its matrix)    */
+    int col_team;          /* CTAs of the column team of the next rgdbek_solve
+                              (option col_team resolved; 0 = one team)          */
 } rgdbek_info_t;
 
 /* Fills *opt with the defaults: eta_col = eta_row = 0.5 (the paper's

@@ -70,6 +70,7 @@ class rgdbek_options(ctypes.Structure):
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
         ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
         ("batch_team", _int), ("warm_start", _int), ("inner_adapt", _dbl),
+        ("col_team", _int),
     ]
 
 
@@ -91,7 +92,7 @@ class rgdbek_info_t(ctypes.Structure):
     _fields_ = [
         ("m", _i64), ("n", _i64), ("nnz", _i64), ("grid", _int), ("threads_per_block", _int),
         ("lanes_per_row", _int), ("lanes_per_col", _int), ("num_sms", _int),
-        ("device_bytes", _i64),
+        ("device_bytes", _i64), ("col_team", _int),
     ]
 
 

@@ -17,8 +17,9 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "librgdbek.so")
 OBJDIR = os.path.join(PKG, "_build")
 
-SOURCES = ["rgdbek_kernels.cu", "rgdbek_solve512.cu", "rgdbek_setup.cu", "rgdbek_api.cu",
-           "rgdbek_noalloc.cu"]
+SOURCES = ["rgdbek_solve512.cu", "rgdbek_solve1024.cu", "rgdbek_refine512.cu",
+           "rgdbek_refine1024.cu", "rgdbek_batched.cu", "rgdbek_kernels.cu", "rgdbek_setup.cu",
+           "rgdbek_api.cu", "rgdbek_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 

@@ -62,6 +62,13 @@ struct rgdbek_s {
     // the FP32 form's refinement loop: FP64 residual, and the right-hand side and
     // solution of its FP64 inner solves
     double *ref_t, *ref_b, *ref_x;
+    // the column team's buffers of the two-team schedule (FP64 and FP32 views)
+    double *uu_z, *vv_z, *ww_z, *dots_z, *dots2_z, *pd_z;
+    float *f_uu_z, *f_vv_z, *f_ww_z, *f_dots_z, *f_dots2_z, *f_pd_z;
+    long long *pi_z;
+    unsigned long long *Q_z;
+    unsigned char *flag_z;
+    int *ulist2;
     Ctrl *ctrl;
     double *b_stage, *x_stage;
     // implicit adjoint scratch, allocated by the first rgdbek_backward call:
@@ -159,6 +166,16 @@ void carve(rgdbek_s *h, Layout &L) {
     h->ref_t = L.take<double>(mx);
     h->ref_b = L.take<double>(mx);
     h->ref_x = L.take<double>(mx);
+    double **zv[] = {&h->uu_z, &h->vv_z, &h->ww_z, &h->dots_z, &h->dots2_z};
+    for (double **p : zv) *p = L.take<double>(mx);
+    h->pd_z = L.take<double>((long long)D_NSLOTS * kMaxGrid);
+    float **zf[] = {&h->f_uu_z, &h->f_vv_z, &h->f_ww_z, &h->f_dots_z, &h->f_dots2_z};
+    for (float **p : zf) *p = L.take<float>(mx);
+    h->f_pd_z = L.take<float>((long long)D_NSLOTS * kMaxGrid);
+    h->pi_z = L.take<long long>((long long)I_NSLOTS * kMaxGrid);
+    h->Q_z = L.take<unsigned long long>(mx);
+    h->flag_z = L.take<unsigned char>(mx);
+    h->ulist2 = L.take<int>(mx);
     h->ctrl = L.take<Ctrl>(1);
     h->b_stage = L.take<double>(m);
     h->x_stage = L.take<double>(n);
@@ -178,6 +195,7 @@ int check_options(const rgdbek_options &o) {
     if (o.batch_team < 0 || o.batch_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.warm_start != 0 && o.warm_start != 1) return RGDBEK_ERR_INVALID_ARG;
     if (!(o.inner_adapt >= 0.0)) return RGDBEK_ERR_INVALID_ARG;
+    if (o.col_team < -1 || o.col_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -284,6 +302,18 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.ipc = h->ipc;
     P.dsmem_bytes = kSolveDsmemBytes;
     P.team = h->grid;
+    P.zteam = 0;  // one team unless the solve chooses two (run_solve)
+    P.uu_z = h->uu_z;
+    P.vv_z = h->vv_z;
+    P.ww_z = h->ww_z;
+    P.dots_z = h->dots_z;
+    P.dots2_z = h->dots2_z;
+    P.pd_z = h->pd_z;
+    P.pi_z = h->pi_z;
+    P.Q_z = h->Q_z;
+    P.flag_z = h->flag_z;
+    P.ulist2 = h->ulist2;
+    P.bar = nullptr;
     if (transposed) {
         P.m = h->n;
         P.n = h->m;
@@ -401,6 +431,18 @@ ParamsF make_params_f(const rgdbek_s *h, const Params &P, bool transposed) {
     F.ipr = P.ipr;
     F.ipc = P.ipc;
     F.dsmem_bytes = P.dsmem_bytes;
+    F.zteam = P.zteam;
+    F.uu_z = h->f_uu_z;
+    F.vv_z = h->f_vv_z;
+    F.ww_z = h->f_ww_z;
+    F.dots_z = h->f_dots_z;
+    F.dots2_z = h->f_dots2_z;
+    F.pd_z = h->f_pd_z;
+    F.pi_z = P.pi_z;
+    F.Q_z = P.Q_z;
+    F.flag_z = P.flag_z;
+    F.ulist2 = P.ulist2;
+    F.bar = nullptr;
     return F;
 }
 
@@ -470,9 +512,19 @@ void fill_stats(const Ctrl &c, int status, rgdbek_stats *st);
 
 // One persistent-kernel solve of A x = b (or of A^T x = b when transposed),
 // x0 = 0; reads the control block back into *st.
+// CTAs of the column team of a single solve (0: one team), option col_team.
+int choose_zteam(const rgdbek_s *h) {
+    const int c = h->opt.col_team;
+    if (c < 0 || h->opt.inner_adapt > 0.0 || h->grid < 8) return 0;
+    if (c > 0) return c < h->grid / 2 ? c : h->grid / 2;
+    const int a = (3 * h->grid + 8) / 16;
+    return a > 1 ? a : 1;
+}
+
 int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double tol,
               long long max_iter, uint64_t seed, rgdbek_stats *st, bool from_zero = false) {
     Params P = make_params(h, transposed);
+    P.zteam = choose_zteam(h);
     if (from_zero) P.warm = 0;  // the adjoint's inner solves and the tuner's probes
     P.b = b;
     P.x = x;
@@ -516,7 +568,8 @@ void fill_stats(const Ctrl &c, int status, rgdbek_stats *st) {
         st->normal_res = c.normal_res;
         st->rse = c.rse;
         st->status = status;
-        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) st->phase_ms[i] = 1e-6 * (double)c.phase_ns[i];
+        for (int i = 0; i < RGDBEK_NUM_PHASES; ++i)
+            st->phase_ms[i] = 1e-6 * ((double)c.phase_ns[i] + (double)c.zphase_ns[i]);
         st->refinements = c.refinements;
     }
 }
@@ -702,6 +755,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->batch_team = 0;
     opt->warm_start = 0;
     opt->inner_adapt = 0.0;
+    opt->col_team = 0;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
@@ -930,6 +984,7 @@ int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
     info->lanes_per_col = h->lpc;
     info->num_sms = h->num_sms;
     info->device_bytes = (int64_t)(h->arena_bytes + (h->mat ? h->mat->bytes : 0));
+    info->col_team = choose_zteam(h);
     return RGDBEK_OK;
 }
 

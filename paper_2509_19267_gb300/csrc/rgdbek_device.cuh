@@ -47,6 +47,7 @@ enum ISlot {
     I_TOT,        // chunk total of quantised weights
     I_CNT,        // chunk count of flagged indices
     I_NNZ,        // count of extracted nonzeros
+    I_STOP,       // two-team schedule: the row team has finished (set by rank 0)
     I_NSLOTS
 };
 
@@ -69,6 +70,25 @@ struct Ctrl {
     int bad_out;
     int pad3[15];
     long long refinements;   // FP64 refinement steps of the FP32 form
+    // ---- two-team schedule (the column steps of Algorithm 1 run one iteration
+    // ahead of the row steps on a team of their own; see solve_split)
+    alignas(128) unsigned long long bar_x;  // barrier counter of the row team
+    alignas(128) unsigned long long bar_z;  // barrier counter of the column team
+    // link words, each (call << 32) | count within the call, written with
+    // release stores by the writing team's rank 0 after a team barrier:
+    alignas(128) unsigned long long lk_zready;  // z_{k+1} written (column team)
+    unsigned long long lk_zused;    // z_{k+1} read by the row team
+    unsigned long long lk_tready;   // t_{k+1} written (row team)
+    unsigned long long lk_colpass;  // column pass k done (its ||A^T t||^2 below)
+    unsigned long long lk_stop;     // the row team has finished this call
+    // values that travel with the link words (slot = iteration parity)
+    double lk_hh[2], lk_gg;
+    long long lk_badc[2], lk_nu[2], lk_nnzu[2], lk_stepsu[2];
+    // the row team's result, for the CTAs of the column team
+    long long lk_res_k;
+    int lk_res_status, pad4;
+    double lk_res_rel, lk_res_nrm;
+    unsigned long long zphase_ns[RGDBEK_NUM_PHASES];  // the column team's phase times
 };
 
 // ---------------------------------------------------------------------------
@@ -107,16 +127,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // __syncthreads (so every thread sees the other CTAs' writes).  Returns false
 // if the wait was abandoned: another CTA raised the abort flag, or the
 // time/spin limit ran out (then this CTA records TIMEOUT and raises abort).
-__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch, int nct) {
+// cnt: the team's arrival counter (c->bar_count, or a counter of its own
+// when two teams work on one system; abort and status stay c's).
+__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long *cnt,
+                                             unsigned long long &epoch, int nct) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned long long target = (unsigned long long)nct * (epoch + 1);
-        atom_add_release_u64(&c->bar_count, 1ull);
+        atom_add_release_u64(cnt, 1ull);
         unsigned long long spins = 0;
         const unsigned long long t0 = globaltimer_ns();
-        while (ld_acquire_u64(&c->bar_count) < target) {
+        while (ld_acquire_u64(cnt) < target) {
             ++spins;
             if ((spins & 1023) == 0) {
                 if (ld_volatile_i32(&c->abort)) { ok = 0; break; }
@@ -134,6 +157,61 @@ __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch,
     }
     __syncthreads();
     return s_ok != 0;
+}
+__device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned long long &epoch, int nct) {
+    return grid_barrier(c, &c->bar_count, epoch, nct);
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Wait limits of a wait on the other team of a two-team solve: that team's
+// progress is itself bounded by its barriers' limits (an abandoned barrier
+// raises the abort flag seen here), so this limit only guards the protocol.
+constexpr unsigned long long kLinkTimeoutNs = 30000000000ull;  // 30 s
+
+// Thread 0 of the CTA waits until *word >= target (acquire), then the CTA
+// synchronises.  With stop_call != 0 the wait also ends when the row team has
+// finished call stop_call (c->lk_stop >= stop_call) while *word < target: the
+// stop word is read before the awaited word, and the row team raises it only
+// after its last link write, so every CTA of a team reaches the same
+// decision.  Returns 0 (reached), 1 (stopped), -1 (abort flag, or the wait
+// limit ran out: then TIMEOUT is recorded and the abort flag raised).
+__device__ __forceinline__ int link_wait(Ctrl *c, const unsigned long long *word,
+                                         unsigned long long target, unsigned long long stop_call) {
+    __shared__ int s_r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int r = 0;
+        unsigned long long spins = 0;
+        const unsigned long long t0 = globaltimer_ns();
+        for (;;) {
+            const unsigned long long st = stop_call ? ld_acquire_u64(&c->lk_stop) : 0ull;
+            if (ld_acquire_u64(word) >= target) break;
+            if (stop_call && st >= stop_call) {
+                r = 1;
+                break;
+            }
+            ++spins;
+            if ((spins & 1023) == 0) {
+                if (ld_volatile_i32(&c->abort)) {
+                    r = -1;
+                    break;
+                }
+                if (spins > kBarrierMaxSpins || globaltimer_ns() - t0 > kLinkTimeoutNs) {
+                    atomicCAS(&c->status, kStatusRunning, RGDBEK_ERR_TIMEOUT);
+                    atomicExch(&c->abort, 1);
+                    r = -1;
+                    break;
+                }
+            }
+            if (spins > 256) __nanosleep(64);
+        }
+        s_r = r;
+    }
+    __syncthreads();
+    return s_r;
 }
 
 // ---------------------------------------------------------------------------
@@ -262,6 +340,24 @@ __device__ __forceinline__ double block_max(double v, BlockScratch &bs) {
     }
     __syncthreads();
     return __longlong_as_double(bs.i[32]);
+}
+
+// Maximum of one int64 per thread over the CTA; every thread returns it.
+__device__ __forceinline__ long long block_max_ll(long long v, BlockScratch &bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    __syncthreads();
+    if (lane == 0) bs.i[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long r = lane < nw ? bs.i[lane] : bs.i[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(kFull, r, o));
+        if (lane == 0) bs.i[32] = r;
+    }
+    __syncthreads();
+    return bs.i[32];
 }
 
 // The same for nonnegative finite floats (bit patterns compared as integers).

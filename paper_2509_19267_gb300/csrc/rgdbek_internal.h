@@ -47,8 +47,11 @@ cudaError_t launch_solve_batched(const SysPair *sys_dev, const int *plan_dev, in
 // the refinement kernel of the FP32 form
 const void *solve_kernel_fn(bool fp32, bool small);
 const void *batched_kernel_fn(bool fp32, bool small);
-const void *solve_kernel_fn_small(bool fp32);      // rgdbek_solve512.cu
-const void *batched_kernel_fn_small(bool fp32);
+const void *solve_fn_512();     // rgdbek_solve512.cu
+const void *solve_fn_1024();    // rgdbek_solve1024.cu
+const void *refine_fn_512();    // rgdbek_refine512.cu
+const void *refine_fn_1024();   // rgdbek_refine1024.cu
+const void *batched_fn(bool fp32, bool small);  // rgdbek_batched.cu
 // control blocks of a batch: reset before the launch, gathered after it
 cudaError_t launch_reset_ctrls(const SysPair *sys_dev, int nsys, cudaStream_t s);
 cudaError_t launch_gather_ctrls(const SysPair *sys_dev, int nsys, Ctrl *out, cudaStream_t s);

@@ -1,7 +1,7 @@
-// Kernels of the library besides the solve device code (rgdbek_solve.cuh):
-// the 1024-thread instantiation of the solve kernels, the batch control
-// kernels, the component kernels that reuse the solve's phases (SpMV, A^T z,
-// weights, sampler, adjoint entry gradients), and the host-side launchers.
+// Kernels of the library besides the solve kernels (rgdbek_solve.cuh,
+// instantiated in their own translation units): the batch control kernels,
+// the component kernels that reuse the solve's phases (SpMV, A^T z, weights,
+// sampler, adjoint entry gradients), and the host-side launchers.
 #include <cmath>
 
 #include "rgdbek_internal.h"
@@ -18,6 +18,7 @@ __global__ void reset_ctrls_kernel(const SysPair *sys, int nsys) {
     c->abort = 0;
     c->status = kStatusRunning;
     c->stop_req = 0;
+    for (int k = 0; k < RGDBEK_NUM_PHASES; ++k) c->zphase_ns[k] = 0;
 }
 
 // Copies the control blocks of a batch into one array (for one host copy).
@@ -175,6 +176,9 @@ __global__ void reset_ctrl_kernel(Ctrl *c) {
     c->emax_out = 0.0;
     c->bad_out = 0;
     c->refinements = 0;
+    c->bar_x = c->bar_z = 0;
+    c->lk_zready = c->lk_zused = c->lk_tready = c->lk_colpass = c->lk_stop = 0;
+    for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) c->zphase_ns[i] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -185,18 +189,12 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// the 1024-thread shape lives in this unit, the 512-thread one in
-// rgdbek_solve512.cu
+// the solve kernels live in translation units of their own
 const void *solve_kernel_fn(bool fp32, bool small) {
-    if (small) return solve_kernel_fn_small(fp32);
-    return fp32 ? (const void *)refine_kernel<kSolveMaxThreads>
-                : (const void *)solve_kernel<kSolveMaxThreads>;
+    if (fp32) return small ? refine_fn_512() : refine_fn_1024();
+    return small ? solve_fn_512() : solve_fn_1024();
 }
-const void *batched_kernel_fn(bool fp32, bool small) {
-    if (small) return batched_kernel_fn_small(fp32);
-    return fp32 ? (const void *)batched_solve_kernel<true, kSolveMaxThreads>
-                : (const void *)batched_solve_kernel<false, kSolveMaxThreads>;
-}
+const void *batched_kernel_fn(bool fp32, bool small) { return batched_fn(fp32, small); }
 
 cudaError_t launch_solve(const Params &P, const ParamsF &F, int grid, int block, cudaStream_t s) {
     Params p = P;

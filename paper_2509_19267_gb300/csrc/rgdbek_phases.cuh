@@ -93,6 +93,18 @@ struct ParamsT {
                             // (A^T z, b - A x, the component SpMVs; tunable)
     int ipr, ipc;           // lanes per row / column of A, integer passes
     long long dsmem_bytes;  // dynamic shared memory per CTA of the solve kernel
+    // two-team schedule (solve_split): zteam > 0 CTAs of the grid run the
+    // column steps, one outer iteration ahead of the row steps that the other
+    // CTAs run (the z recurrence of Algorithm 1 does not depend on x); the
+    // column team's own copies of the buffers both steps use, and the second
+    // list of U (the row team records U_k while U_{k+1} is drawn)
+    int zteam;
+    V *uu_z, *vv_z, *ww_z, *dots_z, *dots2_z, *pd_z;
+    long long *pi_z;
+    unsigned long long *Q_z;
+    unsigned char *flag_z;
+    int *ulist2;
+    unsigned long long *bar;  // this team's barrier counter (null: ctrl->bar_count)
 };
 using Params = ParamsT<double>;
 using ParamsF = ParamsT<float>;
@@ -345,8 +357,11 @@ __device__ __forceinline__ void cols_matvec(const ParamsT<V> &P, const V *zin, V
 //   g = A^T z_k, h = A^T t_k with t_k = b - A x_k (for the stopping test),
 //   eps^z_j = g_j^2 / ||A_j||^2.
 // Partials: max eps^z, ||h||^2, ||g||^2, non-finite flag.
+// The column team of a two-team solve runs it with apply_x = false (the row
+// team adopts x) and, where no t is due, with_h = false (h is not formed).
 template <typename V>
-__device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs) {
+__device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs,
+                                          bool apply_x = true, bool with_h = true) {
     using V2 = typename Vec2<V>::type;
     const Grp G(P.lpc);
     V emax = V(0), hh = V(0), gg = V(0);
@@ -360,14 +375,14 @@ __device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs)
         sg = group_sum(sg, G.L);
         sh = group_sum(sh, G.L);
         if (j < P.n && G.sl == 0) {
-            P.x[j] = P.xt[j];
+            if (apply_x) P.x[j] = P.xt[j];
             const V c = __ldg(P.cn2 + j);
             const V e = c > V(0) ? weight_of(sg, c) : V(0);
             P.g[j] = sg;
             P.epsc[j] = e;
             if (!isfinite(e)) bad = 1;
             else emax = max_nonneg(emax, e);
-            hh = vfma(sh, sh, hh);
+            if (with_h) hh = vfma(sh, sh, hh);
             gg = vfma(sg, sg, gg);
         }
     }
@@ -384,10 +399,14 @@ __device__ __forceinline__ void phase_col(const ParamsT<V> &P, BlockScratch &bs)
 }
 
 // t_{k+1} = b - A x_{k+1} over the CSR rows, x_{k+1} = xt.  Partial: ||t||^2.
+// With apply_x (the row team of a two-team solve) x = xt is also adopted.
 template <typename V>
-__device__ __forceinline__ void phase_residual(const ParamsT<V> &P, BlockScratch &bs) {
+__device__ __forceinline__ void phase_residual(const ParamsT<V> &P, BlockScratch &bs,
+                                               bool apply_x = false) {
     const Grp G(P.lpr);
     V tt = V(0);
+    if (apply_x)
+        for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.x[j] = P.xt[j];
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         V s = V(0);
@@ -442,16 +461,32 @@ __device__ __forceinline__ unsigned long long quantize_weight(float e, float ema
 // Random rule: q_j = floor(2^K eps_j / eps_max), K = 62 - ceil(log2 len), and
 // the chunk-local inclusive prefix of q into Q; clears the marks.  Partial:
 // the chunk total.  Greedy rule: marks {j : eps_j >= eta eps_max, eps_j > 0}.
+// For the solve (count_slot): the chunk's count of marks in slot I_CNT (0 for
+// the random rule: the draws count them), and zero_cnt[0 .. zero_len) cleared
+// (the line counts the scatter of the selected lines will fill).
 template <typename V>
 __device__ __forceinline__ void phase_quantize(const ParamsT<V> &P, const V *eps, long long len,
                                                V emax, bool greedy, double eta,
-                                               BlockScratch &bs) {
+                                               BlockScratch &bs, bool count_slot = false,
+                                               int *zero_cnt = nullptr, long long zero_len = 0) {
     const Chunk C(len, trank(P), tsize(P));
+    for (long long i = tthread(P); i < zero_len; i += tthreads(P)) zero_cnt[i] = 0;
     if (greedy) {
         const V thr = (V)eta * emax;
-        for (long long j = C.lo + threadIdx.x; j < C.hi; j += blockDim.x) {
-            const V e = eps[j];
-            P.flag[j] = (e >= thr && e > V(0)) ? 1 : 0;
+        long long cnt = 0;
+        for (long long base = C.lo; base < C.hi; base += blockDim.x) {
+            const long long j = base + threadIdx.x;
+            bool f = false;
+            if (j < C.hi) {
+                const V e = eps[j];
+                f = e >= thr && e > V(0);
+                P.flag[j] = f ? 1 : 0;
+            }
+            cnt += __popc(__ballot_sync(kFull, f)) * ((threadIdx.x & 31) == 0);
+        }
+        if (count_slot) {
+            cnt = block_sum(cnt, bs);
+            if (threadIdx.x == 0) P.pi[I_CNT * tsize(P) + trank(P)] = cnt;
         }
         return;
     }
@@ -469,18 +504,27 @@ __device__ __forceinline__ void phase_quantize(const ParamsT<V> &P, const V *eps
         if (j < C.hi) P.Q[j] = run + ex + q;
         run += tot;
     }
-    if (threadIdx.x == 0) P.pi[I_TOT * tsize(P) + trank(P)] = (long long)run;
+    if (threadIdx.x == 0) {
+        P.pi[I_TOT * tsize(P) + trank(P)] = (long long)run;
+        if (count_slot) P.pi[I_CNT * tsize(P) + trank(P)] = 0;
+    }
 }
 
 // s independent draws: R = word (t mod 4) of Philox4x64-10 with key
 // (seed, sysid) and counter (k, phase, t div 4, 0); target = floor(R Q_tot /
 // 2^64); the drawn index is the first j whose global inclusive prefix of q
 // exceeds target (located through the per-CTA totals, then inside the chunk).
+// With cnt (the solve), each first mark of an index is also counted for the
+// chunk that holds it (cnt[chunk], cleared by phase_quantize): the marks are
+// set with an atomic OR on the 32-bit word that holds them, and only the
+// draw that finds its byte clear adds one, so every chunk's count of
+// distinct marks is exact whatever the order of the draws.
 template <typename PT>
 __device__ __forceinline__ void phase_draw(const PT &P, long long len, long long s,
                                            unsigned long long seed, unsigned long long sysid,
                                            unsigned long long k, unsigned long long phase,
-                                           long long *tab, BlockScratch &bs) {
+                                           long long *tab, BlockScratch &bs,
+                                           long long *cnt = nullptr) {
     const int nct = tsize(P);
     partials_prefix(P.pi + I_TOT * nct, nct, tab, bs);
     const unsigned long long qtot = (unsigned long long)tab[nct - 1];
@@ -507,7 +551,15 @@ __device__ __forceinline__ void phase_draw(const PT &P, long long len, long long
                 if (P.Q[mid] > local) e = mid;
                 else a = mid + 1;
             }
-            P.flag[a] = 1;
+            if (cnt) {
+                const unsigned sh = 8u * (unsigned)(a & 3);
+                unsigned *w = reinterpret_cast<unsigned *>(P.flag + (a & ~3ll));
+                const unsigned old = atomicOr(w, 1u << sh);
+                if (((old >> sh) & 0xffu) == 0u)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(cnt + lo), 1ull);
+            } else {
+                P.flag[a] = 1;
+            }
         }
     }
 }
@@ -609,70 +661,141 @@ __device__ __forceinline__ long long phase_compact_write(const PT &P, long long 
 }
 
 // ---------------------------------------------------------------------------
-// Block extraction in one pass: for each line (CSR row or CSC column) of A,
-// the entries whose other index is selected (map[idx] >= 0) are written,
-// renumbered through map, at the start of the line's own slot in A's arrays
-// (oidx/oval[ptr[l] .. ptr[l] + ocnt[l])).  No scan over the grid is needed;
-// the block products read each line as (ptr[l], ocnt[l]).  A_U keeps all m
-// rows and A^J all n columns, so both block products are gathers.
-// Partial: the number of extracted entries.
+// Compaction of the marks and extraction of the block in one phase.
+//
+// The marked indices of the CTA's chunk get their place in the ascending
+// list (offsets from the prefix of the per-chunk counts of the draws), and
+// the entries of each selected line of A (a CSC column for the column block,
+// a CSR row for the row block) are scattered into the other side's lines:
+// entry (l, o) goes to line o of the block at dptr[o] + (dcnt[o]++), with l
+// renumbered to its place p in the list (pos[j] = p, or -1 where j is not
+// selected, when pos is given).  Only the selected lines are read
+// (about eta of A), not all of A.  The line counts come from atomic
+// increments, so the entries of a line land in arbitrary order; the inner
+// solve sorts them by index before its first product (sort_scattered_lines),
+// which gives every line the order of A's own lines.
+// init(p, j, total) runs once per selected index j (place p, list length
+// total) before the scatter: the start vectors of the inner solve.
+// Partials over the selected lines, summed per thread in the chunk's order:
+// the sums of norm2 (squared Frobenius norm of the block) and of vec^2 (the
+// LSQR right-hand side, or B^T c in the column step), with unit (the weights
+// eps = vec^2 / norm2) the line count and the sum of the weights, and the
+// number of scattered entries (nnz of the block).
 // ---------------------------------------------------------------------------
-template <typename V>
-struct Lines {
-    const long long *ptr;
-    const int *idx;
-    const V *val;
-    long long n;
-    int L;
-};
-
-template <typename V>
-__device__ __forceinline__ void phase_extract(const ParamsT<V> &P, const Lines<V> &A,
-                                              const int *map, int *ocnt, int *oidx, V *oval,
-                                              BlockScratch &bs) {
-    const Grp G(A.L);
-    const long long L = G.L;
-    long long total = 0;
-    for (long long base = twarp(P) * G.rpw; base < A.n; base += twarps(P) * G.rpw) {
-        const long long i = base + G.sub;
-        const bool valid = i < A.n;
-        const long long e0 = valid ? __ldg(A.ptr + i) : 0;
-        const long long e1 = valid ? __ldg(A.ptr + i + 1) : 0;
-        int nit = valid ? (int)((e1 - e0 + 4 * L - 1) / (4 * L)) : 0;
-        nit = (int)__reduce_max_sync(kFull, (unsigned)nit);
-        long long pos = e0;
-        for (int it = 0; it < nit; ++it) {
-            // four entries per lane per trip: index and value loads, then map gathers
-            const long long e = e0 + (long long)it * 4 * L + G.sl;
-            int p[4];
-            V vq[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const long long f = e + q * L;
-                const bool in = valid && f < e1;
-                p[q] = in ? __ldg(A.idx + f) : -1;
-                vq[q] = in ? __ldg(A.val + f) : V(0);   // with the index: one round trip less
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) p[q] = p[q] >= 0 ? map[p[q]] : -1;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const unsigned gm = G.mine(__ballot_sync(kFull, p[q] >= 0));
-                if (p[q] >= 0) {
-                    const long long o = pos + __popc(gm & ((1u << G.sl) - 1u));
-                    oidx[o] = p[q];
-                    oval[o] = vq[q];
+template <typename V, typename Init>
+__device__ __forceinline__ long long phase_select_scatter(
+    const ParamsT<V> &P, long long len, const V *norm2, const V *vec, const V *unit, int *pos,
+    int *list, long long *tab, BlockScratch &bs, const long long *sptr, const int *sidx,
+    const V *sval, const long long *dptr, int *dcnt, int *didx, V *dval, Init init) {
+    const int nct = tsize(P);
+    partials_prefix(P.pi + I_CNT * nct, nct, tab, bs);
+    const long long total = tab[nct - 1];
+    const Chunk C(len, trank(P), nct);
+    const long long first = trank(P) > 0 ? tab[trank(P) - 1] : 0;
+    long long run = first;
+    V fro = V(0), ext = V(0), frs = V(0), exs = V(0);
+    for (long long base = C.lo; base < C.hi; base += blockDim.x) {
+        const long long j = base + threadIdx.x;
+        const bool f = j < C.hi && P.flag[j];
+        long long tot;
+        const long long ex = block_rank_pred(f, bs, &tot);
+        if (j < C.hi) {
+            if (f) {
+                const long long p = run + ex;
+                if (pos) pos[j] = (int)p;
+                list[p] = (int)j;
+                init(p, j, total);
+                fro += __ldg(norm2 + j);
+                const V v = vec[j];
+                ext = vfma(v, v, ext);
+                if (unit) {
+                    frs += V(1);
+                    exs += unit[j];
                 }
-                pos += __popc(gm);
+            } else if (pos) {
+                pos[j] = -1;
             }
         }
-        if (valid && G.sl == 0) {
-            ocnt[i] = (int)(pos - e0);
-            total += pos - e0;
-        }
+        run += tot;
     }
-    total = block_sum(total, bs);
-    if (threadIdx.x == 0) P.pi[I_NNZ * tsize(P) + trank(P)] = total;
+    __syncthreads();  // the CTA's list entries [first, run) are visible to all its threads
+    // Scatter: the entries of the CTA's selected lines, numbered in line order,
+    // are dealt to the threads in turn (four at a time, all loads and
+    // increments in flight), so the work is even whatever the line lengths.
+    // The line of an entry is found by a binary search of the chunk-local
+    // prefix of the line lengths (bs.big, staged in rounds of blockDim lines).
+    long long nnz = 0;
+    long long *off = reinterpret_cast<long long *>(bs.big);
+    for (long long r0 = first; r0 < run; r0 += blockDim.x) {
+        const long long q = r0 + threadIdx.x;
+        const int nq = (int)min((long long)blockDim.x, run - r0);
+        long long e0 = 0, len = 0;
+        if (q < run) {
+            const long long l = list[q];
+            e0 = __ldg(sptr + l);
+            len = __ldg(sptr + l + 1) - e0;
+        }
+        long long tot;
+        const long long ex = block_excl_scan<long long>(len, bs, &tot);
+        __syncthreads();
+        if (q < run) off[threadIdx.x] = ex;
+        __syncthreads();
+        nnz += tot;
+        for (long long t0 = threadIdx.x; t0 < tot; t0 += 4ll * blockDim.x) {
+            int o[4];
+            V v[4];
+            int qq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long t = t0 + (long long)u * blockDim.x;
+                o[u] = -1;
+                v[u] = V(0);
+                qq[u] = 0;
+                if (t < tot) {
+                    int lo = 0, hi = nq - 1;  // last line whose offset is <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (off[mid] <= t) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const long long l = list[r0 + lo];
+                    const long long f = __ldg(sptr + l) + (t - off[lo]);
+                    o[u] = __ldg(sidx + f);
+                    v[u] = __ldg(sval + f);
+                    qq[u] = (int)(r0 + lo);
+                }
+            }
+            long long d[4];
+            int c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                d[u] = o[u] >= 0 ? __ldg(dptr + o[u]) : 0;
+                c[u] = o[u] >= 0 ? atomicAdd(dcnt + o[u], 1) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (o[u] >= 0) {
+                    didx[d[u] + c[u]] = qq[u];
+                    dval[d[u] + c[u]] = v[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    fro = block_sum(fro, bs);
+    ext = block_sum(ext, bs);
+    if (unit) {
+        frs = block_sum(frs, bs);
+        exs = block_sum(exs, bs);
+    }
+    if (threadIdx.x == 0) {
+        P.pd[D_FRO * nct + trank(P)] = fro;
+        P.pd[D_EXTRA * nct + trank(P)] = ext;
+        P.pd[D_FRO_S * nct + trank(P)] = frs;
+        P.pd[D_EXTRA_S * nct + trank(P)] = exs;
+        P.pi[I_NNZ * nct + trank(P)] = nnz;
+    }
+    return total;
 }
 
 template <typename V>

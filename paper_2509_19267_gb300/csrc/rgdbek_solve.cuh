@@ -2,9 +2,10 @@
 // outer iteration (solve_body), the FP64 refinement loop of the FP32 form
 // (refine_body) and the single and batched solve kernels, templated on the
 // value type V of the iteration (double, or float for the inner solves of
-// RGDBEK_PRECISION_FP32_INNER) and the launch bound (NT threads).  Two
-// translation units include it, each instantiating one launch bound, so that
-// the two shapes compile in parallel.
+// RGDBEK_PRECISION_FP32_INNER) and the launch bound (NT threads).  Each kernel
+// and shape is instantiated in a translation unit of its own
+// (rgdbek_solve512/1024.cu, rgdbek_refine512/1024.cu, rgdbek_batched.cu), so
+// that they compile in parallel.
 //
 // One outer iteration k of Algorithm 1, phase by phase (| = grid barrier):
 //   col:  x_k = x_{k-1} + dx; g = A^T z_k; h = A^T (b - A x_k); eps^z  |
@@ -90,6 +91,9 @@ struct SolveSmem {
     OuterStateT<float> o_f;
     RefineState ref;                                 // refinement scalars (thread 0)
     unsigned long long epoch;                        // grid barriers passed (thread 0 copy)
+    unsigned long long epoch_sub;                    // the same on the CTA's team counter of
+                                                     // a two-team solve (kept between calls)
+    unsigned long long split_calls;                  // two-team solves run by this kernel
     int leader;                                      // this CTA has rank 0 in its team
     unsigned long long tlast;                        // phase timers (CTA 0, thread 0)
     unsigned long long tphase[RGDBEK_NUM_PHASES];
@@ -137,6 +141,8 @@ __device__ __forceinline__ void init_solve_smem(SolveSmem &S, const PT &P) {
     if (threadIdx.x == 0) {
         const unsigned long long now = globaltimer_ns();
         S.epoch = 0;
+        S.epoch_sub = 0;
+        S.split_calls = 0;
         S.leader = trank(P) == 0;
         S.acc = Acc{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         S.tlast = now;
@@ -150,12 +156,18 @@ __device__ __forceinline__ void init_solve_smem(SolveSmem &S, const PT &P) {
 
 #define DS(x) (1u << (x))
 
+// the barrier counter of the CTA's team
+template <typename PT>
+__device__ __forceinline__ unsigned long long *bar_of(const PT &P) {
+    return P.bar ? P.bar : &P.ctrl->bar_count;
+}
+
 // Grid barrier, then the requested partial slots reduced into S.red_*.
 // Returns false if the barrier was abandoned.
 template <typename V>
 __device__ __forceinline__ bool sync_collect(const ParamsT<V> &P, SolveSmem &S, unsigned dmask,
                                              unsigned dmax, unsigned imask, V *out_d) {
-    if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return false;
+    if (!grid_barrier(P.ctrl, bar_of(P), S.epoch, tsize(P))) return false;
     if (dmask | imask)
         collect_partials<V>(P.pd, P.pi, tsize(P), dmask, dmax, imask, out_d, S.red_i);
     return true;
@@ -259,11 +271,129 @@ struct SmemArena {
     }
 };
 
+// New places of the entries of one line, staged at ks/vs[0, len): the entry
+// with index key goes to place (number of the line's indices below key),
+// written to idx/val[0, len).  This lane takes entries first, first + step, ...
+template <typename V>
+__device__ __forceinline__ void rank_place(const int *ks, const V *vs, int len, int first, int step,
+                                           int *idx, V *val) {
+    for (int q = first; q < len; q += step) {
+        const int key = ks[q];
+        int r = 0;
+        for (int t = 0; t < len; ++t) r += ks[t] < key;
+        idx[r] = key;
+        val[r] = vs[q];
+    }
+}
+
+// Sorts by index, in place, the entries of lines [lo, hi) of a block side
+// that phase_select_scatter wrote in arbitrary order (line l: idx/val[ptr[l],
+// ptr[l] + cnt[l])), so that every product over a line sums in one fixed
+// order, the ascending order of A's own lines.  The indices of a line are
+// distinct (each selected line contributes at most one entry), so each
+// entry's place is its rank.  The CTA's lines are staged in shared memory
+// (arena A, released on return) and ranked there by groups of lanes sized to
+// the average line (lines above eight entries per lane are ranked by a
+// whole warp); a chunk that does not fit is sorted line by line in global
+// memory.  All threads of the CTA call it.
+template <typename V>
+__device__ __forceinline__ void sort_scattered_lines(const long long *ptr, const int *cnt, int *idx,
+                                                     V *val, long long lo, long long hi,
+                                                     SmemArena A, BlockScratch &bs) {
+    const int nl = (int)(hi - lo);
+    long long *ps = A.take<long long>(nl + 1);
+    long long run = 0, lmax = 0;
+    for (int base = 0; base < nl; base += blockDim.x) {
+        const int li = base + threadIdx.x;
+        const long long len = li < nl ? cnt[lo + li] : 0;
+        lmax = max(lmax, len);
+        long long tot;
+        const long long ex = block_excl_scan<long long>(len, bs, &tot);
+        if (ps && li < nl) ps[li] = run + ex;
+        run += tot;
+    }
+    lmax = block_max_ll(lmax, bs);
+    if (lmax <= 1) return;  // nothing to order
+    int *ks = ps ? A.take<int>(run) : nullptr;
+    V *vs = ks ? A.take<V>(run) : nullptr;
+    if (!vs) {
+        // insertion sort of each line in global memory (chunks too large to stage)
+        for (int li = threadIdx.x; li < nl; li += blockDim.x) {
+            const long long b = ptr[lo + li];
+            const int len = cnt[lo + li];
+            for (int a = 1; a < len; ++a) {
+                const int key = idx[b + a];
+                const V v = val[b + a];
+                int c = a - 1;
+                while (c >= 0 && idx[b + c] > key) {
+                    idx[b + c + 1] = idx[b + c];
+                    val[b + c + 1] = val[b + c];
+                    --c;
+                }
+                idx[b + c + 1] = key;
+                val[b + c + 1] = v;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    if (threadIdx.x == 0) ps[nl] = run;
+    __syncthreads();
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const Grp G(8);
+        for (int base = 0; base < nl; base += nw * G.rpw) {
+            const int li = base + warp * G.rpw + G.sub;
+            if (li < nl) {
+                const long long o = ps[li], len = ps[li + 1] - o, b = ptr[lo + li];
+                for (long long k = G.sl; k < len; k += G.L) {
+                    ks[o + k] = idx[b + k];
+                    vs[o + k] = val[b + k];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    int Ls = 1;
+    {
+        const long long avg = (run + nl - 1) / nl;
+        while (Ls < 32 && 2ll * Ls < avg) Ls *= 2;
+    }
+    const long long cap = 8ll * Ls;
+    {
+        const Grp G(Ls);
+        for (int base = 0; base < nl; base += nw * G.rpw) {
+            const int li = base + warp * G.rpw + G.sub;
+            if (li < nl) {
+                const long long o = ps[li], len = ps[li + 1] - o;
+                if (len >= 2 && len <= cap)
+                    rank_place(ks + o, vs + o, (int)len, G.sl, G.L, idx + ptr[lo + li],
+                               val + ptr[lo + li]);
+            }
+        }
+    }
+    if (lmax > cap) {
+        for (int li = warp; li < nl; li += nw) {
+            const long long o = ps[li], len = ps[li + 1] - o;
+            if (len > cap)
+                rank_place(ks + o, vs + o, (int)len, lane, 32, idx + ptr[lo + li],
+                           val + ptr[lo + li]);
+        }
+    }
+    __syncthreads();
+}
+
 // Copies this CTA's chunk of a side into shared memory (compacting the
 // lines), if it fits.  All threads of the CTA call it.
+// With sort (a side phase_select_scatter wrote in arbitrary order), every
+// line of the chunk is also sorted by index: each entry's place is its rank
+// among the line's (distinct) indices, taken from the shared-memory copy; the
+// entries are written back to the global arrays in that order and the copy
+// is reloaded.  A chunk that does not fit is sorted in global memory
+// (sort_scattered_lines) and read from there.
 template <typename V>
 __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A, BlockScratch &bs,
-                                                 int rank, int nct) {
+                                                 int rank, int nct, bool sort = false) {
     const Chunk C(S.n, rank, nct);
     CtaSide<V> out;
     out.nl = (int)(C.hi - C.lo);
@@ -280,6 +410,9 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
     long long *gs = ps ? A.take<long long>(out.nl) : nullptr;  // global start of each line
     if (!gs) {
         A = save;
+        if (sort)
+            sort_scattered_lines<V>(S.ptr, S.cnt, const_cast<int *>(S.idx), const_cast<V *>(S.val),
+                                    C.lo, C.hi, A, bs);
         return out;
     }
     // line lengths -> local offsets (exclusive scan in line order)
@@ -314,6 +447,9 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
     if (!vs) {
         A = save;
         __syncthreads();
+        if (sort)
+            sort_scattered_lines<V>(S.ptr, S.cnt, const_cast<int *>(S.idx), const_cast<V *>(S.val),
+                                    C.lo, C.hi, A, bs);
         return out;
     }
     __syncthreads();
@@ -333,6 +469,54 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
         }
     }
     __syncthreads();
+    if (sort) {
+        // ranks from the copy, entries to their places in the global arrays
+        int *gidx = const_cast<int *>(S.idx);
+        V *gval = const_cast<V *>(S.val);
+        const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        int Ls = 1;
+        {
+            const long long avg = out.nl > 0 ? (run + out.nl - 1) / out.nl : 0;
+            while (Ls < 32 && 2ll * Ls < avg) Ls *= 2;
+        }
+        const long long cap = 8ll * Ls;
+        bool has_long = false;
+        {
+            const Grp G(Ls);
+            for (int base = 0; base < out.nl; base += nw * G.rpw) {
+                const int li = base + warp * G.rpw + G.sub;
+                if (li < out.nl) {
+                    const long long o = ps[li], len = ps[li + 1] - o;
+                    if (len >= 2 && len <= cap)
+                        rank_place(is + o, vs + o, (int)len, G.sl, G.L, gidx + gs[li],
+                                   gval + gs[li]);
+                    has_long |= len > cap;
+                }
+            }
+        }
+        if (__syncthreads_or(has_long)) {
+            for (int li = warp; li < out.nl; li += nw) {
+                const long long o = ps[li], len = ps[li + 1] - o;
+                if (len > cap)
+                    rank_place(is + o, vs + o, (int)len, lane, 32, gidx + gs[li], gval + gs[li]);
+            }
+        }
+        __syncthreads();
+        // reload the rewritten lines
+        const Grp G(Ls);
+        for (int base = 0; base < out.nl; base += nw * G.rpw) {
+            const int li = base + warp * G.rpw + G.sub;
+            if (li < out.nl) {
+                const long long o = ps[li], len = ps[li + 1] - o, b = gs[li];
+                if (len >= 2)
+                    for (long long k = G.sl; k < len; k += G.L) {
+                        is[o + k] = gidx[b + k];
+                        vs[o + k] = gval[b + k];
+                    }
+            }
+        }
+        __syncthreads();
+    }
     out.cached = true;
     out.Lf = Lf;
     out.ptr = ps;
@@ -404,7 +588,10 @@ __device__ __forceinline__ V lsqr_block_sum(V v, BlockScratch &bs) {
 // (unit columns): the rows phase gathers D v~, the cols phase scales B^T u~
 // by D, and y_g receives y = D y^, so B y_g is the projection of c0 whatever
 // the scaling.  Returns the number of steps (0 if alpha1 == 0), or -1 if a
-// grid barrier was abandoned.
+// grid barrier was abandoned.  sort_side (1 = R, 2 = C): that side was
+// written by phase_select_scatter, and each CTA sorts the lines of its chunk
+// of it while caching them (cache_side); the CTA alone reads them before the
+// first barrier.
 //
 // Per phase: grid barrier | warp 0 reduces the partials and updates the
 // scalars while warps 1.. compute the dot products of the CTA's lines |
@@ -414,7 +601,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
                                         const SideC<V> &Cs, const V *c0, int c0s, V *y_g, V *xt,
                                         const V *csc, const V *rsc, bool v_given, V alpha1,
                                         V beta1, V fro2, unsigned char *dsmem,
-                                        long long dsmem_bytes, SolveSmem &S) {
+                                        long long dsmem_bytes, SolveSmem &S, int sort_side = 0) {
     LsqrStateT<V> &L = S.lsqr<V>();
     SmemArena A{dsmem, dsmem_bytes, 0};
     const Chunk RC(Rs.n, trank(P), tsize(P)), CC(Cs.n, trank(P), tsize(P));
@@ -458,8 +645,8 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
     const V *usrc = rsc ? P.uus : P.uu;
     // the rows phase gathers D v~ when the v-space is scaled
     const V *vsrc = csc ? P.vvs : P.vv;
-    const CtaSide<V> R = cache_side<V>(Rs, A, S.bs, trank(P), tsize(P));
-    const CtaSide<V> C = cache_side<V>(Cs, A, S.bs, trank(P), tsize(P));
+    const CtaSide<V> R = cache_side<V>(Rs, A, S.bs, trank(P), tsize(P), sort_side == 1);
+    const CtaSide<V> C = cache_side<V>(Cs, A, S.bs, trank(P), tsize(P), sort_side == 2);
     if (threadIdx.x == 0) {
         L.inv_b = V(1) / beta1;
         L.done = 0;
@@ -481,7 +668,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
         }
         acc = lsqr_block_sum(acc, S.bs);
         if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
-        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
+        if (!grid_barrier(P.ctrl, bar_of(P), S.epoch, tsize(P))) return -1;
         if (threadIdx.x < 32) {
             const V vv = warp0_collect(P.pd, D_VV, tsize(P));
             if (threadIdx.x == 0) L.alpha = vsqrt(vv);
@@ -554,7 +741,7 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
             acc = lsqr_block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_UU * tsize(P) + trank(P)] = acc;
         }
-        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
+        if (!grid_barrier(P.ctrl, bar_of(P), S.epoch, tsize(P))) return -1;
 
         // ---- cols phase: v~_new = B^T u~ / beta - (beta/alpha) v~, y update
         cta_dots<V>(C, usrc, dc);
@@ -601,47 +788,232 @@ __device__ __forceinline__ int run_lsqr(const ParamsT<V> &P, const SideC<V> &Rs,
             acc = lsqr_block_sum(acc, S.bs);
             if (threadIdx.x == 0) P.pd[D_VV * tsize(P) + trank(P)] = acc;
         }
-        if (!grid_barrier(P.ctrl, S.epoch, tsize(P))) return -1;
+        if (!grid_barrier(P.ctrl, bar_of(P), S.epoch, tsize(P))) return -1;
     }
 }
 
 // z_{k+1} = z_k - A_U y (A_U as extracted CSR), r = t_k - z_{k+1},
 // eps^x_i = r_i^2 / ||A^(i)||^2.  Partials: max eps^x, ||z_{k+1}||^2, bad.
-template <typename V>
+// kMode 0: all of it.  kMode 1 (column team of a two-team solve): z_{k+1}
+// and ||z_{k+1}||^2 only.  kMode 2 (row team): r and the row weights from the
+// z_{k+1} the column team wrote (hasU ignored).
+template <typename V, int kMode = 0>
 __device__ __forceinline__ void phase_zupdate(const ParamsT<V> &P, bool hasU, int Lsub,
                                               BlockScratch &bs) {
-    const Grp G(hasU ? Lsub : 1);
+    constexpr bool kZ = kMode != 2, kR = kMode != 1;
+    const Grp G(kZ && hasU ? Lsub : 1);
     V emax = V(0), zz = V(0);
     long long bad = 0;
     for (long long base = twarp(P) * G.rpw; base < P.m; base += twarps(P) * G.rpw) {
         const long long i = base + G.sub;
         V s = V(0);
-        if (hasU && i < P.m)
+        if (kZ && hasU && i < P.m)
             s = lane_dot<false>(P.rp[i] + G.sl, P.rp[i] + P.srn[i], G.L, P.sci, P.sav,
                                 [&](int p) { return P.yy[p]; });
         s = group_sum(s, G.L);
         if (i < P.m && G.sl == 0) {
-            const V zi = P.z[2 * i] - s;
-            P.z[2 * i] = zi;
-            const V ri = P.t[2 * i] - zi;
-            P.r[i] = ri;
-            const V c = __ldg(P.rn2 + i);
-            const V e = c > V(0) ? weight_of(ri, c) : V(0);
-            P.epsr[i] = e;
-            if (!isfinite(e)) bad = 1;
-            else emax = max_nonneg(emax, e);
-            zz = vfma(zi, zi, zz);
+            V zi;
+            if constexpr (kZ) {
+                zi = P.z[2 * i] - s;
+                P.z[2 * i] = zi;
+                zz = vfma(zi, zi, zz);
+            } else {
+                zi = P.z[2 * i];
+            }
+            if constexpr (kR) {
+                const V ri = P.t[2 * i] - zi;
+                P.r[i] = ri;
+                const V c = __ldg(P.rn2 + i);
+                const V e = c > V(0) ? weight_of(ri, c) : V(0);
+                P.epsr[i] = e;
+                if (!isfinite(e)) bad = 1;
+                else emax = max_nonneg(emax, e);
+            }
         }
     }
-    emax = block_max(emax, bs);
-    zz = block_sum(zz, bs);
-    bad = block_sum(bad, bs);
+    if (kR) emax = block_max(emax, bs);
+    if (kZ) zz = block_sum(zz, bs);
+    if (kR) bad = block_sum(bad, bs);
     if (threadIdx.x == 0) {
-        P.pd[D_EMAX_R * tsize(P) + trank(P)] = emax;
-        P.pd[D_ZZ * tsize(P) + trank(P)] = zz;
-        P.pi[I_BAD_R * tsize(P) + trank(P)] = bad;
+        if (kR) P.pd[D_EMAX_R * tsize(P) + trank(P)] = emax;
+        if (kZ) P.pd[D_ZZ * tsize(P) + trank(P)] = zz;
+        if (kR) P.pi[I_BAD_R * tsize(P) + trank(P)] = bad;
     }
 }
+
+// Sizes and inner steps of one block of an outer iteration.
+struct BlockInfo {
+    long long n, nnz;
+    int steps, lanes;
+};
+
+#define RGD_SYNC_I(dm, dx, im)                                                   \
+    do {                                                                         \
+        if (!sync_collect(P, S, (dm), (dx), (im), red)) return -1;               \
+    } while (0)
+
+// Column block of iteration k (Algorithm 1, column step; Eq. 4 and Remark
+// 3.1): U_k drawn from eps^z (P.epsc, maximum O.emax_c > 0) with Philox
+// counter (k, 0), A_U scattered from the CSC columns of U into the rows of
+// A_U, and LSQR on A_U D from z_k (beta1 = sqrt(O.zz)); y goes to P.yy for the
+// z update.  ulist receives U_k; with tr_on it is also recorded at
+// P.tr_lists[tr_base ..] if it fits.  Returns 0, or -1 if a barrier was
+// abandoned.
+template <typename V>
+__device__ __forceinline__ int col_block(const ParamsT<V> &P, SolveSmem &S, unsigned char *dsmem,
+                                         long long k, int *ulist, bool tr_on, long long tr_base,
+                                         BlockInfo &U) {
+    BlockScratch &bs = S.bs;
+    OuterStateT<V> &O = S.o<V>();
+    V *const red = S.red<V>();
+    const int nct = tsize(P);
+    const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
+    // quantise (the row counts of A_U cleared) | draws, counted per chunk |
+    // compaction + scatter of the selected columns into the rows of A_U
+    phase_quantize(P, P.epsc, P.n, O.emax_c, greedy, P.eta_col, bs, true, P.srn, P.m);
+    RGD_SYNC_I(0, 0, 0);
+    if (!greedy) {
+        phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs,
+                   P.pi + I_CNT * nct);
+        RGD_SYNC_I(0, 0, 0);
+    }
+    mark(S, PH_COL_SEL);
+    if (threadIdx.x == 0) {
+        O.beta1 = vsqrt(O.zz);
+        O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
+    }
+    __syncthreads();
+    const V inv_beta1 = O.inv_beta1;
+    // LSQR start on B = A_U D (columns scaled to unit norm, D =
+    // diag(1/||A_j||)) with c = z_k: v~_1 = B^T z_k / beta1
+    U.n = phase_select_scatter(
+        P, P.n, P.cn2, P.g, P.epsc, nullptr, ulist, S.tab, bs, P.cp, P.ri, P.cv, P.rp,
+        P.srn, P.sci, P.sav, [&](long long p, long long j, long long tot) {
+            const V d = vrsqrt(P.cn2[j]);           // selected: ||A_j|| > 0
+            const V v1 = P.g[j] * d * inv_beta1;
+            P.dsc[p] = d;
+            P.vv[p] = v1;
+            P.vvs[p] = v1 * d;
+            P.yy[p] = V(0);
+            if (tr_on && tr_base + tot <= P.tr_list_cap) P.tr_lists[tr_base + p] = (int)j;
+        });
+    RGD_SYNC_I(DS(D_FRO_S) | DS(D_EXTRA_S), 0, DS(I_NNZ));
+    mark(S, PH_COL_EXT);
+    if (threadIdx.x == 0) {
+        // beta1 = ||z_k||, alpha1 = ||B^T z_k|| / beta1 = sqrt(sum of the
+        // selected eps^z) / beta1, ||B||_F^2 = |U|
+        O.fro2 = red[D_FRO_S];
+        O.alpha1 = vsqrt(red[D_EXTRA_S]) * O.inv_beta1;
+    }
+    __syncthreads();
+    U.nnz = S.red_i[I_NNZ];
+    U.lanes = pick_lanes_fp64(U.nnz, P.m);
+    if (O.beta1 > V(0) && O.alpha1 > V(0)) {
+        const SideC<V> rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, U.lanes};
+        const SideC<V> cols{P.cp, nullptr, ulist, P.ri, P.cv, U.n, P.tpc};
+        U.steps = run_lsqr<V>(P, rows, cols, P.z, 2, P.yy, nullptr, P.dsc, nullptr, true,
+                             O.alpha1, O.beta1, O.fro2, dsmem, P.dsmem_bytes, S, 1);
+        if (U.steps < 0) return -1;
+        mark(S, PH_COL_LSQR);
+    }
+    return 0;
+}
+
+// Row block of iteration k (Algorithm 1, row step): J_k drawn from eps^x
+// (P.epsr, maximum O.emax_r > 0) with Philox counter (k, 1), A^J scattered from
+// the CSR rows of J into the columns of A^J, and the minimum-norm solution of
+// A^J d = r_J by LSQR (first on the row-scaled block, see below); d goes to
+// P.dx and x + d to P.xt.  With tr_on, J_k is recorded at P.tr_lists[tr_base
+// ..] if it fits.  Returns 0, or -1 if a barrier was abandoned.
+template <typename V>
+__device__ __forceinline__ int row_block(const ParamsT<V> &P, SolveSmem &S, unsigned char *dsmem,
+                                         long long k, bool tr_on, long long tr_base,
+                                         BlockInfo &J) {
+    constexpr bool kF32 = sizeof(V) == 4;
+    BlockScratch &bs = S.bs;
+    OuterStateT<V> &O = S.o<V>();
+    V *const red = S.red<V>();
+    const int nct = tsize(P);
+    const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
+    // quantise (the column counts of A^J cleared) | draws | compaction +
+    // scatter of the selected rows into the columns of A^J
+    phase_quantize(P, P.epsr, P.m, O.emax_r, greedy, P.eta_row, bs, true, P.scn, P.n);
+    RGD_SYNC_I(0, 0, 0);
+    if (!greedy) {
+        phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs,
+                   P.pi + I_CNT * nct);
+        RGD_SYNC_I(0, 0, 0);
+    }
+    mark(S, PH_ROW_SEL);
+    // |J| <= n: first on D A^J (rows scaled to unit norm, D =
+    // diag(1/||A^(i)||)) with c = D r_J, which has the same minimum-norm
+    // solution whenever the block system is consistent
+    J.n = phase_select_scatter(
+        P, P.m, P.rn2, P.r, P.epsr, nullptr, P.jlist, S.tab, bs, P.rp, P.ci, P.av, P.cp,
+        P.scn, P.sri, P.scv, [&](long long p, long long i, long long tot) {
+            const V ri = P.r[i];
+            if (tot <= P.n) {
+                const V d = vrsqrt(P.rn2[i]);      // selected: ||A^(i)|| > 0
+                const V u1 = ri * d;               // u~_1 = D r_J
+                P.dsr[p] = d;
+                P.uu[p] = u1;
+                P.uus[p] = u1 * d;
+            } else {
+                P.uu[p] = ri;  // u~_1 = r_J
+            }
+            if (tr_on && tr_base + tot <= P.tr_list_cap) P.tr_lists[tr_base + p] = (int)i;
+        });
+    RGD_SYNC_I(DS(D_FRO) | DS(D_EXTRA) | DS(D_FRO_S) | DS(D_EXTRA_S), 0, DS(I_NNZ));
+    mark(S, PH_ROW_EXT);
+    if (threadIdx.x == 0) {
+        // LSQR start on A^J with c = r_J: beta1 = ||r_J||; on D A^J
+        // (unit rows) with c = D r_J: beta1 = sqrt(sum of the weights)
+        O.fro2 = red[D_FRO];
+        O.beta1 = vsqrt(red[D_EXTRA]);
+        O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
+        O.fro2s = red[D_FRO_S];
+        O.beta1s = vsqrt(red[D_EXTRA_S]);
+    }
+    __syncthreads();
+    const bool rscale = J.n <= P.n;
+    J.nnz = S.red_i[I_NNZ];
+    if (O.beta1 > V(0)) {
+        const SideC<V> rows{P.rp, nullptr, P.jlist, P.ci, P.av, J.n, P.tpr};
+        const SideC<V> cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
+                            pick_lanes_fp64(J.nnz, P.n)};
+        int fit = 0;
+        if (rscale) {
+            J.steps = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr, P.dsr,
+                                 false, V(0), O.beta1s, O.fro2s, dsmem, P.dsmem_bytes, S,
+                                 2);
+            if (J.steps < 0) return -1;
+            fit = S.lsqr<V>().fit;
+        }
+        // The FP32 inner solve keeps the row-scaled step even when LSQR
+        // finds the block inconsistent at FP32 rounding level: the step
+        // still lies in range(A^T), and the FP64 refinement removes the
+        // difference.  The FP64 solve takes (A^J)^+ r_J exactly.
+        if (!rscale || (!kF32 && fit == 0)) {
+            if (rscale) {
+                // found inconsistent: (A^J)^+ r_J needs the unscaled block;
+                // the scaled attempt's x + y is undone first
+                for (long long p = tthread(P); p < J.n; p += tthreads(P))
+                    P.uu[p] = P.r[P.jlist[p]];
+                for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.xt[j] = P.x[j];
+                RGD_SYNC_I(0, 0, 0);
+            }
+            const int s2 = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr,
+                                       nullptr, false, V(0), O.beta1, O.fro2, dsmem,
+                                       P.dsmem_bytes, S, rscale ? 0 : 2);
+            if (s2 < 0) return -1;
+            J.steps += s2;
+        }
+        mark(S, PH_ROW_LSQR);
+    }
+    return 0;
+}
+
+#undef RGD_SYNC_I
 
 // Result of one solve_body: the status to finish with (kAbandoned when a
 // barrier was abandoned), the iteration reached and the measures of x_k.
@@ -675,7 +1047,6 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
     OuterStateT<V> &O = S.o<V>();
     V *const red = S.red<V>();
     const int nct = tsize(P);
-    const bool greedy = P.selection == RGDBEK_SELECT_GREEDY;
 
     // ---- x_0 = 0, z_0 = b, t_0 = b - A x_0 = b, dx = 0
     {
@@ -765,64 +1136,16 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
         if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, k, O.rel, O.nrm};
 
         // ---- column block U_k and z_{k+1} = z_k - A_U A_U^+ z_k
-        long long nU = 0, nnzU = 0;
-        int stepsU = 0, Lsub_u = 1;
+        BlockInfo U{0, 0, 0, 1};
         bool rec_u = !S.tr_full;
         if (O.emax_c > V(0)) {
-            phase_quantize(P, P.epsc, P.n, O.emax_c, greedy, P.eta_col, bs);
-            RGD_SYNC(0, 0, 0);
-            if (!greedy) {
-                phase_draw(P, P.n, P.s_col, P.seed, P.sysid, (unsigned long long)k, 0ull, S.tab, bs);
-                RGD_SYNC(0, 0, 0);
-            }
-            phase_compact_count(P, P.n, P.cn2, P.g, P.epsc, bs);
-            RGD_SYNC(DS(D_FRO_S) | DS(D_EXTRA_S), 0, 0);
-            if (threadIdx.x == 0) {
-                // LSQR start on B = A_U D (columns scaled to unit norm, D =
-                // diag(1/||A_j||)) with c = z_k: beta1 = ||z_k||, alpha1 =
-                // ||B^T z_k|| / beta1 = sqrt(sum of the selected eps^z) / beta1,
-                // ||B||_F^2 = |U|
-                O.fro2 = red[D_FRO_S];
-                O.beta1 = vsqrt(O.zz);
-                O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
-                O.alpha1 = vsqrt(red[D_EXTRA_S]) * O.inv_beta1;
-            }
-            nU = phase_compact_write(P, P.n, P.colpos, P.ulist, S.tab, bs);
-            RGD_SYNC(0, 0, 0);
-            mark(S, PH_COL_SEL);
-            rec_u = !S.tr_full && S.tr_off + nU <= P.tr_list_cap;
-            const V inv_beta1 = O.inv_beta1;
-            for (long long p = tthread(P); p < nU; p += tthreads(P)) {
-                const int j = P.ulist[p];
-                const V d = vrsqrt(P.cn2[j]);           // selected: ||A_j|| > 0
-                const V v1 = P.g[j] * d * inv_beta1;    // v~_1 = B^T z_k / beta1
-                P.dsc[p] = d;
-                P.vv[p] = v1;
-                P.vvs[p] = v1 * d;
-                P.yy[p] = V(0);
-                if (rec_u) P.tr_lists[S.tr_off + p] = j;
-            }
-            // A_U: the entries of every row of A that lie in U's columns
-            // about ten entries per lane, as in the FP64 passes (measured: fewer
-            // lanes per line keep more lines, and so more loads, in flight)
-            const Lines<V> Arows{P.rp, P.ci, P.av, P.m, P.tpr};
-            phase_extract(P, Arows, P.colpos, P.srn, P.sci, P.sav, bs);
-            RGD_SYNC(0, 0, DS(I_NNZ));
-            mark(S, PH_COL_EXT);
-            nnzU = S.red_i[I_NNZ];
-            Lsub_u = pick_lanes_fp64(nnzU, P.m);
-            if (O.beta1 > V(0) && O.alpha1 > V(0)) {
-                const SideC<V> rows{P.rp, P.srn, nullptr, P.sci, P.sav, P.m, Lsub_u};
-                const SideC<V> cols{P.cp, nullptr, P.ulist, P.ri, P.cv, nU, P.tpc};
-                stepsU = run_lsqr<V>(P, rows, cols, P.z, 2, P.yy, nullptr, P.dsc, nullptr, true,
-                                     O.alpha1, O.beta1, O.fro2, dsmem, P.dsmem_bytes, S);
-                if (stepsU < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
-                mark(S, PH_COL_LSQR);
-            }
+            if (col_block<V>(P, S, dsmem, k, P.ulist, !S.tr_full, S.tr_off, U) < 0)
+                return SolveOut<V>{kAbandoned, k, V(0), V(0)};
+            rec_u = !S.tr_full && S.tr_off + U.n <= P.tr_list_cap;
         }
 
         // ---- z_{k+1}, row residual r = b - z_{k+1} - A x_k, row weights
-        phase_zupdate(P, nU > 0, Lsub_u, bs);
+        phase_zupdate(P, U.n > 0, U.lanes, bs);
         RGD_SYNC(DS(D_EMAX_R) | DS(D_ZZ), DS(D_EMAX_R), DS(I_BAD_R));
         mark(S, PH_ZUPD);
         if (P.tr_r && k < P.tr_vec_cap)  // trace: the row residual r = b - z_{k+1} - A x_k
@@ -837,88 +1160,15 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
         if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, k, O.rel, O.nrm};
 
         // ---- row block J_k and dx = (A^J)^+ r_J
-        long long nJ = 0, nnzJ = 0;
-        int stepsJ = 0;
+        BlockInfo J{0, 0, 0, 1};
         bool rec_j = false;
         if (O.emax_r > V(0)) {
-            phase_quantize(P, P.epsr, P.m, O.emax_r, greedy, P.eta_row, bs);
-            RGD_SYNC(0, 0, 0);
-            if (!greedy) {
-                phase_draw(P, P.m, P.s_row, P.seed, P.sysid, (unsigned long long)k, 1ull, S.tab, bs);
-                RGD_SYNC(0, 0, 0);
-            }
-            phase_compact_count(P, P.m, P.rn2, P.r, P.epsr, bs);
-            RGD_SYNC(DS(D_FRO) | DS(D_EXTRA) | DS(D_FRO_S) | DS(D_EXTRA_S), 0, 0);
-            if (threadIdx.x == 0) {
-                // LSQR start on A^J with c = r_J: beta1 = ||r_J||; on D A^J
-                // (unit rows) with c = D r_J: beta1 = sqrt(sum of the weights)
-                O.fro2 = red[D_FRO];
-                O.beta1 = vsqrt(red[D_EXTRA]);
-                O.inv_beta1 = O.beta1 > V(0) ? V(1) / O.beta1 : V(0);
-                O.fro2s = red[D_FRO_S];
-                O.beta1s = vsqrt(red[D_EXTRA_S]);
-            }
-            nJ = phase_compact_write(P, P.m, P.rowpos, P.jlist, S.tab, bs);
-            RGD_SYNC(0, 0, 0);
-            mark(S, PH_ROW_SEL);
-            rec_j = rec_u && S.tr_off + nU + nJ <= P.tr_list_cap;
-            // |J| <= n: first on D A^J (rows scaled to unit norm, D =
-            // diag(1/||A^(i)||)) with c = D r_J, which has the same minimum-norm
-            // solution whenever the block system is consistent
-            const bool rscale = nJ <= P.n;
-            for (long long p = tthread(P); p < nJ; p += tthreads(P)) {
-                const int i = P.jlist[p];
-                const V ri = P.r[i];
-                if (rscale) {
-                    const V d = vrsqrt(P.rn2[i]);      // selected: ||A^(i)|| > 0
-                    const V u1 = ri * d;               // u~_1 = D r_J
-                    P.dsr[p] = d;
-                    P.uu[p] = u1;
-                    P.uus[p] = u1 * d;
-                } else {
-                    P.uu[p] = ri;  // u~_1 = r_J
-                }
-                if (rec_j) P.tr_lists[S.tr_off + nU + p] = i;
-            }
-            // A^J: the entries of every column of A that lie in J's rows
-            const Lines<V> Acols{P.cp, P.ri, P.cv, P.n, P.tpc};
-            phase_extract(P, Acols, P.rowpos, P.scn, P.sri, P.scv, bs);
-            RGD_SYNC(0, 0, DS(I_NNZ));
-            mark(S, PH_ROW_EXT);
-            nnzJ = S.red_i[I_NNZ];
-            if (O.beta1 > V(0)) {
-                const SideC<V> rows{P.rp, nullptr, P.jlist, P.ci, P.av, nJ, P.tpr};
-                const SideC<V> cols{P.cp, P.scn, nullptr, P.sri, P.scv, P.n,
-                                    pick_lanes_fp64(nnzJ, P.n)};
-                int fit = 0;
-                if (rscale) {
-                    stepsJ = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr, P.dsr,
-                                         false, V(0), O.beta1s, O.fro2s, dsmem, P.dsmem_bytes, S);
-                    if (stepsJ < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
-                    fit = S.lsqr<V>().fit;
-                }
-                // The FP32 inner solve keeps the row-scaled step even when LSQR
-                // finds the block inconsistent at FP32 rounding level: the step
-                // still lies in range(A^T), and the FP64 refinement removes the
-                // difference.  The FP64 solve takes (A^J)^+ r_J exactly.
-                if (!rscale || (!kF32 && fit == 0)) {
-                    if (rscale) {
-                        // found inconsistent: (A^J)^+ r_J needs the unscaled block;
-                        // the scaled attempt's x + y is undone first
-                        for (long long p = tthread(P); p < nJ; p += tthreads(P))
-                            P.uu[p] = P.r[P.jlist[p]];
-                        for (long long j = tthread(P); j < P.n; j += tthreads(P)) P.xt[j] = P.x[j];
-                        RGD_SYNC(0, 0, 0);
-                    }
-                    const int s2 = run_lsqr<V>(P, rows, cols, P.uu, 1, P.dx, P.xt, nullptr,
-                                               nullptr, false, V(0), O.beta1, O.fro2, dsmem,
-                                               P.dsmem_bytes, S);
-                    if (s2 < 0) return SolveOut<V>{kAbandoned, k, V(0), V(0)};
-                    stepsJ += s2;
-                }
-                mark(S, PH_ROW_LSQR);
-            }
+            if (row_block<V>(P, S, dsmem, k, rec_u, S.tr_off + U.n, J) < 0)
+                return SolveOut<V>{kAbandoned, k, V(0), V(0)};
+            rec_j = rec_u && S.tr_off + U.n + J.n <= P.tr_list_cap;
         }
+        const long long nU = U.n, nJ = J.n, nnzU = U.nnz, nnzJ = J.nnz;
+        const int stepsU = U.steps, stepsJ = J.steps;
 
         if (threadIdx.x == 0) {
             Acc &acc = S.acc;
@@ -963,6 +1213,441 @@ __device__ __forceinline__ SolveOut<V> solve_body(const ParamsT<V> &P, SolveSmem
 }
 
 #undef RGD_SYNC
+
+// ---------------------------------------------------------------------------
+// Two-team schedule of one solve (P.zteam > 0).
+//
+// In Algorithm 1 the column step of iteration k maps z_k to z_{k+1} with
+// weights, draws and projections that depend on z_k alone (z_0 = b), while
+// the row step of iteration k needs z_{k+1} and x_k.  So the column step of
+// iteration k+1 can run while the row step of iteration k runs.  The grid is
+// cut into a row team (the first team - zteam CTAs) and a column team (the
+// last zteam CTAs), each with its own barrier counter:
+//   column team, iteration k:  g = A^T z_k, eps^z, and h = A^T t for the row
+//                              team's stopping test | U_k, A_U, LSQR | (once
+//                              the row team has read z_k) z_{k+1} = z_k - A_U y
+//   row team, iteration k:     (once z_{k+1} is written) r = t_k - z_{k+1},
+//                              eps^x | J_k, A^J, LSQR -> x_k + dx | stopping
+//                              test of x_k | t_{k+1} = b - A x_{k+1}, x_{k+1}
+//                              adopted
+// Every quantity comes from the same inputs as in solve_body, so the iterates
+// are those of Algorithm 1; only the partition of the reductions over CTAs
+// differs (rounding level).  The test of x_k needs ||A^T t_k||, which the
+// column team forms in the pass that forms g = A^T z_{k+1} (t_k is written at
+// the end of row step k-1); so the row team tests x_k after its row step k,
+// returns x_k if the test holds (that row step and its counters are then
+// discarded), and otherwise adopts x_{k+1}.  x_{k0} is tested before the first
+// row step, and x_k with k >= max_iter before its row step (that test stops).
+//
+// Link words (Ctrl::lk_*) hold (call << 32) | count, so the calls of one
+// kernel (the inner solves of the refinement loop) never see an earlier
+// call's words:
+//   lk_colpass = c|j+1 after column pass k0 + j, with, in slot j & 1, its
+//                ||A^T t||^2 (t_{k0} for j = 0, t_{k0+j-1} for j >= 2, none
+//                for j = 1), the non-finite flag of eps^z and (j = 0)
+//                ||A^T b||^2
+//   lk_zready  = c|j+1 once z_{k0+j+1} is written; |U|, nnz(A_U) and the
+//                LSQR steps in slot j & 1, U_{k0+j} in list j & 1
+//   lk_zused   = c|j+1 once the row team has read z_{k0+j+1}
+//   lk_tready  = c|j   once t_{k0+j} is written
+//   lk_stop    = c     once the row team has finished
+// The column team writes z_{k+1} over z_k only after the row team has read
+// z_k; the row team writes t_{k+1} over t_k only after the column pass that
+// reads t_k.  A slot or list of parity j is rewritten two iterations later,
+// after its reader has passed a point its writer waits for.
+// ---------------------------------------------------------------------------
+
+// dst = src by all threads of the CTA (dst in shared memory), then a barrier
+template <typename PT>
+__device__ __forceinline__ void copy_params(PT &dst, const PT &src) {
+    const int *s = reinterpret_cast<const int *>(&src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(PT) / sizeof(int)); w += blockDim.x) d[w] = s[w];
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long lk_enc(unsigned long long call, long long n) {
+    return (call << 32) | (unsigned long long)n;
+}
+
+#define X_SYNC(dm, dx, im)                                                        \
+    do {                                                                          \
+        if (!sync_collect(P, S, (dm), (dx), (im), red))                           \
+            return SolveOut<V>{kAbandoned, 0, V(0), V(0)};                        \
+    } while (0)
+#define X_WAIT(word, target)                                                      \
+    do {                                                                          \
+        if (link_wait(C, &C->word, (target), 0ull) != 0)                          \
+            return SolveOut<V>{kAbandoned, 0, V(0), V(0)};                        \
+    } while (0)
+
+// The row team's part of a two-team solve: the status, the iteration and the
+// measures of the returned x (as solve_body).
+template <typename V>
+__device__ __forceinline__ SolveOut<V> xchain_body(const ParamsT<V> &P, SolveSmem &S,
+                                                   unsigned char *dsmem, unsigned long long call,
+                                                   int *const *ulists) {
+    constexpr bool kF32 = sizeof(V) == 4;
+    BlockScratch &bs = S.bs;
+    OuterStateT<V> &O = S.o<V>();
+    V *const red = S.red<V>();
+    const int nct = tsize(P);
+    Ctrl *const C = P.ctrl;
+    const bool lead = trank(P) == 0 && threadIdx.x == 0;
+
+    // ---- x_0 (0 or the caller's), xt = x_0, t_0 = b, ||b||^2, non-finite inputs
+    {
+        V bb = V(0);
+        long long bad = 0;
+        for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
+            const V bi = ld_rhs(P.b + i);
+            P.t[2 * i] = bi;
+            bb = vfma(bi, bi, bb);
+            if (!isfinite(bi)) bad = 1;
+        }
+        for (long long j = tthread(P); j < P.n; j += tthreads(P)) {
+            const V x0 = P.warm ? P.x[j] : V(0);
+            if (!isfinite(x0)) bad = 1;
+            P.x[j] = x0;
+            P.xt[j] = x0;
+        }
+        bb = block_sum(bb, bs);
+        bad = block_sum(bad, bs);
+        if (threadIdx.x == 0) {
+            P.pd[D_BB * nct + trank(P)] = bb;
+            P.pi[I_BAD_R * nct + trank(P)] = bad;
+        }
+    }
+    X_SYNC(DS(D_BB), 0, DS(I_BAD_R));
+    if (P.warm) {
+        phase_residual(P, bs);  // t_0 = b - A x_0
+        X_SYNC(DS(D_TT), 0, 0);
+    }
+    mark(S, PH_SETUP);
+    if (threadIdx.x == 0) {
+        O.bb = red[D_BB];
+        O.tt = P.warm ? red[D_TT] : O.bb;
+        O.atb2 = V(0);
+        O.best = V(0);
+        O.kbest = P.k0;
+        O.itol = (V)P.inner_tol;
+        O.verdict = (S.red_i[I_BAD_R] != 0 || !isfinite(O.bb)) ? RGDBEK_ERR_NONFINITE
+                                                                : kStatusRunning;
+    }
+    __syncthreads();
+    if (O.verdict != kStatusRunning) return SolveOut<V>{O.verdict, P.k0, V(NAN), V(NAN)};
+    if (lead) st_release_u64(&C->lk_tready, lk_enc(call, 0));
+
+    // Stopping test of x_k (the rule of solve_body) from ||t_k||^2 (O.tt) and
+    // the column team's ||A^T t_k||^2 and eps^z flag (link slots sh, sb).
+    const auto verdict_of = [&](long long k, int sh, int sb) -> int {
+        if (threadIdx.x == 0) {
+            if (k == P.k0) O.atb2 = (V)__ldcg(&C->lk_gg);
+            const V hh = (V)__ldcg(&C->lk_hh[sh]);
+            const long long badc = __ldcg(&C->lk_badc[sb]);
+            O.rel = O.bb > V(0) ? vsqrt(O.tt / O.bb) : V(0);
+            O.nrm = O.atb2 > V(0) ? vsqrt(hh / O.atb2) : V(0);
+            const V meas = P.stop_rule == RGDBEK_STOP_REL_RES
+                               ? O.rel
+                               : (P.stop_rule == RGDBEK_STOP_RSE ? O.rel * O.rel : O.nrm);
+            if (k == P.k0 || meas < O.best) {
+                O.best = meas;
+                O.kbest = k;
+            }
+            int v = kStatusRunning;
+            if (badc != 0 || !isfinite(hh) || !isfinite(O.tt)) v = RGDBEK_ERR_NONFINITE;
+            else if (stop_rule_holds(P.stop_rule, P.tol, O.rel, O.nrm)) v = RGDBEK_OK;
+            else if (k >= P.max_iter) v = RGDBEK_NOT_CONVERGED;
+            else if (ld_volatile_i32(&C->stop_req)) v = RGDBEK_ERR_TIMEOUT;
+            else if (kF32 && k - O.kbest >= kInnerStallIters) v = RGDBEK_NOT_CONVERGED;
+            O.verdict = v;
+        }
+        __syncthreads();
+        return O.verdict;
+    };
+
+    for (long long k = P.k0;; ++k) {
+        const long long j = k - P.k0;
+        const int sl = (int)(j & 1), sn = (int)((j + 1) & 1);
+        // the time budget, checked before the barrier of the r phase: every CTA
+        // reads the stop request at the test of x_k, after that barrier
+        if (lead && j >= 1 && P.time_budget_ns > 0.0 &&
+            (double)(globaltimer_ns() - S.t_start) > P.time_budget_ns)
+            C->stop_req = 1;
+        if (j == 0 || k >= P.max_iter) {
+            // x_{k0}: its test needs column pass k0 only; at the cap the test
+            // stops for certain, so it is taken before a row step is spent
+            X_WAIT(lk_colpass, lk_enc(call, j == 0 ? 1 : j + 2));
+            mark(S, PH_COL);
+            const int v = verdict_of(k, j == 0 ? 0 : sn, sl);
+            if (v != kStatusRunning) return SolveOut<V>{v, k, O.rel, O.nrm};
+        }
+
+        // ---- r = t_k - z_{k+1} and the row weights, once z_{k+1} is written
+        X_WAIT(lk_zready, lk_enc(call, j + 1));
+        mark(S, PH_COL);
+        const long long nU = __ldcg(&C->lk_nu[sl]), nnzU = __ldcg(&C->lk_nnzu[sl]);
+        const int stepsU = (int)__ldcg(&C->lk_stepsu[sl]);
+        const bool rec_u = !S.tr_full && S.tr_off + nU <= P.tr_list_cap;
+        if (rec_u) {
+            const int *ul = ulists[sl];
+            for (long long p = tthread(P); p < nU; p += tthreads(P))
+                P.tr_lists[S.tr_off + p] = __ldcg(ul + p);
+        }
+        phase_zupdate<V, 2>(P, false, 1, bs);
+        X_SYNC(DS(D_EMAX_R), DS(D_EMAX_R), DS(I_BAD_R));
+        if (lead) st_release_u64(&C->lk_zused, lk_enc(call, j + 1));
+        mark(S, PH_ZUPD);
+        if (P.tr_r && k < P.tr_vec_cap)  // trace: the row residual r = b - z_{k+1} - A x_k
+            for (long long i = tthread(P); i < P.m; i += tthreads(P))
+                P.tr_r[k * P.m + i] = (double)P.r[i];
+        if (threadIdx.x == 0) O.emax_r = red[D_EMAX_R];
+        __syncthreads();
+        if (S.red_i[I_BAD_R] != 0) {
+            // the test of x_k comes first, as in solve_body
+            if (j >= 1) {
+                X_WAIT(lk_colpass, lk_enc(call, j + 2));
+                const int v = verdict_of(k, sn, sl);
+                if (v != kStatusRunning) return SolveOut<V>{v, k, O.rel, O.nrm};
+            }
+            return SolveOut<V>{RGDBEK_ERR_NONFINITE, k, O.rel, O.nrm};
+        }
+
+        // ---- row block J_k, xt = x_k + (A^J)^+ r_J
+        BlockInfo J{0, 0, 0, 1};
+        bool rec_j = false;
+        if (O.emax_r > V(0)) {
+            if (row_block<V>(P, S, dsmem, k, rec_u, S.tr_off + nU, J) < 0)
+                return SolveOut<V>{kAbandoned, k, V(0), V(0)};
+            rec_j = rec_u && S.tr_off + nU + J.n <= P.tr_list_cap;
+        }
+
+        // ---- stopping test of x_k (column pass k + 1 holds ||A^T t_k||^2)
+        if (j >= 1) {
+            X_WAIT(lk_colpass, lk_enc(call, j + 2));
+            mark(S, PH_COL);
+            const int v = verdict_of(k, sn, sl);
+            if (v != kStatusRunning) return SolveOut<V>{v, k, O.rel, O.nrm};
+        }
+
+        // ---- iteration k stands: its counters and trace
+        const long long nJ = J.n, nnzJ = J.nnz;
+        const int stepsJ = J.steps;
+        if (threadIdx.x == 0) {
+            Acc &acc = S.acc;
+            acc.inner_u += stepsU;
+            acc.inner_j += stepsJ;
+            acc.sum_nu += nU;
+            acc.sum_nj += nJ;
+            acc.sum_nnzu += nnzU;
+            acc.sum_nnzj += nnzJ;
+            acc.lsqr_nnzu += (long long)stepsU * nnzU;
+            acc.lsqr_nnzj += (long long)stepsJ * nnzJ;
+            acc.lsqr_nu += (long long)stepsU * nU;
+            acc.lsqr_nj += (long long)stepsJ * nJ;
+        }
+        if (lead && P.tr_counts && k < P.tr_count_cap) {
+            P.tr_counts[4 * k + 0] = nU;
+            P.tr_counts[4 * k + 1] = nJ;
+            P.tr_counts[4 * k + 2] = stepsU;
+            P.tr_counts[4 * k + 3] = stepsJ;
+        }
+        if (!S.tr_full) {
+            const bool ok = rec_u && (nJ == 0 || rec_j) && S.tr_off + nU + nJ <= P.tr_list_cap;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (ok) S.tr_off += nU + nJ;
+                else S.tr_full = 1;
+            }
+            __syncthreads();
+        }
+        if (nU == 0 && nJ == 0) return SolveOut<V>{RGDBEK_OK, k, O.rel, O.nrm};
+
+        // ---- t_{k+1} = b - A x_{k+1}, x_{k+1} adopted (the column pass that
+        // reads t_k has been waited for above)
+        phase_residual(P, bs, true);
+        X_SYNC(DS(D_TT), 0, 0);
+        if (lead) st_release_u64(&C->lk_tready, lk_enc(call, j + 1));
+        mark(S, PH_RESID);
+        if (threadIdx.x == 0) O.tt = red[D_TT];
+    }
+}
+
+#undef X_SYNC
+#undef X_WAIT
+
+#define Z_SYNC(dm, dx, im)                                                        \
+    do {                                                                          \
+        if (!sync_collect(P, S, (dm), (dx), (im), red)) return -1;                \
+    } while (0)
+#define Z_WAIT(word, target)                                                      \
+    do {                                                                          \
+        const int r_ = link_wait(C, &C->word, (target), call);                    \
+        if (r_ != 0) return r_;                                                   \
+    } while (0)
+
+// The column team's part of a two-team solve.  Returns 1 once the row team
+// has finished, -1 if a barrier or wait was abandoned.
+template <typename V>
+__device__ __forceinline__ int zchain_body(const ParamsT<V> &P, SolveSmem &S,
+                                           unsigned char *dsmem, unsigned long long call,
+                                           int *const *ulists) {
+    BlockScratch &bs = S.bs;
+    OuterStateT<V> &O = S.o<V>();
+    V *const red = S.red<V>();
+    const int nct = tsize(P);
+    Ctrl *const C = P.ctrl;
+    const bool lead = trank(P) == 0 && threadIdx.x == 0;
+
+    // ---- z_0 = b, ||z_0||^2
+    {
+        V zz = V(0);
+        for (long long i = tthread(P); i < P.m; i += tthreads(P)) {
+            const V bi = ld_rhs(P.b + i);
+            P.z[2 * i] = bi;
+            zz = vfma(bi, bi, zz);
+        }
+        zz = block_sum(zz, bs);
+        if (threadIdx.x == 0) P.pd[D_ZZ * nct + trank(P)] = zz;
+    }
+    Z_SYNC(DS(D_ZZ), 0, 0);
+    if (threadIdx.x == 0) {
+        O.zz = red[D_ZZ];
+        O.itol = (V)P.inner_tol;
+    }
+    __syncthreads();
+    mark(S, PH_SETUP);
+
+    for (long long k = P.k0;; ++k) {
+        const long long j = k - P.k0;
+        const int sl = (int)(j & 1);
+        // ---- g = A^T z_k, eps^z, and h = A^T t for the row team's test:
+        // t_{k0} at j = 0, t_{k-1} from j = 2 on (none is due at j = 1)
+        const bool with_h = j != 1;
+        if (with_h) Z_WAIT(lk_tready, lk_enc(call, j == 0 ? 0 : j - 1));
+        phase_col(P, bs, false, with_h);
+        // rank 0 reports whether the row team has finished: all CTAs then
+        // leave after the barrier together
+        if (threadIdx.x == 0)
+            P.pi[I_STOP * nct + trank(P)] =
+                (trank(P) == 0 && ld_acquire_u64(&C->lk_stop) >= call) ? 1 : 0;
+        Z_SYNC(DS(D_EMAX_C) | DS(D_HH) | DS(D_GG), DS(D_EMAX_C), DS(I_BAD_C) | DS(I_STOP));
+        mark(S, PH_COL);
+        if (S.red_i[I_STOP] != 0) return 1;
+        if (P.tr_g && k < P.tr_vec_cap)  // trace: g = A^T z_k
+            for (long long c = tthread(P); c < P.n; c += tthreads(P))
+                P.tr_g[k * P.n + c] = (double)P.g[c];
+        if (lead) {
+            C->lk_hh[sl] = (double)red[D_HH];
+            C->lk_badc[sl] = S.red_i[I_BAD_C];
+            if (j == 0) C->lk_gg = (double)red[D_GG];  // g = A^T z_0 = A^T b
+            st_release_u64(&C->lk_colpass, lk_enc(call, j + 1));
+        }
+        if (threadIdx.x == 0) O.emax_c = red[D_EMAX_C];
+        __syncthreads();
+
+        // ---- column block U_k
+        BlockInfo U{0, 0, 0, 1};
+        if (O.emax_c > V(0)) {
+            if (col_block<V>(P, S, dsmem, k, ulists[sl], false, 0, U) < 0) return -1;
+        }
+
+        // ---- z_{k+1} = z_k - A_U y, once the row team has read z_k
+        if (j >= 1) Z_WAIT(lk_zused, lk_enc(call, j));
+        phase_zupdate<V, 1>(P, U.n > 0, U.lanes, bs);
+        Z_SYNC(DS(D_ZZ), 0, 0);
+        mark(S, PH_ZUPD);
+        if (threadIdx.x == 0) O.zz = red[D_ZZ];
+        if (lead) {
+            C->lk_nu[sl] = U.n;
+            C->lk_nnzu[sl] = U.nnz;
+            C->lk_stepsu[sl] = U.steps;
+            st_release_u64(&C->lk_zready, lk_enc(call, j + 1));
+        }
+        __syncthreads();
+    }
+}
+
+#undef Z_SYNC
+#undef Z_WAIT
+
+// A solve with P.zteam > 0, called by every CTA of the grid (after
+// enter_team and init_solve_smem): the two teams of the two-team schedule
+// run their parts on their own copies of the parameters (in shared memory;
+// the column team with its own work buffers and partials), then every CTA
+// learns the row team's result after a whole-grid barrier (the refinement
+// loop goes on with the whole grid).
+template <typename V>
+__device__ __forceinline__ SolveOut<V> solve_split(const ParamsT<V> &P, SolveSmem &S,
+                                                   unsigned char *dsmem) {
+    __shared__ ParamsT<V> SP;
+    __shared__ unsigned long long s_call;
+    const int tz = P.zteam, tx = P.team - P.zteam;
+    const bool isZ = (int)blockIdx.x >= tx;
+    copy_params(SP, P);
+    if (threadIdx.x == 0) {
+        SP.zteam = 0;
+        SP.team = isZ ? tz : tx;
+        if (isZ) {
+            SP.bar = &P.ctrl->bar_z;
+            SP.pd = P.pd_z;
+            SP.pi = P.pi_z;
+            SP.Q = P.Q_z;
+            SP.flag = P.flag_z;
+            SP.uu = P.uu_z;
+            SP.vv = P.vv_z;
+            SP.ww = P.ww_z;
+            SP.dots = P.dots_z;
+            SP.dots2 = P.dots2_z;
+        } else {
+            SP.bar = &P.ctrl->bar_x;
+        }
+        s_team_rank = isZ ? (int)blockIdx.x - tx : (int)blockIdx.x;
+        S.leader = s_team_rank == 0;
+        S.tlast = globaltimer_ns();
+        const unsigned long long e = S.epoch;
+        S.epoch = S.epoch_sub;
+        S.epoch_sub = e;
+        s_call = ++S.split_calls;
+    }
+    __syncthreads();
+    int *const ulists[2] = {P.ulist, P.ulist2};
+    Ctrl *const C = P.ctrl;
+    if (isZ) {
+        zchain_body<V>(SP, S, dsmem, s_call, ulists);
+        if (S.leader && threadIdx.x == 0)
+            for (int i = 0; i < RGDBEK_NUM_PHASES; ++i) C->zphase_ns[i] = S.tphase[i];
+    } else {
+        const SolveOut<V> o = xchain_body<V>(SP, S, dsmem, s_call, ulists);
+        if (S.leader && threadIdx.x == 0) {
+            C->lk_res_k = o.k;
+            C->lk_res_status = o.status;
+            C->lk_res_rel = (double)o.rel;
+            C->lk_res_nrm = (double)o.nrm;
+            st_release_u64(&C->lk_stop, s_call);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_team_rank = (int)(blockIdx.x % (unsigned)P.team);
+        S.leader = s_team_rank == 0;
+        const unsigned long long e = S.epoch;
+        S.epoch = S.epoch_sub;
+        S.epoch_sub = e;
+    }
+    __syncthreads();
+    if (!grid_barrier(C, S.epoch, P.team)) return SolveOut<V>{kAbandoned, 0, V(0), V(0)};
+    return SolveOut<V>{__ldcg(&C->lk_res_status), __ldcg(&C->lk_res_k), (V)__ldcg(&C->lk_res_rel),
+                       (V)__ldcg(&C->lk_res_nrm)};
+}
+
+// One solve by the whole grid: two-team schedule when P.zteam > 0.
+template <typename V>
+__device__ __forceinline__ SolveOut<V> solve_any(const ParamsT<V> &P, SolveSmem &S,
+                                                 unsigned char *dsmem) {
+    if (P.zteam > 0) return solve_split<V>(P, S, dsmem);
+    return solve_body<V>(P, S, dsmem);
+}
 
 // ---------------------------------------------------------------------------
 // RGDBEK_PRECISION_FP32_INNER: FP32 inner RGDBEK wrapped in FP64 iterative
@@ -1037,11 +1722,20 @@ __device__ __forceinline__ void phase_outer_normal(const Params &P, const double
 // buffers ref_t / ref_b / ref_x and the FP64 work vectors for FP64 inner
 // solves); F: the FP32 view of the same system (A_f32, float work vectors, its
 // own right-hand side F.b written here, solution F.x).
+// kSplit: the inner solves may use the two-team schedule (single solves);
+// the batched kernel runs one team per system and compiles without it.
+template <bool kSplit = true>
 __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F, SolveSmem &S,
                                             unsigned char *dsmem) {
     BlockScratch &bs = S.bs;
     RefineState &R = S.ref;
     double *const t64 = P.ref_t;  // the FP64 residual b - A x
+    // the parameters of the inner solves (their tolerance and first iteration
+    // set per solve), in shared memory
+    __shared__ ParamsF s_fj;
+    __shared__ Params s_pj;
+    copy_params(s_fj, F);
+    copy_params(s_pj, P);
     double *const red = S.red_d;
 #define RGD_SYNC64(dm, im)                                                         \
     do {                                                                           \
@@ -1156,21 +1850,29 @@ __device__ __forceinline__ void refine_body(const Params &P, const ParamsF &F, S
         int ist;
         if (!fp64) {
             // ---- d = FP32 RGDBEK(A_f32, t / ||t||)
-            ParamsF Fj = F;
-            Fj.tol = R.itol;
-            Fj.k0 = k;
-            const SolveOut<float> o = solve_body<float>(Fj, S, dsmem);
+            if (threadIdx.x == 0) {
+                s_fj.tol = R.itol;
+                s_fj.k0 = k;
+            }
+            __syncthreads();
+            SolveOut<float> o;
+            if constexpr (kSplit) o = solve_any<float>(s_fj, S, dsmem);
+            else o = solve_body<float>(s_fj, S, dsmem);
             ist = o.status;
             k = o.k;
         } else {
             // ---- d = FP64 RGDBEK(A, t / ||t||)
-            Params Pj = P;
-            Pj.b = P.ref_b;
-            Pj.x = P.ref_x;
-            Pj.warm = 0;
-            Pj.tol = R.itol;
-            Pj.k0 = k;
-            const SolveOut<double> o = solve_body<double>(Pj, S, dsmem);
+            if (threadIdx.x == 0) {
+                s_pj.b = P.ref_b;
+                s_pj.x = P.ref_x;
+                s_pj.warm = 0;
+                s_pj.tol = R.itol;
+                s_pj.k0 = k;
+            }
+            __syncthreads();
+            SolveOut<double> o;
+            if constexpr (kSplit) o = solve_any<double>(s_pj, S, dsmem);
+            else o = solve_body<double>(s_pj, S, dsmem);
             ist = o.status;
             k = o.k;
         }
@@ -1209,7 +1911,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(const Params P) {
     extern __shared__ __align__(16) unsigned char dsmem[];
     enter_team(P);
     init_solve_smem(S, P);
-    const SolveOut<double> o = solve_body<double>(P, S, dsmem);
+    const SolveOut<double> o = solve_any<double>(P, S, dsmem);
     if (o.status != kAbandoned) finish(P, o.status, o.k, o.rel, o.nrm, 0, S);
 }
 
@@ -1220,7 +1922,7 @@ __global__ void __launch_bounds__(NT, 1) refine_kernel(const Params P, const Par
     extern __shared__ __align__(16) unsigned char dsmem[];
     enter_team(P);
     init_solve_smem(S, P);
-    refine_body(P, F, S, dsmem);
+    refine_body<true>(P, F, S, dsmem);
 }
 
 // Many independent systems in one cooperative launch: the grid is cut into
@@ -1256,7 +1958,7 @@ __global__ void __launch_bounds__(NT, 1)
         enter_team(SP);
         init_solve_smem(S, SP);
         if constexpr (F32) {
-            refine_body(SP, SF, S, dsmem);
+            refine_body<false>(SP, SF, S, dsmem);
         } else {
             const SolveOut<double> o = solve_body<double>(SP, S, dsmem);
             if (o.status != kAbandoned) finish(SP, o.status, o.k, o.rel, o.nrm, 0, S);

@@ -99,8 +99,10 @@ def test_batch_of_one_equals_single_solve_and_is_deterministic(rg, systems):
     import torch
     S, _ = systems
     s0 = S[0]
+    # the batched kernel runs one team per system: compare with the single
+    # solve's one-team schedule
     h = rg.Solver(s0.m, s0.n, s0.row_ptr, s0.col_idx, s0.vals, eta_col=0.2, eta_row=0.2,
-                  stop_rule=rg.STOP_NORMAL)
+                  stop_rule=rg.STOP_NORMAL, col_team=-1)
     grid = h.info().grid
     h.set_options(batch_team=grid)
     b = G.dev(s0.b)

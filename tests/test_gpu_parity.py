@@ -343,13 +343,13 @@ def test_batched_matches_single(rg):
     bs = [G.dev(S.b) for S in systems]
     xs = [torch.empty(S.n, dtype=torch.float64, device="cuda") for S in systems]
     # with the whole grid as the team, each system is solved exactly as
-    # rgdbek_solve would (system_id = its index)
+    # rgdbek_solve with one team (col_team = -1) would (system_id = its index)
     solvers[0].set_options(batch_team=solvers[0].info().grid)
     status, stats = rg.rgdbek_solve_batched([s.handle for s in solvers], bs, xs,
                                             [1e-10] * 3, 3000, seed=6)
     assert status == rg.OK
     for i, (S, s) in enumerate(zip(systems, solvers)):
-        s.set_options(system_id=i)
+        s.set_options(system_id=i, col_team=-1)
         single = s.solve(bs[i], tol=1e-10, max_iter=3000, seed=6)
         assert np.array_equal(G.host(single.x), G.host(xs[i]))
         assert stats[i].iters == single.stats.iters

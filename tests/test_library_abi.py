@@ -67,6 +67,14 @@ def test_host_only_calls():
         assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 1, rp.ctypes.data, ci.ctypes.data,
                                      av.ctypes.data, 0, ctypes.byref(bad), None) \
             == rg.ERR_INVALID_ARG
+    # the column team of the two-team schedule: -1 (one team), 0 (automatic)
+    # or a CTA count up to the largest grid
+    assert rg.default_options().col_team == 0
+    for c in (-2, 1025):
+        bad = rg.default_options(col_team=c)
+        assert rg._lib.rgdbek_create(ctypes.byref(h), 1, 1, 1, rp.ctypes.data, ci.ctypes.data,
+                                     av.ctypes.data, 0, ctypes.byref(bad), None) \
+            == rg.ERR_INVALID_ARG
 
 
 def test_size_limits_rejected_before_any_device_call():
