@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--col-team", type=int, default=None,
                     help="CTAs of the column team of the two-team schedule (0 automatic, -1 one "
                          "team); default: the library's automatic choice")
+    ap.add_argument("--smem-kb", type=int, default=None,
+                    help="dynamic shared memory per CTA of the solve kernel in KB (default: "
+                         "the library's automatic size)")
     ap.add_argument("--fp32", action="store_true",
                     help="batched_deblur: the FP32 form (FP64 refinement) instead of FP64")
     return ap.parse_args()
@@ -123,18 +126,28 @@ def algorithmic_bytes(st, m: int, n: int, nnz: int) -> float:
                         + (12 * nnz + 24 * m + 8 * n))      # residual pass t = b - A xt
     # the last column pass (the converged test) has no residual pass after it
     full_passes += 12 * nnz + 16 * m + 56 * n
-    selection = it * (23 * n + 23 * m)                      # quantise, marks, compaction
-    # one-pass extraction of A_U (over CSR) and A^J (over CSC): pointers,
-    # indices, the selection map once, kept entries and per-line counts
-    extraction = it * ((8 * m + 4 * nnz + 4 * n + 4 * m) + (8 * n + 4 * nnz + 4 * m + 4 * n))
-    extraction += 12 * st.sum_nnz_u + 12 * st.sum_nnz_j + 24 * st.sum_nu + 16 * st.sum_nj
-    # each inner solve first copies both sides of its block into shared memory
-    caching = 24 * st.sum_nnz_u + 24 * st.sum_nnz_j + 16 * it * (m + n)
+    # quantise (weights read, prefix sums and marks written, the other side's
+    # line counts cleared) and compaction (marks read, list written)
+    selection = it * (22 * n + 22 * m) + 4 * (st.sum_nu + st.sum_nj)
+    # extraction by scatter: the selected lines' pointers, and per block entry
+    # its index and value read, the target line's pointer gathered, its count
+    # incremented, index and value written
+    extraction = 16 * (st.sum_nu + st.sum_nj) + 36 * (st.sum_nnz_u + st.sum_nnz_j)
+    # each inner solve first copies both sides of its block into shared memory;
+    # the scattered side is sorted there and written back and reread
+    caching = 48 * st.sum_nnz_u + 48 * st.sum_nnz_j + 16 * it * (m + n)
     zstep = it * 52 * m + 12 * st.sum_nnz_u + 8 * st.sum_nu
     lsqr_u = 24 * st.lsqr_nnz_u + 32 * m * st.inner_u + 90 * st.lsqr_n_u
     lsqr_j = (12 * st.sum_nnz_j + 16 * n * it + 8 * st.sum_nj        # first v of each row block
               + 24 * st.lsqr_nnz_j + 88 * n * st.inner_j + 44 * st.lsqr_n_j)
     return float(full_passes + selection + extraction + caching + zstep + lsqr_u + lsqr_j)
+
+
+def critical_phases(st, col_team: int) -> int:
+    """Grid phases on the critical chain of one solve (see grid_phases)."""
+    if col_team > 0:
+        return 6 * st.iters + 2 * st.inner_j
+    return 10 * st.iters + 2 * (st.inner_u + st.inner_j)
 
 
 # FP64 flops of one solve: 2 per stored nonzero per sparse product (the
@@ -328,6 +341,8 @@ def run_ours(args):
     opts = dict(eta_col=w["eta"], eta_row=w["eta"], stop_rule=rg.STOP_NORMAL)
     if args.col_team is not None:
         opts["col_team"] = args.col_team
+    if args.smem_kb is not None:
+        opts["smem_per_cta"] = 1024 * args.smem_kb
     if args.precision == "fp32":
         opts["precision"] = rg.PRECISION_FP32_INNER
     if args.only_spmv_large:
@@ -438,6 +453,7 @@ def run_ours(args):
                        "tol": w["tol"], "stop_rule": w["stop_rule"],
                        "l2": "flushed before every timed solve (256 MiB write)",
                        "grid": info.grid, "threads_per_block": info.threads_per_block,
+                       "col_team": info.col_team, "smem_per_cta": info.smem_per_cta,
                        "parallelism": "independent system per GPU" if world > 1 else "1 GPU"},
             "time_to_tol_s": statistics.median(ms) / 1e3,
             "iters_per_solve": [s.iters for s in stats],
@@ -459,13 +475,18 @@ def run_ours(args):
                                   "achieved_tflops": fp64_tflops,
                                   "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal",
                                   "frac": fp64_tflops / FP64_PEAK_TFLOPS}},
-            # the solve is a chain of grid-synchronised phases: per outer
-            # iteration 13 (passes, selections, extractions, z update) plus one
-            # for the row step's first LSQR vector, and two per LSQR step
+            # the solve is a chain of grid-synchronised phases.  One team: per
+            # outer iteration 9 (two passes, two quantise and draw phases, two
+            # compaction-scatters, z update) plus one for the row step's first
+            # LSQR vector, and two per LSQR step.  Two teams: the row team's
+            # chain, 6 per iteration (r phase, quantise, draws, scatter, first
+            # vector, residual pass) and two per row LSQR step; the column
+            # team's phases run beside it
             "grid_phases": {
-                "per_solve": (lambda st: 14 * st.iters + 2 * (st.inner_u + st.inner_j))(st0),
+                "chain": "row team" if info.col_team > 0 else "one team",
+                "per_solve": critical_phases(st0, info.col_team),
                 "us_per_phase": 1e6 * statistics.median(ms) / 1e3 / max(
-                    1, 14 * st0.iters + 2 * (st0.inner_u + st0.inner_j))},
+                    1, critical_phases(st0, info.col_team))},
             "spmv": spmv,
             "spmv_large": spmv_big,
             "adaptive_inner": adaptive,

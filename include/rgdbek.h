@@ -116,13 +116,20 @@ typedef struct {
                               x) run one outer iteration ahead of the row steps, on
                               col_team CTAs of the grid with barriers of their own,
                               while the other CTAs run the row steps.  0 = automatic
-                              (3/16 of the grid; one team when inner_adapt > 0, whose
-                              inner tolerance ties the column step to x, or when the
-                              grid is below 8 CTAs), -1 = one team runs every phase
+                              (a quarter of the grid; one team when inner_adapt > 0,
+                              whose inner tolerance ties the column step to x, or when
+                              the grid is below 8 CTAs), -1 = one team runs every phase
                               in turn, k > 0 = k CTAs (at most half the grid).  The
                               iterates are the same either way up to the rounding of
                               the reductions; rgdbek_solve_batched always runs one
                               team per system */
+    int smem_per_cta;      /* dynamic shared memory (bytes) of each CTA of rgdbek_solve's
+                              kernel, where the inner solves keep their chunk of the
+                              block and of its vectors: 0 = 96 KB (more shrinks the
+                              L1 cache that the full-matrix passes gather through),
+                              else a multiple of 1024, at least 32768, capped at what
+                              the GPU allows beside the kernel's static shared
+                              memory.  Batched solves use 96 KB */
 } rgdbek_options;
 
 typedef struct {
@@ -168,6 +175,7 @@ typedef struct {
     int64_t device_bytes;  /* device memory the handle uses (with its matrix)    */
     int col_team;          /* CTAs of the column team of the next rgdbek_solve
                               (option col_team resolved; 0 = one team)          */
+    int smem_per_cta;      /* dynamic shared memory per CTA of rgdbek_solve      */
 } rgdbek_info_t;
 
 /* Fills *opt with the defaults: eta_col = eta_row = 0.5 (the paper's
@@ -300,6 +308,22 @@ int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candid
  * first error (the options are then left as they were). */
 int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uint64_t seed,
                 int *block_out, double *ms_out);
+
+/* Autotuner of the two-team schedule (option col_team): runs probe_iters
+ * outer iterations from x0 = 0 on b (device, m) into x (device, n,
+ * overwritten) with one team and with column teams of 2/16, 3/16, 4/16 and
+ * 5/16 of the grid (RGDBEK_COL_TEAM_CANDIDATES runs, in that order), times
+ * each with CUDA events on the handle's stream and keeps the fastest as the
+ * handle's col_team.  The right split depends on how the column step's work
+ * (the z recurrence) compares with the row step's on the matrix.  *col_team_out
+ * (may be NULL) receives it (-1 = one team); ms_out (host
+ * double[RGDBEK_COL_TEAM_CANDIDATES], may be NULL) each time, -1 where skipped
+ * (grids below 8 CTAs run one team).  The probes run their full length
+ * whatever the handle's time_budget_s.  Returns OK or the first error (the
+ * options are then left as they were). */
+#define RGDBEK_COL_TEAM_CANDIDATES 5
+int rgdbek_tune_teams(rgdbek_t h, const double *b, double *x, int64_t probe_iters,
+                      uint64_t seed, int *col_team_out, double *ms_out);
 
 /* Autotuner of the work split of the full-matrix passes (A^T z and b - A x
  * of every outer iteration, the FP64 passes of the refinement loop and the

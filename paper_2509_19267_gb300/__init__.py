@@ -12,6 +12,7 @@ Entry points (each a function of the same name as in the header):
   rgdbek_solve, rgdbek_solve_host      one solve (device or host buffers)
   rgdbek_solve_batched                 many systems in one persistent launch
   rgdbek_tune, rgdbek_tune_batched     measured choice of kernel shape / team
+  rgdbek_tune_teams                    measured choice of the two-team split
   rgdbek_tune_eta                      measured choice of the block fraction eta
   rgdbek_backward                      implicit adjoint (dL/db, dL/dA)
   rgdbek_spmv, rgdbek_spmv_t, rgdbek_weights, rgdbek_sample,
@@ -70,7 +71,7 @@ class rgdbek_options(ctypes.Structure):
         ("inner_max", _int), ("stop_rule", _int), ("time_budget_s", _dbl), ("system_id", _u64),
         ("blocks_per_sm", _int), ("threads_per_block", _int), ("precision", _int),
         ("batch_team", _int), ("warm_start", _int), ("inner_adapt", _dbl),
-        ("col_team", _int),
+        ("col_team", _int), ("smem_per_cta", _int),
     ]
 
 
@@ -92,7 +93,7 @@ class rgdbek_info_t(ctypes.Structure):
     _fields_ = [
         ("m", _i64), ("n", _i64), ("nnz", _i64), ("grid", _int), ("threads_per_block", _int),
         ("lanes_per_row", _int), ("lanes_per_col", _int), ("num_sms", _int),
-        ("device_bytes", _i64), ("col_team", _int),
+        ("device_bytes", _i64), ("col_team", _int), ("smem_per_cta", _int),
     ]
 
 
@@ -119,6 +120,7 @@ SIGNATURES = [
                            ctypes.POINTER(_dbl)]),
     ("rgdbek_tune_eta", _int, [_ptr, _ptr, _ptr, _ptr, _int, _i64, _u64,
                                ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
+    ("rgdbek_tune_teams", _int, [_ptr, _ptr, _ptr, _i64, _u64, ctypes.POINTER(_int), _ptr]),
     ("rgdbek_tune_spmv", _int, [_ptr, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
                                 ctypes.POINTER(_dbl)]),
     ("rgdbek_set_pass_lanes", _int, [_ptr, _int, _int]),
@@ -315,6 +317,19 @@ def rgdbek_tune(h: int, b, x, probe_iters: int = 5, seed: int = 0):
     return block.value, {512: ms[0], 1024: ms[1]}
 
 
+COL_TEAM_CANDIDATES = 5
+
+
+def rgdbek_tune_teams(h: int, b, x, probe_iters: int = 10, seed: int = 0):
+    """Times one team and column teams of 2/16 .. 5/16 of the grid; the handle
+    keeps the fastest.  Returns (col_team, [ms per candidate], -1 = skipped)."""
+    best = _int(0)
+    ms = (_dbl * COL_TEAM_CANDIDATES)()
+    _check(_lib.rgdbek_tune_teams(h, _dptr(b), _dptr(x), probe_iters, seed, ctypes.byref(best),
+                                  ctypes.cast(ms, ctypes.c_void_p)), "rgdbek_tune_teams")
+    return best.value, list(ms)
+
+
 ETA_CANDIDATES = (0.05, 0.1, 0.2, 0.3, 0.5)
 
 
@@ -472,6 +487,13 @@ class Solver:
 
     def info(self) -> rgdbek_info_t:
         return rgdbek_get_info(self.handle)
+
+    def tune_teams(self, b, probe_iters: int = 10, seed: int = 0):
+        """Measured choice of the column team (rgdbek_tune_teams); the solver
+        keeps it.  Returns (col_team, [ms per candidate])."""
+        import torch
+        x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        return rgdbek_tune_teams(self.handle, b, x, probe_iters, seed)
 
     def tune_eta(self, b, candidates=None, probe_iters: int = 20, seed: int = 0):
         """Measured choice of eta (rgdbek_tune_eta); the solver keeps it.

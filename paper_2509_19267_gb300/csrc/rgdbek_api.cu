@@ -79,6 +79,7 @@ struct rgdbek_s {
     // launch shape
     int grid = 0, block = 0, sample_grid = 0, tpr = 1, tpc = 1, ipr = 1, ipc = 1;
     int lpr = 1, lpc = 1;  // lanes of the full-matrix passes (rgdbek_tune_spmv)
+    int dsmem = kSolveDsmemBytes;  // dynamic shared memory per CTA of the single solve
     int tuned_team = 0;   // team size found by rgdbek_tune_batched (0 = none yet)
     int tuned_block = 0;  // block of the batched solve found by it (0 = automatic)
     // trace
@@ -196,6 +197,8 @@ int check_options(const rgdbek_options &o) {
     if (o.warm_start != 0 && o.warm_start != 1) return RGDBEK_ERR_INVALID_ARG;
     if (!(o.inner_adapt >= 0.0)) return RGDBEK_ERR_INVALID_ARG;
     if (o.col_team < -1 || o.col_team > kMaxGrid) return RGDBEK_ERR_INVALID_ARG;
+    if (o.smem_per_cta != 0 && (o.smem_per_cta < 32768 || o.smem_per_cta % 1024 != 0))
+        return RGDBEK_ERR_INVALID_ARG;
     if (o.threads_per_block != 0 &&
         (o.threads_per_block % 32 != 0 || o.threads_per_block < 64 ||
          o.threads_per_block > kSolveMaxThreads))
@@ -207,7 +210,13 @@ int check_options(const rgdbek_options &o) {
 int configure_launch(rgdbek_s *h) {
     const int block = h->opt.threads_per_block ? h->opt.threads_per_block
                                                : auto_solve_block(h->m, h->n, h->num_sms);
-    int fit = solve_blocks_per_sm(block);
+    const int dmax = solve_dsmem_max();
+    if (dmax <= 0) return RGDBEK_ERR_CUDA;
+    // 96 KB unless asked: more shared memory shrinks the L1 cache, and the
+    // full-matrix passes then lose more than the inner solves gain (measured)
+    const int want = h->opt.smem_per_cta ? h->opt.smem_per_cta : kSolveDsmemBytes;
+    const int dsmem = want < dmax ? want : dmax;
+    int fit = solve_blocks_per_sm(block, dsmem);
     int fit_s = sample_blocks_per_sm(block);
     if (fit < 1 || fit_s < 1) return RGDBEK_ERR_CUDA;
     int bps = h->opt.blocks_per_sm ? h->opt.blocks_per_sm : fit;
@@ -219,6 +228,7 @@ int configure_launch(rgdbek_s *h) {
     h->block = block;
     h->grid = (int)grid;
     h->sample_grid = (int)sgrid;
+    h->dsmem = dsmem;
     return RGDBEK_OK;
 }
 
@@ -300,7 +310,7 @@ Params make_params(const rgdbek_s *h, bool transposed = false) {
     P.lpc = h->lpc;
     P.ipr = h->ipr;
     P.ipc = h->ipc;
-    P.dsmem_bytes = kSolveDsmemBytes;
+    P.dsmem_bytes = h->dsmem;
     P.team = h->grid;
     P.zteam = 0;  // one team unless the solve chooses two (run_solve)
     P.uu_z = h->uu_z;
@@ -517,7 +527,7 @@ int choose_zteam(const rgdbek_s *h) {
     const int c = h->opt.col_team;
     if (c < 0 || h->opt.inner_adapt > 0.0 || h->grid < 8) return 0;
     if (c > 0) return c < h->grid / 2 ? c : h->grid / 2;
-    const int a = (3 * h->grid + 8) / 16;
+    const int a = h->grid / 4;  // measured best on the 200000 x 50000 benchmark (1/4)
     return a > 1 ? a : 1;
 }
 
@@ -637,7 +647,7 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
         for (int i = 0; i < nsys; ++i) vmax = std::max(vmax, std::max(hs[i]->m, hs[i]->n));
         block = auto_solve_block(vmax, 0, team);
     }
-    const int fit = solve_blocks_per_sm(block);
+    const int fit = batched_blocks_per_sm(block);
     if (fit < 1) return RGDBEK_ERR_CUDA;
     const long long gmax = std::min((long long)kMaxGrid, (long long)fit * h0->num_sms);
     if (team > gmax) return RGDBEK_ERR_INVALID_ARG;
@@ -659,6 +669,7 @@ int run_batched(int nsys, rgdbek_t *hs, const double *const *b, double *const *x
         P.s_col = num_draws(hs[i]->opt.eta_col, P.n);
         P.s_row = num_draws(hs[i]->opt.eta_row, P.m);
         P.team = team;
+        P.dsmem_bytes = kSolveDsmemBytes;  // the batched kernel's launch size
         P.tr_counts = nullptr;
         P.tr_count_cap = 0;
         P.tr_lists = nullptr;
@@ -756,6 +767,7 @@ void rgdbek_default_options(rgdbek_options *opt) {
     opt->warm_start = 0;
     opt->inner_adapt = 0.0;
     opt->col_team = 0;
+    opt->smem_per_cta = 0;
 }
 
 int rgdbek_create(rgdbek_t *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
@@ -985,6 +997,7 @@ int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
     info->num_sms = h->num_sms;
     info->device_bytes = (int64_t)(h->arena_bytes + (h->mat ? h->mat->bytes : 0));
     info->col_team = choose_zteam(h);
+    info->smem_per_cta = h->dsmem;
     return RGDBEK_OK;
 }
 
@@ -1156,6 +1169,60 @@ int rgdbek_tune(rgdbek_t h, const double *b, double *x, int64_t probe_iters, uin
     const int st = configure_launch(h);
     if (block_out) *block_out = best;
     return st;
+}
+
+int rgdbek_tune_teams(rgdbek_t h, const double *b, double *x, int64_t probe_iters,
+                      uint64_t seed, int *col_team_out, double *ms_out) {
+    if (!h || !b || !x || probe_iters < 1) return RGDBEK_ERR_INVALID_ARG;
+    // candidates: one team, then 2/16 .. 5/16 of the grid
+    int cand[RGDBEK_COL_TEAM_CANDIDATES];
+    cand[0] = -1;
+    for (int c = 1; c < RGDBEK_COL_TEAM_CANDIDATES; ++c) {
+        int t = ((c + 1) * h->grid + 8) / 16;
+        if (t < 1) t = 1;
+        if (t > h->grid / 2) t = h->grid / 2;
+        cand[c] = t;
+    }
+    const rgdbek_options saved = h->opt;
+    int best = 0;
+    bool have = false;
+    float best_ms = 0.f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    h->opt.time_budget_s = 0.0;  // the probes run their full length
+    for (int c = 0; e == cudaSuccess && c < RGDBEK_COL_TEAM_CANDIDATES; ++c) {
+        if (ms_out) ms_out[c] = -1.0;
+        // a team size the grid cannot take (grid below 8 CTAs: one team only)
+        if (c > 0 && (h->grid < 8 || cand[c] < 1)) continue;
+        h->opt.col_team = cand[c];
+        float ms = 0.f;
+        int st = RGDBEK_OK;
+        e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) st = run_solve(h, false, b, x, 0.0, probe_iters, seed, nullptr, true);
+        if (e == cudaSuccess && st < 0 && st != RGDBEK_ERR_NONFINITE) {
+            h->opt = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out && e == cudaSuccess) ms_out[c] = ms;
+        if (e == cudaSuccess && (!have || ms < best_ms)) {
+            best = cand[c];
+            best_ms = ms;
+            have = true;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->opt = saved;
+    if (e != cudaSuccess) return cuda_status(e);
+    h->opt.col_team = best;
+    if (col_team_out) *col_team_out = best;
+    return RGDBEK_OK;
 }
 
 int rgdbek_tune_eta(rgdbek_t h, const double *b, double *x, const double *candidates,

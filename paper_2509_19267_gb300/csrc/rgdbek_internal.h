@@ -23,7 +23,9 @@ inline int auto_solve_block(long long m, long long n, int ctas) {
     return v > kSolveVecPerCta * (long long)(ctas > 0 ? ctas : 1) ? kSolveMaxThreads
                                                                    : kSolveSmallThreads;
 }
-// dynamic shared memory of a solve CTA: its chunk of the inner-solve block
+// dynamic shared memory of a CTA of the batched solve (its chunk of the
+// inner-solve block); the single solve takes what the device allows, or the
+// option smem_per_cta
 constexpr int kSolveDsmemBytes = 96 * 1024;
 
 // One system of a batch: its FP64 view and (for the FP32 form) its FP32 view.
@@ -78,8 +80,12 @@ cudaError_t launch_adjoint_vals(const Params &P, int grid, int block, const doub
                                 const double *q, double *gv, cudaStream_t s);
 cudaError_t launch_weights(const double *v, const double *norm2, long long len, double *eps,
                            Ctrl *ctrl, int grid, int block, cudaStream_t s);
+// dynamic shared memory the single-solve kernels may use on the current
+// device (set as their limit; 0 on error)
+int solve_dsmem_max();
 // CTAs of `block` threads of the persistent kernels that fit on one SM
-int solve_blocks_per_sm(int block);
+int solve_blocks_per_sm(int block, int dsmem);
+int batched_blocks_per_sm(int block);
 int sample_blocks_per_sm(int block);
 
 // ---- set-up (rgdbek_setup.cu) ----------------------------------------------

@@ -289,29 +289,65 @@ cudaError_t launch_gather_ctrls(const SysPair *sys_dev, int nsys, Ctrl *out, cud
     return cudaGetLastError();
 }
 
-// CTAs of `block` threads of the solve kernels that fit on one SM (the
-// smallest over the shape's kernels).  Every solve kernel of both shapes is
-// given the dynamic shared memory it launches with: a batch may run the other
-// shape than its first handle.
-int solve_blocks_per_sm(int block) {
+// Largest dynamic shared memory of a CTA of the single-solve kernels on the
+// current device: the opt-in limit per block less the largest static shared
+// memory of those kernels (1 KB granules).  Every single-solve kernel is
+// allowed that much; the batched kernels get kSolveDsmemBytes.  0 on error.
+int solve_dsmem_max() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    size_t stat = 0;
     for (int sh = 0; sh < 2; ++sh)
         for (int f32 = 0; f32 < 2; ++f32) {
+            cudaFuncAttributes a{};
+            if (cudaFuncGetAttributes(&a, solve_kernel_fn(f32 != 0, sh != 0)) != cudaSuccess)
+                return 0;
+            if (a.sharedSizeBytes > stat) stat = a.sharedSizeBytes;
+        }
+    const int avail = (int)(((long long)optin - (long long)stat) & ~1023ll);
+    if (avail < kSolveDsmemBytes) return 0;
+    for (int sh = 0; sh < 2; ++sh)
+        for (int f32 = 0; f32 < 2; ++f32)
             if (cudaFuncSetAttribute(solve_kernel_fn(f32 != 0, sh != 0),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSolveDsmemBytes) != cudaSuccess ||
-                cudaFuncSetAttribute(batched_kernel_fn(f32 != 0, sh != 0),
+                                     avail) != cudaSuccess)
+                return 0;
+    return avail;
+}
+
+// CTAs of `block` threads of the single-solve kernels with dsmem bytes of
+// dynamic shared memory that fit on one SM (the smaller of the FP64 and FP32
+// form's kernel); solve_dsmem_max must have run.
+int solve_blocks_per_sm(int block, int dsmem) {
+    const bool small = block <= kSolveSmallThreads;
+    int best = 1 << 30;
+    for (int f32 = 0; f32 < 2; ++f32) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel_fn(f32 != 0, small),
+                                                          block, dsmem) != cudaSuccess)
+            return 0;
+        if (nb < best) best = nb;
+    }
+    return best;
+}
+
+// The same for the batched kernels (kSolveDsmemBytes each; both shapes are
+// given it, as a batch may run the other shape than its first handle).
+int batched_blocks_per_sm(int block) {
+    for (int sh = 0; sh < 2; ++sh)
+        for (int f32 = 0; f32 < 2; ++f32)
+            if (cudaFuncSetAttribute(batched_kernel_fn(f32 != 0, sh != 0),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kSolveDsmemBytes) != cudaSuccess)
                 return 0;
-        }
     const bool small = block <= kSolveSmallThreads;
-    const void *fns[4] = {solve_kernel_fn(false, small), solve_kernel_fn(true, small),
-                          batched_kernel_fn(false, small), batched_kernel_fn(true, small)};
     int best = 1 << 30;
-    for (const void *f : fns) {
+    for (int f32 = 0; f32 < 2; ++f32) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, kSolveDsmemBytes) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel_fn(f32 != 0, small),
+                                                          block, kSolveDsmemBytes) != cudaSuccess)
             return 0;
         if (nb < best) best = nb;
     }

@@ -245,7 +245,7 @@ __device__ __forceinline__ void line_span(const SideC<V> &S, long long l, long l
 // from the global arrays through line_span.
 template <typename V>
 struct CtaSide {
-    const long long *ptr;
+    const int *ptr;      // cached: chunk-local line offsets
     const int *idx;
     const V *val;        // cached values
     int nl;
@@ -406,9 +406,10 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
     out.idx = nullptr;
     out.val = nullptr;
     const SmemArena save = A;
-    long long *ps = A.take<long long>(out.nl + 1);
-    long long *gs = ps ? A.take<long long>(out.nl) : nullptr;  // global start of each line
-    if (!gs) {
+    // chunk-local offsets of the lines (the global starts are reread where
+    // needed: shared memory is kept for the entries)
+    int *ps = A.take<int>(out.nl + 1);
+    if (!ps) {
         A = save;
         if (sort)
             sort_scattered_lines<V>(S.ptr, S.cnt, const_cast<int *>(S.idx), const_cast<V *>(S.val),
@@ -424,14 +425,13 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
             long long b, e;
             line_span(S, C.lo + li, b, e);
             len = e - b;
-            gs[li] = b;
         }
         long long tot;
         const long long ex = block_excl_scan<long long>(len, bs, &tot);
-        if (li < out.nl) ps[li] = run + ex;
+        if (li < out.nl) ps[li] = (int)(run + ex);
         run += tot;
     }
-    if (threadIdx.x == 0) ps[out.nl] = run;
+    if (threadIdx.x == 0) ps[out.nl] = (int)run;
     // FP32 products are cheap to reduce across lanes, so they spread each line
     // over enough lanes for about four entries per lane (one round of
     // gathers), as far as warps 1.. cover all lines in one pass
@@ -442,7 +442,7 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
         while (Lf < 32 && 4ll * Lf < per_line) Lf *= 2;
         while (Lf > 1 && (long long)out.nl * Lf > lanes) Lf >>= 1;
     }
-    int *is = A.take<int>(run);
+    int *is = run < (1ll << 30) ? A.take<int>(run) : nullptr;
     V *vs = is ? A.take<V>(run) : nullptr;
     if (!vs) {
         A = save;
@@ -460,7 +460,9 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
         for (int base = 0; base < out.nl; base += per) {
             const int li = base + (threadIdx.x >> 5) * G.rpw + G.sub;
             if (li < out.nl) {
-                const long long b = gs[li], o = ps[li], len = ps[li + 1] - o;
+                long long b, e;
+                line_span(S, C.lo + li, b, e);
+                const long long o = ps[li], len = ps[li + 1] - o;
                 for (long long k = G.sl; k < len; k += G.L) {
                     is[o + k] = S.idx[b + k];
                     vs[o + k] = S.val[b + k];
@@ -487,9 +489,11 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
                 const int li = base + warp * G.rpw + G.sub;
                 if (li < out.nl) {
                     const long long o = ps[li], len = ps[li + 1] - o;
-                    if (len >= 2 && len <= cap)
-                        rank_place(is + o, vs + o, (int)len, G.sl, G.L, gidx + gs[li],
-                                   gval + gs[li]);
+                    if (len >= 2 && len <= cap) {
+                        long long b, e;
+                        line_span(S, C.lo + li, b, e);
+                        rank_place(is + o, vs + o, (int)len, G.sl, G.L, gidx + b, gval + b);
+                    }
                     has_long |= len > cap;
                 }
             }
@@ -497,8 +501,11 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
         if (__syncthreads_or(has_long)) {
             for (int li = warp; li < out.nl; li += nw) {
                 const long long o = ps[li], len = ps[li + 1] - o;
-                if (len > cap)
-                    rank_place(is + o, vs + o, (int)len, lane, 32, gidx + gs[li], gval + gs[li]);
+                if (len > cap) {
+                    long long b, e;
+                    line_span(S, C.lo + li, b, e);
+                    rank_place(is + o, vs + o, (int)len, lane, 32, gidx + b, gval + b);
+                }
             }
         }
         __syncthreads();
@@ -507,7 +514,9 @@ __device__ __forceinline__ CtaSide<V> cache_side(const SideC<V> &S, SmemArena &A
         for (int base = 0; base < out.nl; base += nw * G.rpw) {
             const int li = base + warp * G.rpw + G.sub;
             if (li < out.nl) {
-                const long long o = ps[li], len = ps[li + 1] - o, b = gs[li];
+                const long long o = ps[li], len = ps[li + 1] - o;
+                long long b = 0, e;
+                if (len >= 2) line_span(S, C.lo + li, b, e);
                 if (len >= 2)
                     for (long long k = G.sl; k < len; k += G.L) {
                         is[o + k] = gidx[b + k];
@@ -534,6 +543,68 @@ __device__ __forceinline__ void cta_dots(const CtaSide<V> &C, const V *vec, V *d
     const int warp = threadIdx.x >> 5;
     if (warp == 0) return;
     const int L = (sizeof(V) == 4 && C.cached) ? C.Lf : C.L;
+    if (!C.cached && L == 1) {
+        // Short lines read from global memory (a chunk larger than shared
+        // memory, e.g. the u-space of a column block on a small team): one
+        // lane per line and four lines per lane at a time, their entries two
+        // per round, so the loads of eight entries and their gathers are in
+        // flight together.  Each line still sums in entry order from zero, as
+        // lane_dot does, so the results are the same.
+        const int per = ((blockDim.x >> 5) - 1) * 32;
+        const int me = (warp - 1) * 32 + (threadIdx.x & 31);
+        for (int base = 0; base < C.nl; base += 4 * per) {
+            long long b[4], e[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int li = base + q * per + me;
+                b[q] = 0;
+                e[q] = 0;
+                if (li < C.nl) line_span(C.g, C.lo + li, b[q], e[q]);
+            }
+            V s[4] = {V(0), V(0), V(0), V(0)};
+            KahanF kf[4];
+            for (;;) {
+                int j[4][2];
+                V a[4][2];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const long long f = b[q] + t;
+                        const bool v = f < e[q];
+                        j[q][t] = v ? C.g.idx[f] : -1;
+                        a[q][t] = v ? C.g.val[f] : V(0);
+                        any |= v;
+                    }
+                if (!any) break;
+                V x[4][2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) x[q][t] = j[q][t] >= 0 ? vec[j[q][t]] : V(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        if (j[q][t] < 0) continue;
+                        if constexpr (sizeof(V) == 8) s[q] = fma(a[q][t], x[q][t], s[q]);
+                        else kf[q].add(a[q][t], x[q][t]);
+                    }
+                    b[q] += 2;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int li = base + q * per + me;
+                if (li < C.nl) {
+                    if constexpr (sizeof(V) == 8) dots[li] = s[q];
+                    else dots[li] = kf[q].sum();
+                }
+            }
+        }
+        return;
+    }
     const Grp G(L);
     const int per = ((blockDim.x >> 5) - 1) * G.rpw;
     const auto gat = [&](int j) { return vec[j]; };

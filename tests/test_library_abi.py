@@ -51,6 +51,7 @@ def test_host_only_calls():
                                    None) == rg.ERR_INVALID_ARG
     assert rg._lib.rgdbek_tune_eta(None, None, None, None, 0, 5, 0, None, None) \
         == rg.ERR_INVALID_ARG
+    assert rg._lib.rgdbek_tune_teams(None, None, None, 5, 0, None, None) == rg.ERR_INVALID_ARG
     # an unknown precision is rejected by the option check, before the device
     rp = np.array([0, 1], dtype=np.int64)
     ci = np.array([0], dtype=np.int32)
