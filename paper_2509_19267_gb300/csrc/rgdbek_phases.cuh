@@ -236,13 +236,60 @@ struct KahanF {
 
 // This lane's share of sum_e val[e] * f(idx[e]) over e = e, e + L, e + 2L, ...
 // below e1, accumulated in exactly that order (FP64: a chain of fused
-// multiply-adds; FP32: Kahan-compensated).  Four entries are handled per
-// trip with all their loads issued before the arithmetic, so four
-// independent index/value loads and four gathers are in flight per lane.
+// multiply-adds; FP32: Kahan-compensated).
+//
+// FP64: eight entries per trip, all their index/value loads and gathers
+// issued before the multiply-adds; the last 1..7 entries likewise, their
+// loads predicated, and their multiply-adds in a loop of exactly that count
+// that shifts the operands down.  GB300 issues about two FP64 lane-operations
+// per SM per clock, and a multiply-add predicated off still takes its issue
+// slot, so no FP64 instruction is spent on an entry that does not exist.
+//
+// FP32: four entries per trip with all their loads issued before the
+// arithmetic, so four independent index/value loads and four gathers are in
+// flight per lane.
 template <bool RO, typename V, typename F>
 __device__ __forceinline__ V lane_dot(long long e, long long e1, long long L, const int *idx,
                                       const V *val, F f) {
-    V s = V(0);
+    if constexpr (sizeof(V) == 8) {
+        V s = V(0);
+        for (; e + 7 * L < e1; e += 8 * L) {
+            int j[8];
+            V a[8], x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                j[q] = ldx<RO>(idx + e + q * L);
+                a[q] = ldx<RO>(val + e + q * L);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = f(j[q]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s = fma(a[q], x[q], s);
+        }
+        if (e < e1) {
+            int rem = 0, j[7];
+            V a[7], x[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const bool v = e + q * L < e1;
+                rem += v ? 1 : 0;
+                j[q] = v ? ldx<RO>(idx + e + q * L) : 0;
+                a[q] = v ? ldx<RO>(val + e + q * L) : V(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q) x[q] = (e + q * L < e1) ? f(j[q]) : V(0);
+#pragma unroll 1
+            for (int q = 0; q < rem; ++q) {
+                s = fma(a[0], x[0], s);
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    a[t] = a[t + 1];
+                    x[t] = x[t + 1];
+                }
+            }
+        }
+        return s;
+    }
     KahanF k;
     for (; e < e1; e += 4 * L) {
         const bool v1 = e + L < e1, v2 = e + 2 * L < e1, v3 = e + 3 * L < e1;
@@ -258,20 +305,12 @@ __device__ __forceinline__ V lane_dot(long long e, long long e1, long long L, co
         const V x1 = v1 ? f(i1) : V(0);
         const V x2 = v2 ? f(i2) : V(0);
         const V x3 = v3 ? f(i3) : V(0);
-        if constexpr (sizeof(V) == 8) {
-            s = fma(a0, x0, s);
-            if (v1) s = fma(a1, x1, s);
-            if (v2) s = fma(a2, x2, s);
-            if (v3) s = fma(a3, x3, s);
-        } else {
-            k.add(a0, x0);
-            if (v1) k.add(a1, x1);
-            if (v2) k.add(a2, x2);
-            if (v3) k.add(a3, x3);
-        }
+        k.add(a0, x0);
+        if (v1) k.add(a1, x1);
+        if (v2) k.add(a2, x2);
+        if (v3) k.add(a3, x3);
     }
-    if constexpr (sizeof(V) == 8) return s;
-    else return k.sum();
+    return k.sum();
 }
 
 // Two dot products sharing the index/value loads (A^T z and A^T t): the two
