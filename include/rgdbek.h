@@ -116,9 +116,12 @@ typedef struct {
                               x) run one outer iteration ahead of the row steps, on
                               col_team CTAs of the grid with barriers of their own,
                               while the other CTAs run the row steps.  0 = automatic
-                              (a quarter of the grid; one team when inner_adapt > 0,
-                              whose inner tolerance ties the column step to x, or when
-                              the grid is below 8 CTAs), -1 = one team runs every phase
+                              (a quarter of the grid when the solved system has at
+                              least four times as many rows as columns, where the row
+                              step dominates; otherwise one team, as also when
+                              inner_adapt > 0, whose inner tolerance ties the column
+                              step to x, or when the grid is below 8 CTAs), -1 = one
+                              team runs every phase
                               in turn, k > 0 = k CTAs (at most half the grid).  The
                               iterates are the same either way up to the rounding of
                               the reductions; rgdbek_solve_batched always runs one

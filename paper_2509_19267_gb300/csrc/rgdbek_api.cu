@@ -522,19 +522,32 @@ void fill_stats(const Ctrl &c, int status, rgdbek_stats *st);
 
 // One persistent-kernel solve of A x = b (or of A^T x = b when transposed),
 // x0 = 0; reads the control block back into *st.
-// CTAs of the column team of a single solve (0: one team), option col_team.
-int choose_zteam(const rgdbek_s *h) {
+// CTAs of the column team of a single solve (0: one team), option col_team;
+// `transposed`: the solve runs on A^T (rows and columns swap roles).
+//
+// Automatic: two teams only where the row step dominates an outer iteration.
+// With equal eta the two blocks hold about the same number of nonzeros, but
+// for m >> n the row block (about eta m rows of n columns) is much closer to
+// square than the column block (m rows, eta n columns), so its LSQR needs
+// many more steps (47.6 against 7.5 per iteration on the 200000 x 50000
+// benchmark, where a quarter of the grid on the column steps was measured
+// fastest).  Where the two steps cost about the same (square or 2:1 systems,
+// fat systems, blocks at the inner step cap) a column team of a quarter of
+// the grid would become the critical path, so m < 4n runs one team.
+int choose_zteam(const rgdbek_s *h, bool transposed) {
     const int c = h->opt.col_team;
     if (c < 0 || h->opt.inner_adapt > 0.0 || h->grid < 8) return 0;
     if (c > 0) return c < h->grid / 2 ? c : h->grid / 2;
-    const int a = h->grid / 4;  // measured best on the 200000 x 50000 benchmark (1/4)
+    const long long rows = transposed ? h->n : h->m, cols = transposed ? h->m : h->n;
+    if (rows < 4 * cols) return 0;
+    const int a = h->grid / 4;
     return a > 1 ? a : 1;
 }
 
 int run_solve(rgdbek_s *h, bool transposed, const double *b, double *x, double tol,
               long long max_iter, uint64_t seed, rgdbek_stats *st, bool from_zero = false) {
     Params P = make_params(h, transposed);
-    P.zteam = choose_zteam(h);
+    P.zteam = choose_zteam(h, transposed);
     if (from_zero) P.warm = 0;  // the adjoint's inner solves and the tuner's probes
     P.b = b;
     P.x = x;
@@ -996,7 +1009,7 @@ int rgdbek_get_info(rgdbek_t h, rgdbek_info_t *info) {
     info->lanes_per_col = h->lpc;
     info->num_sms = h->num_sms;
     info->device_bytes = (int64_t)(h->arena_bytes + (h->mat ? h->mat->bytes : 0));
-    info->col_team = choose_zteam(h);
+    info->col_team = choose_zteam(h, false);
     info->smem_per_cta = h->dsmem;
     return RGDBEK_OK;
 }

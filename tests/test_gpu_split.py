@@ -64,6 +64,24 @@ def test_team_sizes_against_the_oracle(rg, system, col_team):
     s.close()
 
 
+@pytest.mark.parametrize("m,n,two", [(4000, 1000, True), (6000, 1000, True), (3000, 1000, False),
+                                      (2000, 2000, False), (1000, 3000, False)])
+def test_automatic_choice_follows_the_shape(rg, m, n, two):
+    # two teams (a quarter of the grid on the column steps) only where the row
+    # step dominates: at least four rows per column; one team otherwise
+    S = workloads.sparse_ls(m, n, 8, sigma=1e-2, seed=3)
+    s = rg.Solver(S.m, S.n, *S.A, eta_col=0.2, eta_row=0.2, stop_rule=rg.STOP_NORMAL)
+    grid = s.info().grid
+    assert s.info().col_team == (grid // 4 if two else 0)
+    # either way the solve meets the oracle
+    ref = oracle.solve(S.A, S.b, oracle.Options(eta_col=0.2, eta_row=0.2, stop_rule=2, tol=1e-10,
+                                                max_iter=5000, seed=6), n=S.n)
+    r = s.solve(G.dev(S.b), tol=1e-10, max_iter=5000, seed=6)
+    assert r.stats.status == rg.OK and ref.status == 0
+    assert G.rel(G.host(r.x), ref.x) <= X_TOL
+    s.close()
+
+
 @pytest.mark.parametrize("col_team", [3, 29])
 def test_blocks_replayed_bit_exactly(rg, col_team):
     """Every block of 20 iterations under two teams is the oracle's draw on the
